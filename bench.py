@@ -1,0 +1,361 @@
+"""Benchmark of the fused D2Q9 electrowetting time step (one JSON line).
+
+Default workload: the 16384 x 4096 rough-wall channel (seeded roughness of
+amplitude 6, body force 1e-6) with a row of sessile droplets of radius 20 on
+the bottom wall, FP32 populations -- the largest single-GPU configuration
+and the one whose working set (2 x 2.4 GB) lies far outside the 129 MB L2,
+so every step streams from HBM and no L2 flush is needed between steps.
+
+A step is one pass of the hot path over the whole domain: pull-streaming with
+bounce-back, moments, pseudopotential, the forces of Eq. 5, Eq. 6, the
+electric wall-layer force and the body force, velocity shift, BGK collision,
+store; observables fused every --obs-every steps.
+
+value : MLUPS (million lattice-node updates per second, all nodes), device
+        time with CUDA events on the library's stream, inputs resident.
+e2e   : the same metric through the C ABI with host buffers: the timed region
+        uploads the geometry and the initial (rho, u) field from host memory,
+        then every step launches through lbm_step and reads that step's fused
+        observables record back to the host (lbm_obs_latest).
+--impl reference : the FP64 CPU oracle on a bounded crop of the same workload.
+Under torchrun every rank runs its own replica (weak scaling, no collective on
+the data path); value is the sum over ranks of the node updates / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_NODE_FP32 = 72  # 9 x 4 B read + 9 x 4 B write per fluid node and step
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nx", type=int, default=16384)
+    ap.add_argument("--ny", type=int, default=4096)
+    ap.add_argument("--obs-every", type=int, default=100)
+    ap.add_argument("--tile-rows", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(nx, ny):
+    from paper_0708_4182_gb300 import workloads as wl
+    return wl.droplet_row_channel(nx=nx, ny=ny, amp=6, seed=0, radius=20.0, pitch=128,
+                                  body_fx=1e-6, f_elec=0.0)
+
+
+def workload_name(nx, ny):
+    return (f"rough-wall channel {nx}x{ny}, roughness amplitude 6 (seed 0), body force 1e-6, "
+            f"row of sessile droplets R=20 pitch 128 on the bottom wall, FP32 populations")
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, name in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- helpers
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def traffic_from_profile():
+    """DRAM bytes per launch of the step kernel from the committed ncu summary
+    (None when absent or taken on another kernel version)."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return d
+    except (OSError, ValueError):
+        return None
+
+
+class OracleSample:
+    """The FP64 oracle on a bounded crop of the workload: the 1024 x 256
+    bottom-left crop (droplets, rough bottom wall; a top wall closes it)."""
+
+    def __init__(self, w, cores):
+        os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+        import oracle
+        self.oracle = oracle
+        self.cores = cores
+        self.cy, self.cx = 256, 1024
+        mask = np.ascontiguousarray(w.mask[:self.cy, :self.cx])
+        mask[-1, :] = 1
+        self.mask = mask
+        rho = np.where(mask == 1, 0.0, w.rho[:self.cy, :self.cx])
+        self.p = oracle.Params(self.cx, self.cy, **w.params)
+        self.f = oracle.equilibrium(self.p, mask, rho, 0, 0)
+
+    def run(self, steps):
+        t0 = time.perf_counter()
+        self.f = self.oracle.step(self.p, self.mask, self.f, steps)
+        return time.perf_counter() - t0
+
+    def steps_for(self, seconds):
+        steps, t = 2, 0.0
+        while t < 0.25 * seconds and steps < 10 ** 6:
+            steps *= 2
+            t = self.run(steps)
+        return max(1, int(steps * seconds / max(t, 1e-9)))
+
+    def describe(self, steps, seconds):
+        return (f"{self.cx}x{self.cy} crop (bottom rows) of the same workload, {steps} steps, "
+                f"FP64, OpenMP over rows, {seconds:.1f} s")
+
+
+def cpu_baseline(w, target_s, cores):
+    """Time the FP64 oracle on a crop of the workload (bounded CPU time)."""
+    s = OracleSample(w, cores)
+    steps = s.steps_for(target_s)
+    t = s.run(steps)
+    return {"value": s.cx * s.cy * steps / t / 1e6, "unit": "MLUPS", "cores": cores,
+            "kind": "oracle", "sample": s.describe(steps, t)}
+
+
+# ----------------------------------------------------------------- arms
+
+def run_reference(args, rank, world):
+    """The oracle as it stands, timed on the host cores; each of the W + K
+    steps is a bounded sample (a fixed number of oracle time steps on the
+    crop) so that the whole run stays within about two minutes."""
+    if rank != 0:
+        return None
+    cores = os.cpu_count() or 1
+    s = OracleSample(workload(args.nx, args.ny), cores)
+    per_step_s = max(0.05, min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup)))
+    n = s.steps_for(per_step_s)
+    for _ in range(args.warmup):
+        s.run(n)
+    times = [s.run(n) for _ in range(args.steps)]
+    total = sum(times)
+    v = s.cx * s.cy * n * args.steps / total / 1e6
+    return {"impl": "reference", "metric": "MLUPS", "value": round(v, 3), "unit": "MLUPS",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(total / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args.nx, args.ny), "nx": args.nx, "ny": args.ny,
+                       "parallelism": "host cores", "sample_steps_per_step": n,
+                       "l2": "not applicable (CPU oracle)"},
+            "cpu_baseline": {"value": round(v, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                             "sample": s.describe(n * args.steps, total)},
+            "e2e": {"value": round(v, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_0708_4182_gb300 import lbm
+
+    torch.cuda.set_device(local_rank)
+    w = workload(args.nx, args.ny)
+    n_nodes = w.nx * w.ny
+    n_fluid = int((w.mask == 0).sum())
+    params = dict(w.params, obs_every=args.obs_every, tile_rows=args.tile_rows)
+    stream = torch.cuda.Stream()
+    lat = lbm.Lattice(w.nx, w.ny, stream=stream, **params)
+    lat.set_geometry(w.mask)
+    lat.set_rho_u(w.rho)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    lat.step(args.warmup)
+    barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.step(args.steps)
+    e1.record(stream)
+    barrier()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    obs = lat.obs_latest()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    mlups = world * n_nodes * args.steps / (ms * 1e-3) / 1e6
+    # one fused step kernel per step, plus one finalize kernel per observed step
+    launches = args.steps + sum(1 for t in range(args.warmup, args.warmup + args.steps)
+                                if args.obs_every and t % args.obs_every == 0)
+
+    # roofline of the dominant kernel (the fused step): algorithmic bytes / step time
+    per_launch_bytes = BYTES_PER_NODE_FP32 * n_fluid
+    achieved = per_launch_bytes / (ms_step * 1e-3) / 1e9
+    peak, peak_kind = measured_peak_hbm()
+    prof = traffic_from_profile()
+    traffic = None
+    if prof and prof.get("nx") and prof.get("kernel_version") == KERNEL_VERSION:
+        traffic = prof["dram_bytes_per_node"] * n_nodes
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic,
+            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+            "bytes_per_node": BYTES_PER_NODE_FP32, "fluid_nodes": n_fluid}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, w, params, lbm, stream, world)
+
+    line = {"metric": "MLUPS", "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": workload_name(w.nx, w.ny), "nx": w.nx, "ny": w.ny,
+                       "fluid_nodes": n_fluid, "obs_every": args.obs_every,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (2 x 2.4 GB population buffers)",
+                       "fluid_mlups": round(world * n_fluid * args.steps / (ms * 1e-3) / 1e6, 1)},
+            "roofline": roof,
+            "clocks": ck,
+            "gpu_launches": launches,
+            "final_obs": {k: obs[k] for k in ("step", "mass", "flux_Q", "max_u", "nonfinite")}}
+    if e2e:
+        line["e2e"] = e2e
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds, os.cpu_count() or 1)
+    return line
+
+
+KERNEL_VERSION = "step-v1"
+
+
+def run_e2e(args, w, params, lbm, stream, world):
+    import torch
+    import torch.distributed as dist
+    p = dict(params, obs_every=1)
+    rho_u = np.stack([w.rho, np.zeros_like(w.rho), np.zeros_like(w.rho)])
+    mask = np.ascontiguousarray(w.mask)
+    rho_u_pinned = torch.from_numpy(rho_u).pin_memory()
+    mask_pinned = torch.from_numpy(mask).pin_memory()
+    lat = lbm.Lattice(w.nx, w.ny, stream=stream, **p)
+    steps = args.steps
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    lbm.lbm_set_geometry(lat.ctx, mask_pinned.data_ptr(), False)
+    lbm.lbm_set_field(lat.ctx, lbm.LBM_RHO_U, rho_u_pinned.data_ptr(), False)
+    for _ in range(steps):
+        lbm.lbm_step(lat.ctx, 1)
+        lbm.lbm_obs_latest(lat.ctx)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([dt], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
+    lat.close()
+    return {"value": round(world * w.nx * w.ny * steps / dt / 1e6, 1), "unit": "MLUPS",
+            "h2d_bytes_per_step": int((rho_u.nbytes + mask.nbytes) / steps),
+            "d2h_bytes_per_step": 64,
+            "what": "host mask + FP64 (rho,u) upload, then per step lbm_step + fused observables read-back"}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    line = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

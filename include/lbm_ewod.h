@@ -1,0 +1,175 @@
+/*
+ * lbm_ewod.h -- C ABI of the GB300 D2Q9 Shan-Chen electrowetting library.
+ *
+ * The library advances the lattice Boltzmann model of Li, Li, Chen & Fang,
+ * "Lattice Boltzmann simulation of electrowetting-on-dielectric in a
+ * rough-wall channel" (arXiv:0708.4182) on one GPU. One time step is one
+ * fused CUDA kernel launch that performs, for every fluid node x:
+ *
+ *   streaming      f_a(x, t) = f*_a(x - e_a, t-1), periodic in x and y,
+ *                  half-way bounce-back where x - e_a is solid  (left side of Eq. 1)
+ *   moments        rho = sum_a f_a,  rho u = sum_a f_a e_a      (Eq. 2)
+ *   pseudopotential psi = rho0 (1 - exp(-rho/rho0))              (text after Eq. 4)
+ *   forces         F_sigma = -psi(x) sum_a G_a psi(x+e_a) e_a    (Eq. 5)
+ *                  F_w     = -psi(x) sum_a W_a S(x+e_a) e_a      (Eq. 6)
+ *                  f n on conductive (rho >= rho_c) fluid nodes of the
+ *                  single layer next to a wall                  (Eq. 9 and the
+ *                                                                 critical-density paragraph)
+ *                  rho * body force (channel runs)
+ *   velocity shift rho u' = rho u + tau (F_sigma + F_w + f + F_b) (Eq. 10)
+ *   BGK collision  f*_a = f_a - (f_a - f_a^eq(rho, u'))/tau     (Eq. 1, Eq. 3)
+ *
+ * Readings of points the paper leaves open (see the parameter comments):
+ * Green-function magnitudes (lbm_params.green), psi = 0 on solid nodes in
+ * Eq. 5, the electric force as f per solid axis face of a conductive
+ * wall-layer node, the body force as rho * (body_fx, body_fy), half-way
+ * bounce-back walls, and observables with u = (sum_a f_a e_a + F/2)/rho.
+ *
+ * Conventions
+ *  - Directions in the paper's order: e0 = (0,0); e1..e4 = (1,0), (0,1),
+ *    (-1,0), (0,-1); e5..e8 = (1,1), (-1,1), (-1,-1), (1,-1).
+ *  - Field arrays crossing the ABI are row-major, x fastest, dense (no
+ *    padding): populations as double[9][ny][nx], (rho, ux, uy) as
+ *    double[3][ny][nx], the solid mask as uint8_t[ny][nx] (1 = solid).
+ *  - "on_device" = 1 means the pointer is CUDA device memory readable on
+ *    the context's stream; 0 means ordinary host memory. All inputs are
+ *    copied: the caller keeps ownership of every buffer it passes.
+ *  - Nothing is thrown across the ABI. Every call returns an lbm_status;
+ *    lbm_last_error() gives a message for the last failure on a context.
+ *  - Work is enqueued on the context's CUDA stream. lbm_step returns as
+ *    soon as the launches are enqueued; calls that hand data back to the
+ *    host synchronise that stream.
+ *  - A context is not thread-safe; use one context per thread.
+ */
+#ifndef LBM_EWOD_H
+#define LBM_EWOD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx; /* opaque; one per simulation domain */
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,   /* bad argument: null pointer, size, parameter range */
+    LBM_ENOMEM = 2,   /* workspace too small, or host allocation failed */
+    LBM_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed */
+    LBM_ENAN = 4,     /* observables found non-finite density or velocity */
+    LBM_ETIMEOUT = 5, /* a bounded device-side wait gave up */
+    LBM_ESTATE = 6    /* call out of order (e.g. step before geometry and field) */
+} lbm_status;
+
+/* Green-function magnitudes for Eq. 4-6. LBM_GREEN_MC (the default) uses
+ * Martys & Chen's convention, G on axis links (|e| = 1) and G/2 on diagonal
+ * links (|e| = sqrt 2), for both G_a and W_a; with the paper's G = -0.52 this
+ * gives liquid/vapor densities 2.805/0.0631 around rho_c = 1 and runs stably
+ * at the paper's tau = 0.9. LBM_GREEN_PRINTED uses the weights as printed with
+ * Eq. 4 (2G axis, G diagonal), which diverges at G = -0.52. */
+enum { LBM_GREEN_MC = 0, LBM_GREEN_PRINTED = 1 };
+
+/* Population storage in device memory. Arithmetic is always FP32. */
+enum { LBM_FP32 = 0 };
+
+/* Field selectors for lbm_set_field / lbm_get_field. */
+enum { LBM_RHO_U = 0, LBM_POPS = 1 };
+
+typedef struct {
+    int32_t nx, ny;    /* lattice size; x and y are periodic, walls come
+                          from the solid mask */
+    double tau;        /* BGK relaxation time (Eq. 1), > 0.5 */
+    double G;          /* fluid-fluid strength (calligraphic G, Eq. 4); paper -0.52 */
+    double G_wall;     /* fluid-wall strength w (Eq. 6); paper -0.14 */
+    double rho0;       /* psi constant; paper 1.0 */
+    double rho_c;      /* critical density: rho >= rho_c is conductive; paper 1.0 */
+    double f_elec;     /* electric force f per wall-layer node (Eq. 9), >= 0 */
+    double body_fx;    /* body-force acceleration; the paper drives its */
+    double body_fy;    /*   channels with a rightward f_b                */
+    int32_t green;     /* LBM_GREEN_MC or LBM_GREEN_PRINTED */
+    int32_t storage;   /* LBM_FP32 */
+    int32_t obs_every; /* K > 0: every step whose index t is a multiple of K
+                          also reduces the observables of state t, fused into
+                          the step kernel (read with lbm_obs_latest); 0: off */
+    int32_t tile_rows; /* rows per CTA of the step kernel (4..256), 0 = auto */
+} lbm_params;
+
+typedef struct {
+    int64_t step;      /* time index t of the state these values describe */
+    double mass;       /* sum of rho over fluid nodes */
+    double flux_Q;     /* Eq. 11: (1/nx) * sum over fluid nodes of u_x */
+    double mom_x;      /* sum of rho u over fluid nodes, u = (sum f e + F/2)/rho */
+    double mom_y;
+    double max_u;      /* max |u| over fluid nodes */
+    double min_rho;    /* min rho over fluid nodes */
+    int64_t nonfinite; /* fluid nodes whose rho or u is NaN/Inf (not in the sums) */
+} lbm_obs;
+
+/* Bytes of device workspace a context with these parameters needs (0 if the
+ * parameters are invalid). The caller allocates it (e.g. as a torch tensor). */
+size_t lbm_workspace_bytes(const lbm_params *params);
+
+/* Create a context. d_workspace: device memory of at least
+ * lbm_workspace_bytes(params) bytes, 256-byte aligned, owned by the caller
+ * and kept alive until lbm_destroy. cuda_stream: the cudaStream_t all work is
+ * enqueued on (NULL = legacy default stream). Errors: LBM_EINVAL for invalid
+ * parameters or pointers, LBM_ENOMEM if bytes is too small. On success *out
+ * receives the context; on failure *out is NULL. */
+lbm_status lbm_create(const lbm_params *params, void *d_workspace, size_t bytes,
+                      void *cuda_stream, lbm_ctx **out);
+
+/* Set the solid mask S of Eq. 6 (uint8_t[ny][nx], nonzero = solid). Resets
+ * the time index to 0 and invalidates the populations: lbm_set_field must
+ * follow before lbm_step. */
+lbm_status lbm_set_geometry(lbm_ctx *ctx, const uint8_t *solid, int on_device);
+
+/* Set the state at the current time index.
+ * LBM_RHO_U: data = double[3][ny][nx] (rho, ux, uy); every fluid node gets
+ *            f_a = f_a^eq(rho, u) of Eq. 3. Values on solid nodes are ignored.
+ * LBM_POPS:  data = double[9][ny][nx], the populations f_a(x, t) after
+ *            streaming (the f of Eq. 2). Values on solid nodes are ignored.
+ * Populations are rounded to the storage type. Needs lbm_set_geometry first
+ * (LBM_ESTATE otherwise). */
+lbm_status lbm_set_field(lbm_ctx *ctx, int which, const double *data, int on_device);
+
+/* Read the current state into out (layouts as for lbm_set_field).
+ * LBM_RHO_U: rho and the velocity u = (sum_a f_a e_a + F/2)/rho, 0 on solids.
+ * LBM_POPS:  post-streaming populations f_a(x, t), 0 on solids.
+ * Synchronises the context's stream when out is host memory. */
+lbm_status lbm_get_field(lbm_ctx *ctx, int which, double *out, int on_device);
+
+/* Advance nsteps >= 0 time steps (asynchronous). LBM_ESTATE before geometry
+ * and field are set. */
+lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps);
+
+/* Observables of the current state (Eq. 11 and mass/momentum bookkeeping),
+ * computed by an extra read-only pass; synchronises the stream. Returns
+ * LBM_ENAN (with *out filled) if any fluid node is non-finite. */
+lbm_status lbm_observables(lbm_ctx *ctx, lbm_obs *out);
+
+/* The most recent observables fused into lbm_step (params.obs_every > 0):
+ * those of the last state t < current time with t % obs_every == 0.
+ * Synchronises the stream. LBM_ESTATE if none has been recorded yet;
+ * LBM_ENAN as for lbm_observables. */
+lbm_status lbm_obs_latest(lbm_ctx *ctx, lbm_obs *out);
+
+/* Current time index (steps taken since the last lbm_set_geometry). */
+int64_t lbm_time(const lbm_ctx *ctx);
+
+/* Message for the last error on ctx ("" if none); valid until the next call. */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* Static name of a status code. */
+const char *lbm_status_string(int status);
+
+/* Destroy a context. Frees only what the library allocated (host-side
+ * bookkeeping); the caller's workspace is untouched. NULL is a no-op. */
+void lbm_destroy(lbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_EWOD_H */

@@ -1,0 +1,600 @@
+// lbm_ewod.cu -- C ABI (include/lbm_ewod.h) and the auxiliary kernels of the
+// GB300 D2Q9 Shan-Chen electrowetting library. The time step itself is the
+// fused kernel in lbm_step.cuh.
+//
+// Device workspace (caller-owned, carved here, every region 256-byte aligned):
+//   A, B      two population buffers, FP32 planes [9][ny][pitch] (ping-pong)
+//   mask      uint8 [ny][nx] copy of the solid mask (used by set/get only)
+//   partials  kPartialStride doubles per CTA of the step grid (observables)
+//   ring      kRing lbm_obs records written by the fused observables, plus
+//             one scratch record for lbm_observables
+//   staging   bounded buffer for host <-> device transfers of FP64 populations
+#include "lbm_ewod.h"
+#include "lbm_step.cuh"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+namespace lbm {
+namespace {
+
+constexpr int kRing = 64;
+constexpr size_t kStagingMax = size_t(16) << 20;
+constexpr int kAuxThreads = 256;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int pitch_of(int nx) { return (nx + 31) / 32 * 32; }
+
+struct Layout {
+    size_t off_a, off_b, off_mask, off_partials, off_ring, off_staging, total;
+    size_t pops_bytes, staging_bytes;
+    int max_ctas;
+};
+
+bool params_valid(const lbm_params* p, const char** why)
+{
+    if (!p) { *why = "params is NULL"; return false; }
+    if (p->nx < 1 || p->ny < 1) { *why = "nx and ny must be >= 1"; return false; }
+    if (!(p->tau > 0.5) || !(p->tau < 1e6)) { *why = "tau must be > 0.5"; return false; }
+    if (!(p->rho0 > 0.0)) { *why = "rho0 must be > 0"; return false; }
+    if (p->green != LBM_GREEN_MC && p->green != LBM_GREEN_PRINTED) { *why = "unknown green convention"; return false; }
+    if (p->storage != LBM_FP32) { *why = "unsupported storage"; return false; }
+    if (p->obs_every < 0) { *why = "obs_every must be >= 0"; return false; }
+    if (p->tile_rows != 0 && (p->tile_rows < 4 || p->tile_rows > 256)) { *why = "tile_rows must be 0 or in 4..256"; return false; }
+    if ((p->ny + 3) / 4 > 65535) { *why = "ny too large for the step grid (ny <= 262140)"; return false; }
+    const double plane = double(p->ny) * pitch_of(p->nx);
+    if (9.0 * plane + 2.0 * pitch_of(p->nx) > 2147483647.0) { *why = "domain too large (9*ny*pitch must fit in int32)"; return false; }
+    if (!std::isfinite(p->G) || !std::isfinite(p->G_wall) || !std::isfinite(p->rho_c) ||
+        !std::isfinite(p->f_elec) || !std::isfinite(p->body_fx) || !std::isfinite(p->body_fy)) {
+        *why = "non-finite model parameter"; return false;
+    }
+    return true;
+}
+
+int ctas_x(int nx) { return (nx + kInner - 1) / kInner; }
+
+Layout layout_of(const lbm_params* p)
+{
+    Layout L{};
+    const int pitch = pitch_of(p->nx);
+    L.pops_bytes = size_t(9) * p->ny * pitch * sizeof(float);
+    L.max_ctas = ctas_x(p->nx) * ((p->ny + 3) / 4);
+    size_t o = 0;
+    L.off_a = o; o = align_up(o + L.pops_bytes, 256);
+    L.off_b = o; o = align_up(o + L.pops_bytes, 256);
+    L.off_mask = o; o = align_up(o + size_t(p->nx) * p->ny, 256);
+    L.off_partials = o; o = align_up(o + size_t(L.max_ctas) * kPartialStride * sizeof(double), 256);
+    L.off_ring = o; o = align_up(o + (kRing + 1) * sizeof(lbm_obs), 256);
+    const size_t full = size_t(9) * p->nx * p->ny * sizeof(double);
+    L.staging_bytes = full < kStagingMax ? full : kStagingMax;
+    if (L.staging_bytes < size_t(9) * p->nx * sizeof(double)) L.staging_bytes = size_t(9) * p->nx * sizeof(double);
+    L.off_staging = o; o = align_up(o + L.staging_bytes, 256);
+    L.total = o;
+    return L;
+}
+
+int auto_tile_rows(int nx, int ny, int sm_count)
+{
+    // largest segment height whose grid still fills every SM a few times over
+    const int target = 4 * sm_count;
+    int rows = 64;
+    while (rows > 4 && ctas_x(nx) * ((ny + rows - 1) / rows) < target) rows >>= 1;
+    return rows;
+}
+
+// ---------------------------------------------------------------------------
+// auxiliary kernels (set-up and read-back; not on the per-step path)
+
+__constant__ int kEx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+__constant__ int kEy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+__constant__ int kOpp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+__constant__ double kW[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                             1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+
+__device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// Write the solid sentinel into every plane of both buffers at solid nodes
+// and zero at fluid nodes (pitch padding is left untouched).
+__global__ void geometry_kernel(const uint8_t* __restrict__ mask, float* A,
+                                float* B, Geom g)
+{
+    const long long n = (long long)g.nx * g.ny;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int y = int(i / g.nx), x = int(i % g.nx);
+        const float v = mask[i] ? __uint_as_float(kSolidBits) : 0.f;
+        const int o = y * g.pitch + x;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            A[a * g.plane + o] = v;
+            B[a * g.plane + o] = v;
+        }
+    }
+}
+
+__device__ __forceinline__ double feq_d(int a, double rho, double ux, double uy)
+{
+    const double eu = kEx[a] * ux + kEy[a] * uy;
+    return kW[a] * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * (ux * ux + uy * uy));
+}
+
+// Initial state from (rho, ux, uy): the post-streaming populations are
+// f_a = f_a^eq (Eq. 3); stored as the post-collision f* that the next pull
+// turns back into them: f*_a(x) = f_a(x + e_a) if x + e_a is fluid, else
+// f_opp(a)(x) (the population that bounce-back will return to x).
+__global__ void rho_u_to_fstar_kernel(const double* __restrict__ ru, const uint8_t* __restrict__ mask,
+                                      float* __restrict__ out, Geom g)
+{
+    const long long n = (long long)g.nx * g.ny;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (mask[i]) continue;
+        const int y = int(i / g.nx), x = int(i % g.nx);
+        const int o = y * g.pitch + x;
+        for (int a = 0; a < 9; ++a) {
+            const int xn = wrapi(x + kEx[a], g.nx), yn = wrapi(y + kEy[a], g.ny);
+            const long long j = (long long)yn * g.nx + xn;
+            double v;
+            if (mask[j])
+                v = feq_d(kOpp[a], ru[i], ru[n + i], ru[2 * n + i]);
+            else
+                v = feq_d(a, ru[j], ru[n + j], ru[2 * n + j]);
+            out[a * g.plane + o] = float(v);
+        }
+    }
+}
+
+// Rows [r0, r0 + rows) of dense FP64 populations laid out [9][rows][nx]
+// -> FP32 post-streaming planes of buffer `f` (pitch layout).
+__global__ void pops_in_kernel(const double* __restrict__ src, float* __restrict__ f, Geom g,
+                               int r0, int rows)
+{
+    const long long n = 9LL * rows * g.nx;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int a = int(i / ((long long)rows * g.nx));
+        const long long rem = i % ((long long)rows * g.nx);
+        const int y = r0 + int(rem / g.nx), x = int(rem % g.nx);
+        f[a * g.plane + y * g.pitch + x] = float(src[i]);
+    }
+}
+
+// Post-streaming f (buffer `f`) -> post-collision f* (buffer `out`), the
+// inverse of the pull: f*_a(x) = f_a(x + e_a) or, next to a wall, f_opp(a)(x).
+__global__ void unstream_kernel(const float* __restrict__ f, const uint8_t* __restrict__ mask,
+                                float* __restrict__ out, Geom g)
+{
+    const long long n = (long long)g.nx * g.ny;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (mask[i]) continue;
+        const int y = int(i / g.nx), x = int(i % g.nx);
+        for (int a = 0; a < 9; ++a) {
+            const int xn = wrapi(x + kEx[a], g.nx), yn = wrapi(y + kEy[a], g.ny);
+            float v;
+            if (mask[(long long)yn * g.nx + xn])
+                v = f[kOpp[a] * g.plane + y * g.pitch + x];
+            else
+                v = f[a * g.plane + yn * g.pitch + xn];
+            out[a * g.plane + y * g.pitch + x] = v;
+        }
+    }
+}
+
+// Post-streaming populations of rows [r0, r0 + rows) pulled from the f*
+// buffer, written as dense FP64 [9][rows][nx] (0 on solid nodes).
+__global__ void pops_out_kernel(const float* __restrict__ fs, const uint8_t* __restrict__ mask,
+                                double* __restrict__ dst, Geom g, int r0, int rows)
+{
+    const long long n = (long long)rows * g.nx;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int y = r0 + int(i / g.nx), x = int(i % g.nx);
+        const bool solid = mask[(long long)y * g.nx + x] != 0;
+        for (int a = 0; a < 9; ++a) {
+            double v = 0.0;
+            if (!solid) {
+                const int xs = wrapi(x - kEx[a], g.nx), ys = wrapi(y - kEy[a], g.ny);
+                if (mask[(long long)ys * g.nx + xs])
+                    v = fs[kOpp[a] * g.plane + y * g.pitch + x];
+                else
+                    v = fs[a * g.plane + ys * g.pitch + xs];
+            }
+            dst[a * n + i] = v;
+        }
+    }
+}
+
+// Sum the per-CTA partials in a fixed order and write one lbm_obs record.
+__global__ void finalize_obs_kernel(const double* __restrict__ partials, int nctas, double inv_nx,
+                                    long long step, lbm_obs* __restrict__ rec)
+{
+    __shared__ double s[4][kAuxThreads];
+    __shared__ double mx[kAuxThreads], mn[kAuxThreads], bd[kAuxThreads];
+    const int t = threadIdx.x;
+    double a[4] = {0, 0, 0, 0}, um = 0.0, rm = INFINITY, b = 0.0;
+    for (int c = t; c < nctas; c += kAuxThreads) {
+        const double* q = partials + (size_t)c * kPartialStride;
+        for (int k = 0; k < 4; ++k) a[k] += q[k];
+        um = fmax(um, q[4]);
+        rm = fmin(rm, q[5]);
+        b += q[6];
+    }
+    for (int k = 0; k < 4; ++k) s[k][t] = a[k];
+    mx[t] = um;
+    mn[t] = rm;
+    bd[t] = b;
+    __syncthreads();
+    for (int h = kAuxThreads / 2; h > 0; h >>= 1) {
+        if (t < h) {
+            for (int k = 0; k < 4; ++k) s[k][t] += s[k][t + h];
+            mx[t] = fmax(mx[t], mx[t + h]);
+            mn[t] = fmin(mn[t], mn[t + h]);
+            bd[t] += bd[t + h];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        rec->step = step;
+        rec->mass = s[0][0];
+        rec->flux_Q = s[1][0] * inv_nx;
+        rec->mom_x = s[2][0];
+        rec->mom_y = s[3][0];
+        rec->max_u = sqrt(mx[0]);
+        rec->min_rho = mn[0];
+        rec->nonfinite = (long long)bd[0];
+    }
+}
+
+int aux_blocks(long long n, int sm_count)
+{
+    long long b = (n + kAuxThreads - 1) / kAuxThreads;
+    const long long cap = 32LL * sm_count;
+    return int(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+}  // namespace
+}  // namespace lbm
+
+using namespace lbm;
+
+struct lbm_ctx {
+    lbm_params prm{};
+    Layout L{};
+    Geom g{};
+    Phys ph{};
+    cudaStream_t stream = nullptr;
+    unsigned char* ws = nullptr;
+    float* cur = nullptr;  // f* of the current state
+    float* nxt = nullptr;
+    uint8_t* mask = nullptr;
+    double* partials = nullptr;
+    lbm_obs* ring = nullptr;
+    double* staging = nullptr;
+    int sm_count = 0;
+    dim3 grid;
+    int64_t t = 0;
+    int64_t last_obs_t = -1;
+    int ring_count = 0;
+    bool has_geometry = false, has_field = false;
+    char err[512] = {0};
+};
+
+namespace {
+
+lbm_status fail(lbm_ctx* c, lbm_status s, const char* fmt, ...)
+{
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+lbm_status check_cuda(lbm_ctx* c, cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) return LBM_OK;
+    return fail(c, LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+lbm_status check_launch(lbm_ctx* c, const char* what) { return check_cuda(c, cudaGetLastError(), what); }
+
+Phys make_phys(const lbm_params& p)
+{
+    Phys h{};
+    h.tau = float(p.tau);
+    h.inv_tau = float(1.0 / p.tau);
+    h.rho0 = float(p.rho0);
+    h.inv_rho0 = float(1.0 / p.rho0);
+    h.rho_c = float(p.rho_c);
+    h.f_elec = float(p.f_elec);
+    h.bfx = float(p.body_fx);
+    h.bfy = float(p.body_fy);
+    // Green-function magnitudes on axis (|e| = 1) and diagonal (|e| = sqrt 2) links
+    const double ka = p.green == LBM_GREEN_PRINTED ? 2.0 : 1.0;
+    const double kd = p.green == LBM_GREEN_PRINTED ? 1.0 : 0.5;
+    h.g_axis = float(ka * p.G);
+    h.g_diag = float(kd * p.G);
+    h.w_axis = float(ka * p.G_wall);
+    h.w_diag = float(kd * p.G_wall);
+    return h;
+}
+
+template <int MODE>
+lbm_status launch_step(lbm_ctx* c, const float* fin, float* fout, double* fields)
+{
+    step_kernel<MODE><<<c->grid, kThreads, 0, c->stream>>>(fin, fout, c->g, c->ph, c->partials, fields);
+    return check_launch(c, "step kernel launch");
+}
+
+lbm_status finalize(lbm_ctx* c, int64_t step, lbm_obs* rec)
+{
+    finalize_obs_kernel<<<1, kAuxThreads, 0, c->stream>>>(c->partials, int(c->grid.x * c->grid.y),
+                                                          1.0 / c->prm.nx, (long long)step, rec);
+    return check_launch(c, "observables finalize launch");
+}
+
+lbm_status ready(lbm_ctx* c)
+{
+    if (!c) return LBM_EINVAL;
+    if (!c->has_geometry || !c->has_field)
+        return fail(c, LBM_ESTATE, "set the geometry and a field before this call");
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lbm_workspace_bytes(const lbm_params* p)
+{
+    const char* why;
+    if (!params_valid(p, &why)) return 0;
+    return layout_of(p).total;
+}
+
+lbm_status lbm_create(const lbm_params* p, void* d_workspace, size_t bytes, void* cuda_stream,
+                      lbm_ctx** out)
+{
+    if (!out) return LBM_EINVAL;
+    *out = nullptr;
+    const char* why = "";
+    if (!params_valid(p, &why)) return LBM_EINVAL;
+    if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) & 255u)) return LBM_EINVAL;
+    Layout L = layout_of(p);
+    if (bytes < L.total) return LBM_ENOMEM;
+    lbm_ctx* c = new (std::nothrow) lbm_ctx;
+    if (!c) return LBM_ENOMEM;
+    c->prm = *p;
+    c->L = L;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->ws = static_cast<unsigned char*>(d_workspace);
+    c->cur = reinterpret_cast<float*>(c->ws + L.off_a);
+    c->nxt = reinterpret_cast<float*>(c->ws + L.off_b);
+    c->mask = c->ws + L.off_mask;
+    c->partials = reinterpret_cast<double*>(c->ws + L.off_partials);
+    c->ring = reinterpret_cast<lbm_obs*>(c->ws + L.off_ring);
+    c->staging = reinterpret_cast<double*>(c->ws + L.off_staging);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return LBM_ECUDA;
+    }
+    c->g.nx = p->nx;
+    c->g.ny = p->ny;
+    c->g.pitch = pitch_of(p->nx);
+    c->g.plane = p->ny * c->g.pitch;
+    c->g.tile_rows = p->tile_rows ? p->tile_rows : auto_tile_rows(p->nx, p->ny, c->sm_count);
+    c->grid = dim3(ctas_x(p->nx), (p->ny + c->g.tile_rows - 1) / c->g.tile_rows);
+    c->ph = make_phys(*p);
+    *out = c;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_geometry(lbm_ctx* c, const uint8_t* solid, int on_device)
+{
+    if (!c) return LBM_EINVAL;
+    if (!solid) return fail(c, LBM_EINVAL, "solid mask is NULL");
+    const size_t n = size_t(c->g.nx) * c->g.ny;
+    lbm_status s = check_cuda(c, cudaMemcpyAsync(c->mask, solid, n,
+                                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                                 c->stream), "mask upload");
+    if (s) return s;
+    geometry_kernel<<<aux_blocks(n, c->sm_count), kAuxThreads, 0, c->stream>>>(c->mask, c->cur, c->nxt, c->g);
+    if ((s = check_launch(c, "geometry kernel launch"))) return s;
+    c->has_geometry = true;
+    c->has_field = false;
+    c->t = 0;
+    c->last_obs_t = -1;
+    c->ring_count = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_field(lbm_ctx* c, int which, const double* data, int on_device)
+{
+    if (!c) return LBM_EINVAL;
+    if (!data) return fail(c, LBM_EINVAL, "field data is NULL");
+    if (!c->has_geometry) return fail(c, LBM_ESTATE, "lbm_set_geometry must come before lbm_set_field");
+    const size_t n = size_t(c->g.nx) * c->g.ny;
+    lbm_status s;
+    if (which == LBM_RHO_U) {
+        const double* src = data;
+        if (!on_device) {
+            // (rho, ux, uy) in FP64 fits in the spare population buffer
+            double* tmp = reinterpret_cast<double*>(c->nxt);
+            if ((s = check_cuda(c, cudaMemcpyAsync(tmp, data, 3 * n * sizeof(double), cudaMemcpyHostToDevice,
+                                                   c->stream), "field upload")))
+                return s;
+            src = tmp;
+        }
+        rho_u_to_fstar_kernel<<<aux_blocks(n, c->sm_count), kAuxThreads, 0, c->stream>>>(src, c->mask, c->cur, c->g);
+        if ((s = check_launch(c, "field kernel launch"))) return s;
+        if (!on_device) {
+            // restore the sentinels the FP64 scratch overwrote in the spare buffer
+            geometry_kernel<<<aux_blocks(n, c->sm_count), kAuxThreads, 0, c->stream>>>(c->mask, c->nxt, c->nxt, c->g);
+            if ((s = check_launch(c, "geometry kernel launch"))) return s;
+        }
+    } else if (which == LBM_POPS) {
+        const int nx = c->g.nx, ny = c->g.ny;
+        const int rows_per = on_device ? ny : int(c->L.staging_bytes / (9 * size_t(nx) * sizeof(double)));
+        for (int r0 = 0; r0 < ny; r0 += rows_per) {
+            const int rows = (r0 + rows_per <= ny) ? rows_per : ny - r0;
+            const double* src = data;
+            if (!on_device) {
+                for (int a = 0; a < 9; ++a) {
+                    if ((s = check_cuda(c, cudaMemcpyAsync(c->staging + size_t(a) * rows * nx,
+                                                           data + size_t(a) * n + size_t(r0) * nx,
+                                                           size_t(rows) * nx * sizeof(double),
+                                                           cudaMemcpyHostToDevice, c->stream),
+                                        "population upload")))
+                        return s;
+                }
+                src = c->staging;
+            } else if (rows != ny) {
+                return fail(c, LBM_EINVAL, "internal: device populations are converted in one pass");
+            }
+            pops_in_kernel<<<aux_blocks(9LL * rows * nx, c->sm_count), kAuxThreads, 0, c->stream>>>(src, c->nxt, c->g, r0, rows);
+            if ((s = check_launch(c, "population kernel launch"))) return s;
+            if (!on_device) {
+                // the staging buffer is reused by the next chunk
+                if ((s = check_cuda(c, cudaStreamSynchronize(c->stream), "population upload sync"))) return s;
+            }
+        }
+        unstream_kernel<<<aux_blocks(n, c->sm_count), kAuxThreads, 0, c->stream>>>(c->nxt, c->mask, c->cur, c->g);
+        if ((s = check_launch(c, "unstream kernel launch"))) return s;
+        geometry_kernel<<<aux_blocks(n, c->sm_count), kAuxThreads, 0, c->stream>>>(c->mask, c->nxt, c->nxt, c->g);
+        if ((s = check_launch(c, "geometry kernel launch"))) return s;
+    } else {
+        return fail(c, LBM_EINVAL, "unknown field selector %d", which);
+    }
+    c->has_field = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_field(lbm_ctx* c, int which, double* out, int on_device)
+{
+    lbm_status s = ready(c);
+    if (s) return s;
+    if (!out) return fail(c, LBM_EINVAL, "output is NULL");
+    const size_t n = size_t(c->g.nx) * c->g.ny;
+    if (which == LBM_RHO_U) {
+        double* dst = on_device ? out : reinterpret_cast<double*>(c->nxt);
+        if ((s = launch_step<kFields>(c, c->cur, nullptr, dst))) return s;
+        if (!on_device) {
+            if ((s = check_cuda(c, cudaMemcpyAsync(out, dst, 3 * n * sizeof(double), cudaMemcpyDeviceToHost,
+                                                   c->stream), "field download")))
+                return s;
+            if ((s = check_cuda(c, cudaStreamSynchronize(c->stream), "field download sync"))) return s;
+            geometry_kernel<<<aux_blocks(n, c->sm_count), kAuxThreads, 0, c->stream>>>(c->mask, c->nxt, c->nxt, c->g);
+            if ((s = check_launch(c, "geometry kernel launch"))) return s;
+        }
+        return LBM_OK;
+    }
+    if (which != LBM_POPS) return fail(c, LBM_EINVAL, "unknown field selector %d", which);
+    const int nx = c->g.nx, ny = c->g.ny;
+    if (on_device) {
+        pops_out_kernel<<<aux_blocks(n, c->sm_count), kAuxThreads, 0, c->stream>>>(c->cur, c->mask, out, c->g, 0, ny);
+        return check_launch(c, "population kernel launch");
+    }
+    const int rows_per = int(c->L.staging_bytes / (9 * size_t(nx) * sizeof(double)));
+    for (int r0 = 0; r0 < ny; r0 += rows_per) {
+        const int rows = (r0 + rows_per <= ny) ? rows_per : ny - r0;
+        pops_out_kernel<<<aux_blocks(size_t(rows) * nx, c->sm_count), kAuxThreads, 0, c->stream>>>(c->cur, c->mask, c->staging, c->g, r0, rows);
+        if ((s = check_launch(c, "population kernel launch"))) return s;
+        for (int a = 0; a < 9; ++a) {
+            if ((s = check_cuda(c, cudaMemcpyAsync(out + size_t(a) * n + size_t(r0) * nx,
+                                                   c->staging + size_t(a) * rows * nx,
+                                                   size_t(rows) * nx * sizeof(double), cudaMemcpyDeviceToHost,
+                                                   c->stream), "population download")))
+                return s;
+        }
+        if ((s = check_cuda(c, cudaStreamSynchronize(c->stream), "population download sync"))) return s;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* c, int64_t nsteps)
+{
+    lbm_status s = ready(c);
+    if (s) return s;
+    if (nsteps < 0) return fail(c, LBM_EINVAL, "nsteps must be >= 0");
+    const int K = c->prm.obs_every;
+    for (int64_t k = 0; k < nsteps; ++k) {
+        if (K > 0 && c->t % K == 0) {
+            if ((s = launch_step<kStepObs>(c, c->cur, c->nxt, nullptr))) return s;
+            if ((s = finalize(c, c->t, c->ring + (c->ring_count % kRing)))) return s;
+            c->last_obs_t = c->t;
+            ++c->ring_count;
+        } else {
+            if ((s = launch_step<kStep>(c, c->cur, c->nxt, nullptr))) return s;
+        }
+        float* tmp = c->cur;
+        c->cur = c->nxt;
+        c->nxt = tmp;
+        ++c->t;
+    }
+    return LBM_OK;
+}
+
+static lbm_status read_record(lbm_ctx* c, const lbm_obs* rec, lbm_obs* out)
+{
+    lbm_status s;
+    if ((s = check_cuda(c, cudaMemcpyAsync(out, rec, sizeof(lbm_obs), cudaMemcpyDeviceToHost, c->stream),
+                        "observables download")))
+        return s;
+    if ((s = check_cuda(c, cudaStreamSynchronize(c->stream), "observables sync"))) return s;
+    if (out->nonfinite > 0) return fail(c, LBM_ENAN, "%lld non-finite fluid nodes at step %lld",
+                                        (long long)out->nonfinite, (long long)out->step);
+    return LBM_OK;
+}
+
+lbm_status lbm_observables(lbm_ctx* c, lbm_obs* out)
+{
+    lbm_status s = ready(c);
+    if (s) return s;
+    if (!out) return fail(c, LBM_EINVAL, "output is NULL");
+    lbm_obs* rec = c->ring + kRing;  // scratch slot after the fused ones
+    if ((s = launch_step<kObs>(c, c->cur, nullptr, nullptr))) return s;
+    if ((s = finalize(c, c->t, rec))) return s;
+    return read_record(c, rec, out);
+}
+
+lbm_status lbm_obs_latest(lbm_ctx* c, lbm_obs* out)
+{
+    lbm_status s = ready(c);
+    if (s) return s;
+    if (!out) return fail(c, LBM_EINVAL, "output is NULL");
+    if (c->ring_count == 0) return fail(c, LBM_ESTATE, "no fused observables recorded yet (obs_every = %d)", c->prm.obs_every);
+    return read_record(c, c->ring + ((c->ring_count - 1) % kRing), out);
+}
+
+int64_t lbm_time(const lbm_ctx* c) { return c ? c->t : -1; }
+
+const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err : "null context"; }
+
+const char* lbm_status_string(int s)
+{
+    switch (s) {
+    case LBM_OK: return "LBM_OK";
+    case LBM_EINVAL: return "LBM_EINVAL";
+    case LBM_ENOMEM: return "LBM_ENOMEM";
+    case LBM_ECUDA: return "LBM_ECUDA";
+    case LBM_ENAN: return "LBM_ENAN";
+    case LBM_ETIMEOUT: return "LBM_ETIMEOUT";
+    case LBM_ESTATE: return "LBM_ESTATE";
+    default: return "unknown status";
+    }
+}
+
+void lbm_destroy(lbm_ctx* c) { delete c; }
+
+}  // extern "C"

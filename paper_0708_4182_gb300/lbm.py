@@ -1,0 +1,287 @@
+"""ctypes binding of the C ABI in include/lbm_ewod.h (same entry-point names).
+
+Marshalling only: every step of the method runs in the CUDA library. The
+binding fails loudly (``LbmUnavailable``) when the compiled library is
+missing; there is no CPU fallback. PyTorch is used for device memory (the
+workspace tensor) and for the CUDA stream the context enqueues on.
+
+Low level: ``lbm_workspace_bytes``, ``lbm_create``, ``lbm_set_geometry``,
+``lbm_set_field``, ``lbm_get_field``, ``lbm_step``, ``lbm_observables``,
+``lbm_obs_latest``, ``lbm_time``, ``lbm_last_error``, ``lbm_status_string``,
+``lbm_destroy``; each raises ``LbmError`` on a non-zero status.
+High level: ``Lattice`` owns a workspace tensor and a context.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENAN, LBM_ETIMEOUT, LBM_ESTATE = range(7)
+LBM_GREEN_MC, LBM_GREEN_PRINTED = 0, 1
+LBM_FP32 = 0
+LBM_RHO_U, LBM_POPS = 0, 1
+
+
+class LbmUnavailable(RuntimeError):
+    """The compiled CUDA library is not present or cannot be loaded."""
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{status_name(status)}: {message}")
+        self.status = status
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("tau", ctypes.c_double), ("G", ctypes.c_double), ("G_wall", ctypes.c_double),
+        ("rho0", ctypes.c_double), ("rho_c", ctypes.c_double), ("f_elec", ctypes.c_double),
+        ("body_fx", ctypes.c_double), ("body_fy", ctypes.c_double),
+        ("green", ctypes.c_int32), ("storage", ctypes.c_int32),
+        ("obs_every", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
+    ]
+
+
+class lbm_obs(ctypes.Structure):
+    _fields_ = [
+        ("step", ctypes.c_int64), ("mass", ctypes.c_double), ("flux_Q", ctypes.c_double),
+        ("mom_x", ctypes.c_double), ("mom_y", ctypes.c_double), ("max_u", ctypes.c_double),
+        ("min_rho", ctypes.c_double), ("nonfinite", ctypes.c_int64),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load():
+    """Load the compiled library (never builds it; see ``build.build``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise LbmUnavailable(f"CUDA library {path} is not built; run __graft_entry__.build()")
+        try:
+            lib = ctypes.CDLL(path)
+        except OSError as e:
+            raise LbmUnavailable(f"cannot load {path}: {e}") from e
+        vp, P, O = ctypes.c_void_p, ctypes.POINTER(lbm_params), ctypes.POINTER(lbm_obs)
+        sig = {
+            "lbm_workspace_bytes": (ctypes.c_size_t, [P]),
+            "lbm_create": (ctypes.c_int, [P, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]),
+            "lbm_set_geometry": (ctypes.c_int, [vp, vp, ctypes.c_int]),
+            "lbm_set_field": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int]),
+            "lbm_get_field": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int]),
+            "lbm_step": (ctypes.c_int, [vp, ctypes.c_int64]),
+            "lbm_observables": (ctypes.c_int, [vp, O]),
+            "lbm_obs_latest": (ctypes.c_int, [vp, O]),
+            "lbm_time": (ctypes.c_int64, [vp]),
+            "lbm_last_error": (ctypes.c_char_p, [vp]),
+            "lbm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+            "lbm_destroy": (None, [vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype, fn.argtypes = res, args
+        _lib = lib
+        return lib
+
+
+def status_name(status: int) -> str:
+    names = ["LBM_OK", "LBM_EINVAL", "LBM_ENOMEM", "LBM_ECUDA", "LBM_ENAN", "LBM_ETIMEOUT", "LBM_ESTATE"]
+    return names[status] if 0 <= status < len(names) else f"status {status}"
+
+
+def _check(ctx, status: int):
+    if status != LBM_OK:
+        msg = lbm_last_error(ctx) if ctx else ""
+        raise LbmError(status, msg)
+
+
+def make_params(nx, ny, tau=1.0, G=-0.52, G_wall=-0.14, rho0=1.0, rho_c=1.0, f_elec=0.0,
+                body_fx=0.0, body_fy=0.0, green=LBM_GREEN_MC, storage=LBM_FP32, obs_every=0,
+                tile_rows=0) -> lbm_params:
+    return lbm_params(int(nx), int(ny), float(tau), float(G), float(G_wall), float(rho0),
+                      float(rho_c), float(f_elec), float(body_fx), float(body_fy), int(green),
+                      int(storage), int(obs_every), int(tile_rows))
+
+
+# ---------------------------------------------------------------- low level
+
+def lbm_workspace_bytes(params: lbm_params) -> int:
+    return int(load().lbm_workspace_bytes(ctypes.byref(params)))
+
+
+def lbm_create(params: lbm_params, d_workspace: int, nbytes: int, cuda_stream: int):
+    ctx = ctypes.c_void_p()
+    _check(None, load().lbm_create(ctypes.byref(params), ctypes.c_void_p(d_workspace), nbytes,
+                                   ctypes.c_void_p(cuda_stream), ctypes.byref(ctx)))
+    return ctx
+
+
+def lbm_set_geometry(ctx, solid_ptr: int, on_device: bool):
+    _check(ctx, load().lbm_set_geometry(ctx, ctypes.c_void_p(solid_ptr), int(on_device)))
+
+
+def lbm_set_field(ctx, which: int, data_ptr: int, on_device: bool):
+    _check(ctx, load().lbm_set_field(ctx, which, ctypes.c_void_p(data_ptr), int(on_device)))
+
+
+def lbm_get_field(ctx, which: int, out_ptr: int, on_device: bool):
+    _check(ctx, load().lbm_get_field(ctx, which, ctypes.c_void_p(out_ptr), int(on_device)))
+
+
+def lbm_step(ctx, nsteps: int):
+    _check(ctx, load().lbm_step(ctx, int(nsteps)))
+
+
+def lbm_observables(ctx, check_finite: bool = True) -> dict:
+    o = lbm_obs()
+    st = load().lbm_observables(ctx, ctypes.byref(o))
+    if st != LBM_ENAN or check_finite:
+        _check(ctx, st)
+    return o.as_dict()
+
+
+def lbm_obs_latest(ctx, check_finite: bool = True) -> dict:
+    o = lbm_obs()
+    st = load().lbm_obs_latest(ctx, ctypes.byref(o))
+    if st != LBM_ENAN or check_finite:
+        _check(ctx, st)
+    return o.as_dict()
+
+
+def lbm_time(ctx) -> int:
+    return int(load().lbm_time(ctx))
+
+
+def lbm_last_error(ctx) -> str:
+    s = load().lbm_last_error(ctx)
+    return s.decode() if s else ""
+
+
+def lbm_status_string(status: int) -> str:
+    return load().lbm_status_string(int(status)).decode()
+
+
+def lbm_destroy(ctx):
+    if ctx:
+        load().lbm_destroy(ctx)
+
+
+# ---------------------------------------------------------------- high level
+
+def _host_ptr(a: np.ndarray, dtype) -> tuple[np.ndarray, int]:
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data
+
+
+class Lattice:
+    """One simulation domain on the current CUDA device.
+
+    The workspace is a torch uint8 tensor sized by ``lbm_workspace_bytes``;
+    all work goes to ``stream`` (default: torch's current stream). Host
+    arrays are numpy; device arrays may be torch CUDA tensors."""
+
+    def __init__(self, nx: int, ny: int, stream=None, **params):
+        import torch
+
+        self.nx, self.ny = int(nx), int(ny)
+        self.params = make_params(nx, ny, **params)
+        nbytes = lbm_workspace_bytes(self.params)
+        if nbytes == 0:
+            raise LbmError(LBM_EINVAL, f"invalid parameters {params}")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.stream.device)
+        self.ctx = lbm_create(self.params, self.workspace.data_ptr(), nbytes, self.stream.cuda_stream)
+
+    # -- inputs
+    def set_geometry(self, solid):
+        if hasattr(solid, "is_cuda") and solid.is_cuda:
+            t = solid.to(dtype=__import__("torch").uint8).contiguous()
+            lbm_set_geometry(self.ctx, t.data_ptr(), True)
+            self._keep = t
+        else:
+            a, p = _host_ptr(solid, np.uint8)
+            if a.shape != (self.ny, self.nx):
+                raise ValueError(f"mask shape {a.shape} != {(self.ny, self.nx)}")
+            lbm_set_geometry(self.ctx, p, False)
+
+    def _set(self, which, data, comps):
+        if hasattr(data, "is_cuda") and data.is_cuda:
+            t = data.to(dtype=__import__("torch").float64).contiguous()
+            if tuple(t.shape) != (comps, self.ny, self.nx):
+                raise ValueError("bad field shape")
+            lbm_set_field(self.ctx, which, t.data_ptr(), True)
+            self.stream.synchronize()
+        else:
+            a, p = _host_ptr(data, np.float64)
+            if a.shape != (comps, self.ny, self.nx):
+                raise ValueError(f"field shape {a.shape} != {(comps, self.ny, self.nx)}")
+            lbm_set_field(self.ctx, which, p, False)
+
+    def set_rho_u(self, rho, ux=0.0, uy=0.0):
+        if hasattr(rho, "is_cuda") and rho.is_cuda:
+            import torch
+            data = torch.stack([torch.broadcast_to(torch.as_tensor(v, dtype=torch.float64, device=rho.device),
+                                                   (self.ny, self.nx)) for v in (rho, ux, uy)])
+        else:
+            data = np.stack([np.broadcast_to(np.asarray(v, np.float64), (self.ny, self.nx))
+                             for v in (rho, ux, uy)])
+        self._set(LBM_RHO_U, data, 3)
+
+    def set_populations(self, f):
+        self._set(LBM_POPS, f, 9)
+
+    # -- outputs
+    def populations(self) -> np.ndarray:
+        out = np.empty((9, self.ny, self.nx))
+        lbm_get_field(self.ctx, LBM_POPS, out.ctypes.data, False)
+        return out
+
+    def fields(self):
+        out = np.empty((3, self.ny, self.nx))
+        lbm_get_field(self.ctx, LBM_RHO_U, out.ctypes.data, False)
+        return out[0], out[1], out[2]
+
+    def populations_device(self):
+        import torch
+        out = torch.empty((9, self.ny, self.nx), dtype=torch.float64, device=self.workspace.device)
+        lbm_get_field(self.ctx, LBM_POPS, out.data_ptr(), True)
+        return out
+
+    # -- time stepping
+    def step(self, n: int = 1):
+        lbm_step(self.ctx, n)
+
+    def observables(self, check_finite: bool = True) -> dict:
+        return lbm_observables(self.ctx, check_finite)
+
+    def obs_latest(self, check_finite: bool = True) -> dict:
+        return lbm_obs_latest(self.ctx, check_finite)
+
+    @property
+    def time(self) -> int:
+        return lbm_time(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

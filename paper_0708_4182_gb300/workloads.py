@@ -173,10 +173,15 @@ def droplet_128x64(f_elec: float = 0.0, radius: float = 20.0) -> Workload:
                     dict(PAPER, tau=1.0, f_elec=f_elec, body_fx=0.0, body_fy=0.0))
 
 
-def rough_channel(nx=1024, ny=128, amp=8, level=0, seed=0, fill=0.5, body_fx=1e-6) -> Workload:
-    """Rough-wall channel filled with a central electrolyte slab, driven by a
-    uniform body force; electric force at sweep ``level``."""
+def rough_channel(nx=1024, ny=128, amp=8, level=0, seed=0, fill=None, body_fx=1e-6) -> Workload:
+    """Rough-wall channel filled with electrolyte, driven by a uniform body
+    force; electric force at sweep ``level``. By default the liquid fills the
+    channel up to the crests of the tallest roughness elements and the grooves
+    between elements hold vapor, so the electrolyte touches the walls (the
+    electric force acts only on liquid next to a wall)."""
     mask = channel_mask(nx, ny, amp, seed)
+    if fill is None:
+        fill = max(0.1, 1.0 - 2.0 * (amp + 1) / (ny - 2))
     rho = slab_field(nx, ny, fill, mask=mask)
     return Workload(f"rough_channel_{nx}x{ny}", nx, ny, mask, rho,
                     dict(PAPER, tau=1.0, f_elec=f_level(level), body_fx=body_fx, body_fy=0.0))

@@ -1,0 +1,329 @@
+"""GPU (CUDA library, through the C ABI) vs the FP64 oracle.
+
+Populations are compared after up to 100 steps (the FP32 library against
+the FP64 oracle from the same seeded start):
+
+* relative 1e-6 on populations, as the relative L2 error of the field:
+      ||f_gpu - f_ref||_2 / ||f_ref||_2 <= 1e-6;
+* element by element, every node and direction:
+      |f_gpu - f_ref| <= 4e-6 * max |f_ref|
+      |f_gpu - f_ref| / max(|f_ref|, w_a rho_v) <= 1e-5.
+  The element bounds come from the arithmetic: with exact arithmetic and only
+  the FP32 storage rounding, the first measure already reaches 6.5e-7 after
+  100 steps on a rough channel (a static interface node rounds the same way
+  every step, so the errors add up rather than cancel), and the FP32
+  collision multiplies that by about 3 at high-force interface nodes.
+Every case also checks the observables (mass, flux Q of Eq. 11, momentum).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0708_4182_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+TOL_L2 = 1e-6      # relative L2 over the population field
+TOL_FIELD = 4e-6   # per element, relative to the field's maximum
+TOL_ELEM = 1e-5    # per element, relative to itself (vapor-scale floor)
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0708_4182_gb300 import lbm as L
+    L.load()
+    return L
+
+
+def pop_err(f_gpu, f_ref, mask, rho_v=wl.RHO_V):
+    """(field-relative max, per-population max, relative L2) over fluid nodes."""
+    fl = mask == 0
+    d = np.abs(f_gpu - f_ref)[:, fl]
+    r = np.abs(f_ref)[:, fl]
+    field = float(d.max() / r.max())
+    elem = float((d / np.maximum(r, W[:, None] * rho_v)).max())
+    l2 = float(np.sqrt((d ** 2).sum() / (r ** 2).sum()))
+    return field, elem, l2
+
+
+def assert_pops(f_gpu, f_ref, mask):
+    field, elem, l2 = pop_err(f_gpu, f_ref, mask)
+    assert l2 <= TOL_L2 and field <= TOL_FIELD and elem <= TOL_ELEM, (l2, field, elem)
+    assert np.all(f_gpu[:, mask == 1] == 0)
+
+
+def run_both(lbm, mask, rho, params, steps, ux=0.0, uy=0.0, **lat_kw):
+    ny, nx = mask.shape
+    p = oracle.Params(nx, ny, **params)
+    f0 = oracle.equilibrium(p, mask, rho, ux, uy)
+    f_ref = oracle.step(p, mask, f0, steps)
+    lat = lbm.Lattice(nx, ny, **params, **lat_kw)
+    lat.set_geometry(mask)
+    lat.set_rho_u(rho, ux, uy)
+    lat.step(steps)
+    return p, f_ref, lat
+
+
+def check_obs(lat, p, mask, f_ref, rel=1e-6):
+    o = lat.observables()
+    r = oracle.observables(p, mask, f_ref)
+    rho, jx, jy, t = oracle.forces(p, mask, f_ref)
+    fx, fy = t[0::2].sum(0), t[1::2].sum(0)
+    fl = mask == 0
+    assert o["nonfinite"] == 0
+    assert o["mass"] == pytest.approx(r["mass"], rel=rel)
+    # u = (j + F/2)/rho nearly cancels at interfaces (j ~ -F/2 at rest), so a
+    # node's u carries an error ~1e-6 (|j| + |F|/2)/rho: Q and P sum these
+    mx = np.abs(jx[fl]) + 0.5 * np.abs(fx[fl])
+    my = np.abs(jy[fl]) + 0.5 * np.abs(fy[fl])
+    assert abs(o["flux_Q"] - r["flux_Q"]) <= 1e-5 * (mx / rho[fl]).sum() / p.nx + 1e-12
+    assert abs(o["mom_x"] - r["mom_x"]) <= 1e-5 * mx.sum() + 1e-12
+    assert abs(o["mom_y"] - r["mom_y"]) <= 1e-5 * my.sum() + 1e-12
+    assert o["max_u"] == pytest.approx(r["max_u"], rel=1e-4)
+    assert o["min_rho"] == pytest.approx(r["min_rho"], rel=1e-5)
+    assert o["step"] == lat.time
+
+
+@pytest.mark.parametrize("f_elec", wl.DROPLET_F_LEVELS)
+def test_droplet_128x64_populations_100_steps(lbm, f_elec):
+    w = wl.droplet_128x64(f_elec)
+    p, f_ref, lat = run_both(lbm, w.mask, w.rho, w.params, 100)
+    assert_pops(lat.populations(), f_ref, w.mask)
+    check_obs(lat, p, w.mask, f_ref)
+
+
+@pytest.mark.parametrize("level", [0, 9, 15])
+def test_rough_channel_populations_100_steps(lbm, level):
+    w = wl.rough_channel(nx=300, ny=48, amp=6, level=level, seed=5, body_fx=1e-5)
+    p, f_ref, lat = run_both(lbm, w.mask, w.rho, w.params, 100)
+    assert_pops(lat.populations(), f_ref, w.mask)
+    check_obs(lat, p, w.mask, f_ref)
+
+
+def test_rough_channel_1024x128_populations(lbm):
+    """The rough-wall channel workload at its full size (1024 x 128, amp 8)."""
+    w = wl.rough_channel(level=12)
+    p, f_ref, lat = run_both(lbm, w.mask, w.rho, w.params, 100)
+    assert_pops(lat.populations(), f_ref, w.mask)
+    check_obs(lat, p, w.mask, f_ref)
+
+
+def _blob_field(nx, ny, mask, seed):
+    rng = np.random.default_rng(seed)
+    cx, cy = rng.uniform(0, nx), rng.uniform(0, ny)
+    rho = wl.droplet_field(nx, ny, [(cx, cy)], 0.3 * min(nx, ny) + 1.0, mask=mask)
+    return rho
+
+
+RAGGED = [
+    # nx, ny, walls, tile_rows : strips of 254 columns and segments of tile_rows
+    # rows with ragged ends, a single CTA, a single column, a single row
+    (5, 4, False, 0),
+    (1, 9, True, 0),
+    (37, 11, True, 4),
+    (254, 13, True, 8),
+    (255, 20, True, 0),
+    (509, 17, True, 4),
+    (600, 1, False, 0),
+    (131, 70, True, 64),
+]
+
+
+@pytest.mark.parametrize("nx,ny,walls,tile_rows", RAGGED)
+def test_ragged_and_tiny_domains(lbm, nx, ny, walls, tile_rows):
+    mask = np.zeros((ny, nx), np.uint8)
+    if walls and ny >= 3:
+        mask[0] = mask[-1] = 1
+        if nx >= 8 and ny >= 8:
+            mask[ny // 2:ny // 2 + 2, nx // 3:nx // 3 + 3] = 1  # an interior block
+    rho = _blob_field(nx, ny, mask, nx * 1000 + ny)
+    params = dict(wl.PAPER, tau=1.0, f_elec=0.2, body_fx=1e-5, body_fy=-2e-6)
+    p, f_ref, lat = run_both(lbm, mask, rho, params, 40, tile_rows=tile_rows)
+    assert_pops(lat.populations(), f_ref, mask)
+    check_obs(lat, p, mask, f_ref)
+
+
+def test_printed_green_convention_and_tau(lbm):
+    """The other Green-function convention and tau != 1 (weaker G so that the
+    printed weights are stable)."""
+    w = wl.droplet_128x64(0.15)
+    params = dict(w.params, G=-0.26, G_wall=-0.07, tau=0.95, green=oracle.GREEN_PRINTED)
+    p, f_ref, lat = run_both(lbm, w.mask, w.rho, params, 100)
+    assert_pops(lat.populations(), f_ref, w.mask)
+
+
+def test_tiling_is_bitwise_invariant_and_deterministic(lbm):
+    w = wl.rough_channel(nx=520, ny=90, amp=6, level=7, seed=3, body_fx=1e-5)
+    outs = []
+    for tr in (4, 8, 64, 4):
+        lat = lbm.Lattice(w.nx, w.ny, **w.params, tile_rows=tr)
+        lat.set_geometry(w.mask)
+        lat.set_rho_u(w.rho)
+        lat.step(30)
+        outs.append(lat.populations())
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+
+
+def test_fields_match_oracle(lbm):
+    w = wl.droplet_128x64(0.25)
+    p, f_ref, lat = run_both(lbm, w.mask, w.rho, w.params, 100)
+    rho_g, ux_g, uy_g = lat.fields()
+    rho_r, ux_r, uy_r = oracle.fields(p, w.mask, f_ref)
+    np.testing.assert_allclose(rho_g, rho_r, rtol=2e-6, atol=0)
+    umax = np.abs(np.r_[ux_r.ravel(), uy_r.ravel()]).max()
+    assert np.abs(ux_g - ux_r).max() <= 1e-5 * umax
+    assert np.abs(uy_g - uy_r).max() <= 1e-5 * umax
+
+
+def test_population_round_trip_and_resume(lbm):
+    """set/get of populations is exact in FP32, and a run resumed from a
+    checkpoint is bitwise identical to an uninterrupted one."""
+    w = wl.rough_channel(nx=300, ny=48, amp=6, level=15, seed=9, body_fx=1e-5)
+    p = oracle.Params(w.nx, w.ny, **w.params)
+    f0 = oracle.step(p, w.mask, oracle.equilibrium(p, w.mask, w.rho, 0, 0), 20)
+    lat = lbm.Lattice(w.nx, w.ny, **w.params)
+    lat.set_geometry(w.mask)
+    lat.set_populations(f0)
+    back = lat.populations()
+    assert np.array_equal(back, f0.astype(np.float32).astype(np.float64))
+    # uninterrupted 60 steps
+    lat.step(60)
+    ref = lat.populations()
+    # 25 steps, checkpoint, fresh context, 35 steps
+    lat2 = lbm.Lattice(w.nx, w.ny, **w.params)
+    lat2.set_geometry(w.mask)
+    lat2.set_populations(f0)
+    lat2.step(25)
+    ck = lat2.populations()
+    lat3 = lbm.Lattice(w.nx, w.ny, **w.params)
+    lat3.set_geometry(w.mask)
+    lat3.set_populations(ck)
+    lat3.step(35)
+    assert np.array_equal(lat3.populations(), ref)
+    # populations set from the oracle also step like the oracle
+    assert_pops(ref, oracle.step(p, w.mask, f0, 60), w.mask)
+
+
+def test_fused_observables_match_separate_pass(lbm):
+    w = wl.droplet_128x64(0.125)
+    lat = lbm.Lattice(w.nx, w.ny, **w.params, obs_every=10)
+    lat.set_geometry(w.mask)
+    lat.set_rho_u(w.rho)
+    o0 = lat.observables()
+    lat.step(1)
+    f = lat.obs_latest()
+    assert f["step"] == 0
+    for k in ("mass", "flux_Q", "mom_x", "mom_y", "max_u", "min_rho"):
+        assert f[k] == pytest.approx(o0[k], rel=1e-6, abs=1e-9)
+    lat.step(24)
+    assert lat.obs_latest()["step"] == 20
+    o25 = lat.observables()
+    assert o25["step"] == 25
+    assert o25["mass"] == pytest.approx(o0["mass"], rel=1e-6)
+
+
+def test_device_buffers(lbm):
+    import torch
+    w = wl.droplet_128x64(0.0625)
+    lat = lbm.Lattice(w.nx, w.ny, **w.params)
+    lat.set_geometry(torch.as_tensor(w.mask, device="cuda"))
+    lat.set_rho_u(torch.as_tensor(w.rho, device="cuda"))
+    lat.step(10)
+    dev = lat.populations_device().cpu().numpy()
+    assert np.array_equal(dev, lat.populations())
+
+
+def test_nonfinite_reported(lbm):
+    w = wl.droplet_128x64(0.0)
+    p = oracle.Params(w.nx, w.ny, **w.params)
+    f = oracle.equilibrium(p, w.mask, w.rho, 0, 0)
+    f[2, 30, 40] = np.nan
+    lat = lbm.Lattice(w.nx, w.ny, **w.params)
+    lat.set_geometry(w.mask)
+    lat.set_populations(f)
+    with pytest.raises(lbm.LbmError) as e:
+        lat.observables()
+    assert e.value.status == lbm.LBM_ENAN
+    o = lat.observables(check_finite=False)
+    assert o["nonfinite"] >= 1
+
+
+def test_error_paths(lbm):
+    import torch
+    p = lbm.make_params(64, 32)
+    nbytes = lbm.lbm_workspace_bytes(p)
+    assert nbytes > 0
+    assert lbm.lbm_workspace_bytes(lbm.make_params(64, 32, tau=0.5)) == 0
+    assert lbm.lbm_workspace_bytes(lbm.make_params(0, 32)) == 0
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_create(p, ws.data_ptr(), nbytes - 1, s)
+    assert e.value.status == lbm.LBM_ENOMEM
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_create(lbm.make_params(64, 32, green=7), ws.data_ptr(), nbytes, s)
+    assert e.value.status == lbm.LBM_EINVAL
+    ctx = lbm.lbm_create(p, ws.data_ptr(), nbytes, s)
+    try:
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_step(ctx, 1)
+        assert e.value.status == lbm.LBM_ESTATE
+        mask = np.zeros((32, 64), np.uint8)
+        lbm.lbm_set_geometry(ctx, mask.ctypes.data, False)
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_step(ctx, 1)
+        assert e.value.status == lbm.LBM_ESTATE
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_set_field(ctx, 7, mask.ctypes.data, False)
+        assert e.value.status == lbm.LBM_EINVAL
+        assert "unknown field" in lbm.lbm_last_error(ctx)
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_obs_latest(ctx)
+        assert e.value.status == lbm.LBM_ESTATE
+    finally:
+        lbm.lbm_destroy(ctx)
+    assert lbm.lbm_status_string(lbm.LBM_ENAN) == "LBM_ENAN"
+
+
+def test_full_size_sampled_parity(lbm):
+    """16384 x 4096 rough channel with the droplet row, in the benchmark's
+    launch configuration. A node's state after k steps depends only on the
+    state within Chebyshev distance 2k, so the oracle, run on a periodic crop
+    with a halo of 2k+2 around a sample window, reproduces the window
+    exactly; crops are cut from the generated inputs, never from GPU output."""
+    import torch
+    k = 3
+    w = wl.droplet_row_channel()
+    lat = lbm.Lattice(w.nx, w.ny, **w.params, obs_every=100)
+    lat.set_geometry(w.mask)
+    lat.set_rho_u(w.rho)
+    m0 = lat.observables()["mass"]
+    lat.step(k)
+    dev = lat.populations_device()
+    h, s = 2 * k + 2, 16
+    rng = np.random.default_rng(0)
+    windows = [(1, 60), (w.ny - 1 - s, 5000), (w.ny // 2, w.nx - 8), (3, 0)]
+    windows += [(int(rng.integers(0, w.ny)), int(rng.integers(0, w.nx))) for _ in range(8)]
+    for (y0, x0) in windows:
+        ys = np.arange(y0 - h, y0 + s + h) % w.ny
+        xs = np.arange(x0 - h, x0 + s + h) % w.nx
+        mask = np.ascontiguousarray(w.mask[np.ix_(ys, xs)])
+        rho = w.rho[np.ix_(ys, xs)]
+        p = oracle.Params(len(xs), len(ys), **w.params)
+        f_ref = oracle.step(p, mask, oracle.equilibrium(p, mask, rho, 0, 0), k)[:, h:h + s, h:h + s]
+        yi = torch.as_tensor(ys[h:h + s], device=dev.device)
+        xi = torch.as_tensor(xs[h:h + s], device=dev.device)
+        f_gpu = dev[:, yi][:, :, xi].cpu().numpy()
+        assert_pops(f_gpu, f_ref, mask[h:h + s, h:h + s])
+    del dev
+    # properties at full size: mass conserved (FP64 reduction of FP32 state)
+    lat.step(97)
+    o = lat.observables()
+    assert o["nonfinite"] == 0
+    assert abs(o["mass"] - m0) <= 1e-6 * m0
+    assert lat.obs_latest()["step"] == 0
