@@ -299,7 +299,7 @@ def run_ours(args, rank, world, local_rank):
     return line
 
 
-KERNEL_VERSION = "step-v1"
+KERNEL_VERSION = "step-v2-bulk-ring"
 
 
 def run_e2e(args, w, params, lbm, stream, world):

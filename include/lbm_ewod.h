@@ -93,7 +93,7 @@ typedef struct {
     int32_t obs_every; /* K > 0: every step whose index t is a multiple of K
                           also reduces the observables of state t, fused into
                           the step kernel (read with lbm_obs_latest); 0: off */
-    int32_t tile_rows; /* rows per CTA of the step kernel (4..256), 0 = auto */
+    int32_t tile_rows; /* rows per CTA segment of the step kernel (>= 4), 0 = auto */
 } lbm_params;
 
 typedef struct {

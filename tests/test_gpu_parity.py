@@ -76,13 +76,15 @@ def check_obs(lat, p, mask, f_ref, rel=1e-6):
     fl = mask == 0
     assert o["nonfinite"] == 0
     assert o["mass"] == pytest.approx(r["mass"], rel=rel)
-    # u = (j + F/2)/rho nearly cancels at interfaces (j ~ -F/2 at rest), so a
-    # node's u carries an error ~1e-6 (|j| + |F|/2)/rho: Q and P sum these
-    mx = np.abs(jx[fl]) + 0.5 * np.abs(fx[fl])
-    my = np.abs(jy[fl]) + 0.5 * np.abs(fy[fl])
-    assert abs(o["flux_Q"] - r["flux_Q"]) <= 1e-5 * (mx / rho[fl]).sum() / p.nx + 1e-12
-    assert abs(o["mom_x"] - r["mom_x"]) <= 1e-5 * mx.sum() + 1e-12
-    assert abs(o["mom_y"] - r["mom_y"]) <= 1e-5 * my.sum() + 1e-12
+    # j = sum_a f_a e_a cancels between populations of size ~rho, and
+    # u = (j + F/2)/rho cancels again at interfaces (j ~ -F/2 at rest): a
+    # node's u carries an error of a few 1e-7 (rho + |j| + |F|/2)/rho after
+    # 100 FP32 steps, and Q and P sum these per-node errors
+    mx = rho[fl] + np.abs(jx[fl]) + 0.5 * np.abs(fx[fl])
+    my = rho[fl] + np.abs(jy[fl]) + 0.5 * np.abs(fy[fl])
+    assert abs(o["flux_Q"] - r["flux_Q"]) <= 2e-6 * (mx / rho[fl]).sum() / p.nx
+    assert abs(o["mom_x"] - r["mom_x"]) <= 2e-6 * mx.sum()
+    assert abs(o["mom_y"] - r["mom_y"]) <= 2e-6 * my.sum()
     assert o["max_u"] == pytest.approx(r["max_u"], rel=1e-4)
     assert o["min_rho"] == pytest.approx(r["min_rho"], rel=1e-5)
     assert o["step"] == lat.time
