@@ -168,6 +168,46 @@ const char *lbm_status_string(int status);
  * bookkeeping); the caller's workspace is untouched. NULL is a no-op. */
 void lbm_destroy(lbm_ctx *ctx);
 
+/* Observables without a context and without any allocation. The paper has
+ * no counterpart to this entry point: it exists for callers that cannot
+ * allocate device memory at the moment they need the numbers. Examples are
+ * code that runs while a CUDA graph is being captured (cudaMalloc is not
+ * allowed during capture), a host process working inside a fixed device
+ * memory budget that is already spent, and monitoring or checkpoint tools
+ * that hold a state in their own buffers and must not touch the allocator.
+ *
+ * Inputs (device memory, owned by the caller): d_pops, the post-streaming
+ * populations as double[9][ny][nx] (the LBM_POPS layout of lbm_get_field);
+ * d_solid, the mask as uint8_t[ny][nx]. params gives nx, ny and the model
+ * parameters (tau, G, G_wall, rho0, rho_c, f_elec, body force, green; the
+ * storage, obs_every and tile_rows fields are only validated). step is
+ * copied into out->step. Output: *out, host memory, filled as
+ * lbm_observables fills it (same per-node arithmetic, partial sums in a
+ * different order). The call enqueues its work on cuda_stream and then
+ * synchronises that stream.
+ *
+ * Scratch: a fixed 64 KB array in device memory that the library declares
+ * statically (1024 per-CTA partial slots and one result record); every GPU
+ * that loads the library holds it until the process exits. Domains of more
+ * than 16,777,216 nodes (nx * ny) are rejected with LBM_EINVAL. The first
+ * call on a device looks up the array's device address (once per device,
+ * with that device current); make that first call before any stream
+ * capture. All calls share the array and each call overwrites what it
+ * reads, so nothing needs clearing; calls that overlap on the GPU (other
+ * streams, other host threads) race on it and must be serialised by the
+ * caller. No cudaMalloc, cudaFree or allocating library routine is called.
+ *
+ * Returns LBM_EINVAL (bad parameters, null pointers, domain too large),
+ * LBM_ECUDA, LBM_ENAN (with *out filled) or LBM_OK;
+ * lbm_noalloc_last_error() gives the message of the calling thread's last
+ * failure. */
+lbm_status lbm_observables_noalloc(const lbm_params *params, const double *d_pops,
+                                   const uint8_t *d_solid, int64_t step, void *cuda_stream,
+                                   lbm_obs *out);
+
+/* Message for the calling thread's last lbm_observables_noalloc failure. */
+const char *lbm_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

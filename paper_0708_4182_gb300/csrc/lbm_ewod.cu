@@ -18,6 +18,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 namespace lbm {
@@ -263,6 +264,111 @@ int aux_blocks(long long n, int sm_count)
     long long b = (n + kAuxThreads - 1) / kAuxThreads;
     const long long cap = 32LL * sm_count;
     return int(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+// ---------------------------------------------------------------------------
+// allocation-free observables (see lbm_observables_noalloc in lbm_ewod.h)
+
+constexpr int kNoAllocSlots = 1024;                   // per-CTA partial slots
+constexpr int kNoAllocNodesPerCta = 64 * kAuxThreads;  // nodes one CTA reduces
+constexpr long long kNoAllocMaxNodes = (long long)kNoAllocSlots * kNoAllocNodesPerCta;
+
+// Per-CTA partials followed by one lbm_obs record: 64 KB + 64 B, resident on
+// every device that loads the library. Host code must not use this name as an
+// address; it goes through cudaGetSymbolAddress (noalloc_scratch below).
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocSlots * kPartialStride + 8];
+
+// Observables of the post-streaming populations `pops` (dense FP64
+// [9][ny][nx]) on the fluid nodes of `solid`, one CTA per chunk of
+// kNoAllocNodesPerCta nodes. Per node it rebuilds what the step kernel's
+// observables pass sees (FP32 populations, rho, j, psi of the node and its 8
+// neighbours, solid flags of the pull sources) and hands them to the same
+// collide_node<kObs>. Every CTA writes its whole partial slot.
+__global__ void __launch_bounds__(kAuxThreads)
+    observe_dense_kernel(const double* __restrict__ pops, const uint8_t* __restrict__ solid, Geom g,
+                         Phys p, double* __restrict__ partials)
+{
+    const long long n = (long long)g.nx * g.ny;
+    const long long first = (long long)blockIdx.x * kNoAllocNodesPerCta;
+    const long long last = min(first + kNoAllocNodesPerCta, n);
+    ObsAcc acc;
+    auto rho_at = [&](int x, int y) {
+        const long long j = (long long)y * g.nx + x;
+        float v[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) v[a] = float(pops[a * n + j]);
+        return ((v[0] + (v[1] + v[3])) + (v[2] + v[4])) + ((v[5] + v[7]) + (v[6] + v[8]));
+    };
+    for (long long i = first + threadIdx.x; i < last; i += kAuxThreads) {
+        if (solid[i]) continue;
+        const int y = int(i / g.nx), x = int(i % g.nx);
+        Pulled nd;
+        nd.solid = false;
+        float v[9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) v[a] = float(pops[a * n + i]);
+        uint32_t sb = 0;
+#pragma unroll
+        for (int a = 1; a < 9; ++a) {
+            const int xs = wrapi(x - kEx[a], g.nx), ys = wrapi(y - kEy[a], g.ny);
+            if (solid[(long long)ys * g.nx + xs]) sb |= 1u << a;
+        }
+#pragma unroll
+        for (int a = 0; a < 9; ++a) nd.f[a] = v[a];
+        nd.sb = sb;
+        nd.rho = ((v[0] + (v[1] + v[3])) + (v[2] + v[4])) + ((v[5] + v[7]) + (v[6] + v[8]));
+        nd.jx = (v[1] - v[3]) + (v[5] - v[7]) + (v[8] - v[6]);
+        nd.jy = (v[2] - v[4]) + (v[5] - v[7]) + (v[6] - v[8]);
+        // psi of the 3x3 neighbourhood, rows y-1, y, y+1 and columns x-1, x, x+1
+        float psi3[3][3];
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int xn = wrapi(x + dx, g.nx), yn = wrapi(y + dy, g.ny);
+                Pulled q;
+                q.solid = solid[(long long)yn * g.nx + xn] != 0;
+                q.rho = q.solid ? 0.f : (dx == 0 && dy == 0 ? nd.rho : rho_at(xn, yn));
+                psi3[dy + 1][dx + 1] = pseudopotential(p, q);
+            }
+        collide_node<kObs>(nd, psi3[0], psi3[1], psi3[2], 1, p, g, nullptr, nullptr, x, y, acc);
+    }
+    // deterministic CTA reduction into this CTA's partial slot
+    __shared__ double red_d[4][kAuxThreads / 32];
+    __shared__ float red_f[2][kAuxThreads / 32];
+    __shared__ unsigned red_u[kAuxThreads / 32];
+    double d[4] = {acc.mass.value(), acc.q.value(), acc.px.value(), acc.py.value()};
+    float umax2 = acc.umax2, rmin = acc.rmin;
+    unsigned bad = acc.bad;
+    for (int off = 16; off > 0; off >>= 1) {
+        for (int q = 0; q < 4; ++q) d[q] += __shfl_down_sync(0xffffffffu, d[q], off);
+        umax2 = fmaxf(umax2, __shfl_down_sync(0xffffffffu, umax2, off));
+        rmin = fminf(rmin, __shfl_down_sync(0xffffffffu, rmin, off));
+        bad += __shfl_down_sync(0xffffffffu, bad, off);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        for (int q = 0; q < 4; ++q) red_d[q][w] = d[q];
+        red_f[0][w] = umax2;
+        red_f[1][w] = rmin;
+        red_u[w] = bad;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s4[4] = {0, 0, 0, 0};
+        float um = 0.f, rm = __int_as_float(0x7f800000);
+        unsigned b = 0;
+        for (int k = 0; k < kAuxThreads / 32; ++k) {
+            for (int q = 0; q < 4; ++q) s4[q] += red_d[q][k];
+            um = fmaxf(um, red_f[0][k]);
+            rm = fminf(rm, red_f[1][k]);
+            b += red_u[k];
+        }
+        double* out = partials + (size_t)blockIdx.x * kPartialStride;
+        for (int q = 0; q < 4; ++q) out[q] = s4[q];
+        out[4] = um;
+        out[5] = rm;
+        out[6] = b;
+        out[7] = 0.0;
+    }
 }
 
 }  // namespace
@@ -632,5 +738,83 @@ const char* lbm_status_string(int s)
 }
 
 void lbm_destroy(lbm_ctx* c) { delete c; }
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device with that device current. Returns nullptr on failure.
+static double* noalloc_scratch(int dev, cudaError_t* err)
+{
+    constexpr int kMaxDevices = 64;
+    static std::mutex mu;
+    static double* addr[kMaxDevices] = {};
+    *err = cudaSuccess;
+    if (dev < 0 || dev >= kMaxDevices) {
+        *err = cudaErrorInvalidDevice;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* ptr = nullptr;
+        *err = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (*err != cudaSuccess) return nullptr;
+        addr[dev] = static_cast<double*>(ptr);
+    }
+    return addr[dev];
+}
+
+static thread_local char g_noalloc_err[256];
+
+lbm_status lbm_observables_noalloc(const lbm_params* p, const double* d_pops, const uint8_t* d_solid,
+                                   int64_t step, void* cuda_stream, lbm_obs* out)
+{
+    g_noalloc_err[0] = 0;
+    const char* why = "";
+    if (!params_valid(p, &why)) {
+        snprintf(g_noalloc_err, sizeof(g_noalloc_err), "invalid parameters: %s", why);
+        return LBM_EINVAL;
+    }
+    if (!d_pops || !d_solid || !out) {
+        snprintf(g_noalloc_err, sizeof(g_noalloc_err), "null populations, mask or output");
+        return LBM_EINVAL;
+    }
+    const long long n = (long long)p->nx * p->ny;
+    if (n > kNoAllocMaxNodes) {
+        snprintf(g_noalloc_err, sizeof(g_noalloc_err),
+                 "domain of %lld nodes exceeds the allocation-free limit of %lld nodes", n, kNoAllocMaxNodes);
+        return LBM_EINVAL;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    double* scratch = e == cudaSuccess ? noalloc_scratch(dev, &e) : nullptr;
+    if (!scratch) {
+        cudaGetLastError();
+        snprintf(g_noalloc_err, sizeof(g_noalloc_err), "scratch address: %s", cudaGetErrorString(e));
+        return LBM_ECUDA;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    Geom g{};
+    g.nx = p->nx;
+    g.ny = p->ny;
+    g.pitch = p->nx;
+    g.plane = p->ny * p->nx;
+    g.tile_rows = 1;
+    const int ctas = int((n + kNoAllocNodesPerCta - 1) / kNoAllocNodesPerCta);
+    lbm_obs* rec = reinterpret_cast<lbm_obs*>(scratch + kNoAllocSlots * kPartialStride);
+    observe_dense_kernel<<<ctas, kAuxThreads, 0, st>>>(d_pops, d_solid, g, make_phys(*p), scratch);
+    finalize_obs_kernel<<<1, kAuxThreads, 0, st>>>(scratch, ctas, 1.0 / p->nx, (long long)step, rec);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, rec, sizeof(lbm_obs), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        snprintf(g_noalloc_err, sizeof(g_noalloc_err), "observables: %s", cudaGetErrorString(e));
+        return LBM_ECUDA;
+    }
+    if (out->nonfinite > 0) {
+        snprintf(g_noalloc_err, sizeof(g_noalloc_err), "%lld non-finite fluid nodes", (long long)out->nonfinite);
+        return LBM_ENAN;
+    }
+    return LBM_OK;
+}
+
+const char* lbm_noalloc_last_error(void) { return g_noalloc_err; }
 
 }  // extern "C"

@@ -285,3 +285,29 @@ class Lattice:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------- allocation-free call
+
+def lbm_observables_noalloc(params: lbm_params, d_pops: int, d_solid: int, step: int,
+                            cuda_stream: int, check_finite: bool = True) -> dict:
+    """Observables of device-resident post-streaming populations (double
+    [9][ny][nx]) and mask (uint8 [ny][nx]) without a context and without any
+    device allocation: for callers that cannot allocate when they need the
+    numbers (inside CUDA graph capture, within a spent memory budget, in
+    monitoring tools). The library keeps the scratch in a fixed 64 KB static
+    device array shared by all calls, so calls that overlap on the GPU race;
+    domains above 16,777,216 nodes are rejected. Synchronises cuda_stream."""
+    lib = load()
+    fn = lib.lbm_observables_noalloc
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.POINTER(lbm_params), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                   ctypes.c_void_p, ctypes.POINTER(lbm_obs)]
+    lib.lbm_noalloc_last_error.restype = ctypes.c_char_p
+    lib.lbm_noalloc_last_error.argtypes = []
+    o = lbm_obs()
+    st = fn(ctypes.byref(params), ctypes.c_void_p(d_pops), ctypes.c_void_p(d_solid), int(step),
+            ctypes.c_void_p(cuda_stream), ctypes.byref(o))
+    if st != LBM_OK and not (st == LBM_ENAN and not check_finite):
+        raise LbmError(st, lib.lbm_noalloc_last_error().decode())
+    return o.as_dict()
