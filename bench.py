@@ -38,6 +38,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 BYTES_PER_NODE_FP32 = 72  # 9 x 4 B read + 9 x 4 B write per fluid node and step
+# storage form -> (lbm storage code, algorithmic bytes per fluid node and step)
+STORAGE = {"fp32": (0, 72), "fp32dev": (1, 72), "fp16dev": (2, 40), "bf16dev": (3, 40)}
 
 
 def parse():
@@ -50,6 +52,9 @@ def parse():
     ap.add_argument("--ny", type=int, default=4096)
     ap.add_argument("--obs-every", type=int, default=100)
     ap.add_argument("--tile-rows", type=int, default=0)
+    ap.add_argument("--storage", default="fp32", choices=list(STORAGE),
+                    help="population storage: fp32 (plain), fp32dev (deviation from the weighted "
+                         "rest equilibrium), fp16dev / bf16dev (16-bit deviations)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -65,7 +70,7 @@ def workload(nx, ny):
 
 def workload_name(nx, ny):
     return (f"rough-wall channel {nx}x{ny}, roughness amplitude 6 (seed 0), body force 1e-6, "
-            f"row of sessile droplets R=20 pitch 128 on the bottom wall, FP32 populations")
+            f"row of sessile droplets R=20 pitch 128 on the bottom wall")
 
 
 # ----------------------------------------------------------------- clocks
@@ -226,7 +231,8 @@ def run_ours(args, rank, world, local_rank):
     w = workload(args.nx, args.ny)
     n_nodes = w.nx * w.ny
     n_fluid = int((w.mask == 0).sum())
-    params = dict(w.params, obs_every=args.obs_every, tile_rows=args.tile_rows)
+    storage_code, bytes_per_node = STORAGE[args.storage]
+    params = dict(w.params, obs_every=args.obs_every, tile_rows=args.tile_rows, storage=storage_code)
     stream = torch.cuda.Stream()
     lat = lbm.Lattice(w.nx, w.ny, stream=stream, **params)
     lat.set_geometry(w.mask)
@@ -263,17 +269,18 @@ def run_ours(args, rank, world, local_rank):
                                 if args.obs_every and t % args.obs_every == 0)
 
     # roofline of the dominant kernel (the fused step): algorithmic bytes / step time
-    per_launch_bytes = BYTES_PER_NODE_FP32 * n_fluid
+    per_launch_bytes = bytes_per_node * n_fluid
     achieved = per_launch_bytes / (ms_step * 1e-3) / 1e9
     peak, peak_kind = measured_peak_hbm()
     prof = traffic_from_profile()
     traffic = None
-    if prof and prof.get("nx") and prof.get("kernel_version") == KERNEL_VERSION:
+    if prof and prof.get("nx") and prof.get("kernel_version") == KERNEL_VERSION and \
+            prof.get("storage", "fp32") == args.storage:
         traffic = prof["dram_bytes_per_node"] * n_nodes
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic,
             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
-            "bytes_per_node": BYTES_PER_NODE_FP32, "fluid_nodes": n_fluid}
+            "bytes_per_node": bytes_per_node, "fluid_nodes": n_fluid}
 
     e2e = None
     if not args.no_e2e:
@@ -284,7 +291,7 @@ def run_ours(args, rank, world, local_rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": workload_name(w.nx, w.ny), "nx": w.nx, "ny": w.ny,
-                       "fluid_nodes": n_fluid, "obs_every": args.obs_every,
+                       "fluid_nodes": n_fluid, "obs_every": args.obs_every, "storage": args.storage,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (2 x 2.4 GB population buffers)",
                        "fluid_mlups": round(world * n_fluid * args.steps / (ms * 1e-3) / 1e6, 1)},

@@ -71,8 +71,17 @@ typedef enum {
  * Eq. 4 (2G axis, G diagonal), which diverges at G = -0.52. */
 enum { LBM_GREEN_MC = 0, LBM_GREEN_PRINTED = 1 };
 
-/* Population storage in device memory. Arithmetic is always FP32. */
-enum { LBM_FP32 = 0 };
+/* Population storage in device memory (arithmetic is FP32 in all forms).
+ * LBM_FP32:     the post-collision populations f*_a, FP32 (36 B per node).
+ * LBM_FP32_DEV: rho* = sum_a f*_a (FP32) and the deviations
+ *               d_a = f*_a - w_a rho* from the node's weighted rest
+ *               equilibrium, FP32 (36 B per node). Slow flows whose per-step
+ *               change is below half an ulp of a plain FP32 population keep
+ *               evolving in this form (plain FP32 stalls short of the steady
+ *               state, e.g. 0.4% low in the flux of a channel driven by 1e-6).
+ * LBM_FP16_DEV / LBM_BF16_DEV: as LBM_FP32_DEV with d_a in 16 bits (20 B per
+ *               node, rounded to nearest); nx must be a multiple of 8. */
+enum { LBM_FP32 = 0, LBM_FP32_DEV = 1, LBM_FP16_DEV = 2, LBM_BF16_DEV = 3 };
 
 /* Field selectors for lbm_set_field / lbm_get_field. */
 enum { LBM_RHO_U = 0, LBM_POPS = 1 };
@@ -89,7 +98,7 @@ typedef struct {
     double body_fx;    /* body-force acceleration; the paper drives its */
     double body_fy;    /*   channels with a rightward f_b                */
     int32_t green;     /* LBM_GREEN_MC or LBM_GREEN_PRINTED */
-    int32_t storage;   /* LBM_FP32 */
+    int32_t storage;   /* LBM_FP32, LBM_FP32_DEV, LBM_FP16_DEV or LBM_BF16_DEV */
     int32_t obs_every; /* K > 0: every step whose index t is a multiple of K
                           also reduces the observables of state t, fused into
                           the step kernel (read with lbm_obs_latest); 0: off */

@@ -45,7 +45,10 @@ bool params_valid(const lbm_params* p, const char** why)
     if (!(p->tau > 0.5) || !(p->tau < 1e6)) { *why = "tau must be > 0.5"; return false; }
     if (!(p->rho0 > 0.0)) { *why = "rho0 must be > 0"; return false; }
     if (p->green != LBM_GREEN_MC && p->green != LBM_GREEN_PRINTED) { *why = "unknown green convention"; return false; }
-    if (p->storage != LBM_FP32) { *why = "unsupported storage"; return false; }
+    if (p->storage < LBM_FP32 || p->storage > LBM_BF16_DEV) { *why = "unsupported storage"; return false; }
+    if ((p->storage == LBM_FP16_DEV || p->storage == LBM_BF16_DEV) && (p->nx % 8) != 0) {
+        *why = "16-bit storage needs nx to be a multiple of 8"; return false;
+    }
     if (p->obs_every < 0) { *why = "obs_every must be >= 0"; return false; }
     if (p->tile_rows < 0 || (p->tile_rows != 0 && p->tile_rows < 4)) { *why = "tile_rows must be 0 or >= 4"; return false; }
     if ((p->ny + 3) / 4 > 65535) { *why = "ny too large for the step grid (ny <= 262140)"; return false; }
@@ -131,29 +134,25 @@ __device__ __forceinline__ double feq_d(int a, double rho, double ux, double uy)
     return kW[a] * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * (ux * ux + uy * uy));
 }
 
-// Initial state from (rho, ux, uy): the post-streaming populations are
-// f_a = f_a^eq (Eq. 3); stored as the post-collision f* that the next pull
-// turns back into them: f*_a(x) = f_a(x + e_a) if x + e_a is fluid, else
-// f_opp(a)(x) (the population that bounce-back will return to x).
-__global__ void rho_u_to_fstar_kernel(const double* __restrict__ ru, const uint8_t* __restrict__ mask,
-                                      float* __restrict__ out, Geom g)
+// Initial state from (rho, ux, uy): the post-streaming populations
+// f_a = f_a^eq(rho, u) of Eq. 3 (evaluated in FP64, rounded once), written
+// into buffer `f` in plane layout; solid nodes get the sentinel.
+__global__ void feq_kernel(const double* __restrict__ ru, const uint8_t* __restrict__ mask,
+                           float* __restrict__ f, Geom g)
 {
     const long long n = (long long)g.nx * g.ny;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        if (mask[i]) continue;
         const int y = int(i / g.nx), x = int(i % g.nx);
         const int o = y * g.pitch + x;
-        for (int a = 0; a < 9; ++a) {
-            const int xn = wrapi(x + kEx[a], g.nx), yn = wrapi(y + kEy[a], g.ny);
-            const long long j = (long long)yn * g.nx + xn;
-            double v;
-            if (mask[j])
-                v = feq_d(kOpp[a], ru[i], ru[n + i], ru[2 * n + i]);
-            else
-                v = feq_d(a, ru[j], ru[n + j], ru[2 * n + j]);
-            out[a * g.plane + o] = float(v);
+        if (mask[i]) {
+#pragma unroll
+            for (int a = 0; a < 9; ++a) f[a * g.plane + o] = __uint_as_float(kSolidBits);
+            continue;
         }
+        const double rho = ru[i], ux = ru[n + i], uy = ru[2 * n + i];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) f[a * g.plane + o] = float(feq_d(a, rho, ux, uy));
     }
 }
 
@@ -174,14 +173,18 @@ __global__ void pops_in_kernel(const double* __restrict__ src, float* __restrict
 
 // Post-streaming f (buffer `f`) -> post-collision f* (buffer `out`), the
 // inverse of the pull: f*_a(x) = f_a(x + e_a) or, next to a wall, f_opp(a)(x).
+// Solid nodes of `out` get the sentinel.
 __global__ void unstream_kernel(const float* __restrict__ f, const uint8_t* __restrict__ mask,
                                 float* __restrict__ out, Geom g)
 {
     const long long n = (long long)g.nx * g.ny;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        if (mask[i]) continue;
         const int y = int(i / g.nx), x = int(i % g.nx);
+        if (mask[i]) {
+            for (int a = 0; a < 9; ++a) out[a * g.plane + y * g.pitch + x] = __uint_as_float(kSolidBits);
+            continue;
+        }
         for (int a = 0; a < 9; ++a) {
             const int xn = wrapi(x + kEx[a], g.nx), yn = wrapi(y + kEy[a], g.ny);
             float v;
@@ -215,6 +218,58 @@ __global__ void pops_out_kernel(const float* __restrict__ fs, const uint8_t* __r
             }
             dst[a * n + i] = v;
         }
+    }
+}
+
+// Plain post-collision planes f* (FP32) -> deviation form: plane 0 gets
+// rho* = sum_a f*_a, planes 1..8 (type T) get d_a = f*_a - w_a rho*
+// (FP64 arithmetic, one rounding each). Solid nodes get the sentinel.
+template <typename T>
+__global__ void plain_to_dev_kernel(const float* __restrict__ fs, const uint8_t* __restrict__ mask,
+                                    float* __restrict__ out, Geom g)
+{
+    const long long n = (long long)g.nx * g.ny;
+    T* od = reinterpret_cast<T*>(out + g.plane);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int y = int(i / g.nx), x = int(i % g.nx);
+        const int o = y * g.pitch + x;
+        if (mask[i]) {
+            out[o] = __uint_as_float(kSolidBits);
+            continue;
+        }
+        double r = 0.0;
+        for (int a = 0; a < 9; ++a) r += fs[a * g.plane + o];
+        const float r32 = float(r);
+        out[o] = r32;
+        for (int a = 1; a < 9; ++a) od[(a - 1) * g.plane + o] = from_f<T>(float(double(fs[a * g.plane + o]) - kW[a] * double(r32)));
+    }
+}
+
+// Deviation form -> plain post-collision planes: f*_a = w_a rho* + d_a,
+// f*_0 = w_0 rho* - sum_a d_a (FP64, one rounding each); solids get the sentinel.
+template <typename T>
+__global__ void dev_to_plain_kernel(const float* __restrict__ in, const uint8_t* __restrict__ mask,
+                                    float* __restrict__ fs, Geom g)
+{
+    const long long n = (long long)g.nx * g.ny;
+    const T* id = reinterpret_cast<const T*>(in + g.plane);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int y = int(i / g.nx), x = int(i % g.nx);
+        const int o = y * g.pitch + x;
+        if (mask[i]) {
+            for (int a = 0; a < 9; ++a) fs[a * g.plane + o] = __uint_as_float(kSolidBits);
+            continue;
+        }
+        const double r = in[o];
+        double dsum = 0.0;
+        for (int a = 1; a < 9; ++a) {
+            const double d = to_f(id[(a - 1) * g.plane + o]);
+            dsum += d;
+            fs[a * g.plane + o] = float(kW[a] * r + d);
+        }
+        fs[o] = float(kW[0] * r - dsum);
     }
 }
 
@@ -441,19 +496,76 @@ Phys make_phys(const lbm_params& p)
     return h;
 }
 
+template <int MODE, int ST>
+lbm_status launch_step_st(lbm_ctx* c, const float* fin, float* fout, double* fields)
+{
+    step_kernel<MODE, ST><<<c->grid, kThreads, smem_bytes<ST>(), c->stream>>>(fin, fout, c->g, c->ph,
+                                                                               c->partials, fields, c->status);
+    return check_launch(c, "step kernel launch");
+}
+
 template <int MODE>
 lbm_status launch_step(lbm_ctx* c, const float* fin, float* fout, double* fields)
 {
-    step_kernel<MODE><<<c->grid, kThreads, kSmemBytes, c->stream>>>(fin, fout, c->g, c->ph, c->partials,
-                                                                    fields, c->status);
-    return check_launch(c, "step kernel launch");
+    switch (c->prm.storage) {
+    case LBM_FP32_DEV: return launch_step_st<MODE, kF32Dev>(c, fin, fout, fields);
+    case LBM_FP16_DEV: return launch_step_st<MODE, kF16Dev>(c, fin, fout, fields);
+    case LBM_BF16_DEV: return launch_step_st<MODE, kBF16Dev>(c, fin, fout, fields);
+    default: return launch_step_st<MODE, kF32>(c, fin, fout, fields);
+    }
+}
+
+template <int MODE, int ST>
+cudaError_t allow_smem_st()
+{
+    return cudaFuncSetAttribute(step_kernel<MODE, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(smem_bytes<ST>()));
 }
 
 template <int MODE>
 cudaError_t allow_smem()
 {
-    return cudaFuncSetAttribute(step_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                int(kSmemBytes));
+    cudaError_t e = allow_smem_st<MODE, kF32>();
+    if (e == cudaSuccess) e = allow_smem_st<MODE, kF32Dev>();
+    if (e == cudaSuccess) e = allow_smem_st<MODE, kF16Dev>();
+    if (e == cudaSuccess) e = allow_smem_st<MODE, kBF16Dev>();
+    return e;
+}
+
+// Convert the plain f* in c->cur to the context's deviation form (into the
+// spare buffer, which becomes current). No-op for plain storage.
+lbm_status plain_to_storage(lbm_ctx* c)
+{
+    const long long n = (long long)c->g.nx * c->g.ny;
+    const int b = aux_blocks(n, c->sm_count);
+    switch (c->prm.storage) {
+    case LBM_FP32_DEV: plain_to_dev_kernel<float><<<b, kAuxThreads, 0, c->stream>>>(c->cur, c->mask, c->nxt, c->g); break;
+    case LBM_FP16_DEV: plain_to_dev_kernel<__half><<<b, kAuxThreads, 0, c->stream>>>(c->cur, c->mask, c->nxt, c->g); break;
+    case LBM_BF16_DEV: plain_to_dev_kernel<__nv_bfloat16><<<b, kAuxThreads, 0, c->stream>>>(c->cur, c->mask, c->nxt, c->g); break;
+    default: return LBM_OK;
+    }
+    lbm_status s = check_launch(c, "storage conversion launch");
+    if (s) return s;
+    float* tmp = c->cur;
+    c->cur = c->nxt;
+    c->nxt = tmp;
+    return LBM_OK;
+}
+
+// Plain f* of the current state: c->cur itself for plain storage, else a
+// conversion into the spare buffer (which the next step overwrites).
+lbm_status storage_to_plain(lbm_ctx* c, const float** plain)
+{
+    const long long n = (long long)c->g.nx * c->g.ny;
+    const int b = aux_blocks(n, c->sm_count);
+    switch (c->prm.storage) {
+    case LBM_FP32_DEV: dev_to_plain_kernel<float><<<b, kAuxThreads, 0, c->stream>>>(c->cur, c->mask, c->nxt, c->g); break;
+    case LBM_FP16_DEV: dev_to_plain_kernel<__half><<<b, kAuxThreads, 0, c->stream>>>(c->cur, c->mask, c->nxt, c->g); break;
+    case LBM_BF16_DEV: dev_to_plain_kernel<__nv_bfloat16><<<b, kAuxThreads, 0, c->stream>>>(c->cur, c->mask, c->nxt, c->g); break;
+    default: *plain = c->cur; return LBM_OK;
+    }
+    *plain = c->nxt;
+    return check_launch(c, "storage conversion launch");
 }
 
 // Read and clear the device error flag (the stream must be synchronised).
@@ -567,6 +679,8 @@ lbm_status lbm_set_field(lbm_ctx* c, int which, const double* data, int on_devic
     const size_t n = size_t(c->g.nx) * c->g.ny;
     lbm_status s;
     if (which == LBM_RHO_U) {
+        // (rho, u) -> f_eq into the current buffer -> un-streamed into the
+        // spare one, which becomes current; both end with solid sentinels
         const double* src = data;
         if (!on_device) {
             // (rho, ux, uy) in FP64 fits in the spare population buffer
@@ -576,13 +690,14 @@ lbm_status lbm_set_field(lbm_ctx* c, int which, const double* data, int on_devic
                 return s;
             src = tmp;
         }
-        rho_u_to_fstar_kernel<<<aux_blocks(n, c->sm_count), kAuxThreads, 0, c->stream>>>(src, c->mask, c->cur, c->g);
+        feq_kernel<<<aux_blocks(n, c->sm_count), kAuxThreads, 0, c->stream>>>(src, c->mask, c->cur, c->g);
         if ((s = check_launch(c, "field kernel launch"))) return s;
-        if (!on_device) {
-            // restore the sentinels the FP64 scratch overwrote in the spare buffer
-            geometry_kernel<<<aux_blocks(n, c->sm_count), kAuxThreads, 0, c->stream>>>(c->mask, c->nxt, c->nxt, c->g);
-            if ((s = check_launch(c, "geometry kernel launch"))) return s;
-        }
+        unstream_kernel<<<aux_blocks(n, c->sm_count), kAuxThreads, 0, c->stream>>>(c->cur, c->mask, c->nxt, c->g);
+        if ((s = check_launch(c, "unstream kernel launch"))) return s;
+        float* tmpb = c->cur;
+        c->cur = c->nxt;
+        c->nxt = tmpb;
+        if ((s = plain_to_storage(c))) return s;
     } else if (which == LBM_POPS) {
         const int nx = c->g.nx, ny = c->g.ny;
         const int rows_per = on_device ? ny : int(c->L.staging_bytes / (9 * size_t(nx) * sizeof(double)));
@@ -613,6 +728,7 @@ lbm_status lbm_set_field(lbm_ctx* c, int which, const double* data, int on_devic
         if ((s = check_launch(c, "unstream kernel launch"))) return s;
         geometry_kernel<<<aux_blocks(n, c->sm_count), kAuxThreads, 0, c->stream>>>(c->mask, c->nxt, c->nxt, c->g);
         if ((s = check_launch(c, "geometry kernel launch"))) return s;
+        if ((s = plain_to_storage(c))) return s;
     } else {
         return fail(c, LBM_EINVAL, "unknown field selector %d", which);
     }
@@ -642,14 +758,16 @@ lbm_status lbm_get_field(lbm_ctx* c, int which, double* out, int on_device)
     }
     if (which != LBM_POPS) return fail(c, LBM_EINVAL, "unknown field selector %d", which);
     const int nx = c->g.nx, ny = c->g.ny;
+    const float* plain = nullptr;
+    if ((s = storage_to_plain(c, &plain))) return s;
     if (on_device) {
-        pops_out_kernel<<<aux_blocks(n, c->sm_count), kAuxThreads, 0, c->stream>>>(c->cur, c->mask, out, c->g, 0, ny);
+        pops_out_kernel<<<aux_blocks(n, c->sm_count), kAuxThreads, 0, c->stream>>>(plain, c->mask, out, c->g, 0, ny);
         return check_launch(c, "population kernel launch");
     }
     const int rows_per = int(c->L.staging_bytes / (9 * size_t(nx) * sizeof(double)));
     for (int r0 = 0; r0 < ny; r0 += rows_per) {
         const int rows = (r0 + rows_per <= ny) ? rows_per : ny - r0;
-        pops_out_kernel<<<aux_blocks(size_t(rows) * nx, c->sm_count), kAuxThreads, 0, c->stream>>>(c->cur, c->mask, c->staging, c->g, r0, rows);
+        pops_out_kernel<<<aux_blocks(size_t(rows) * nx, c->sm_count), kAuxThreads, 0, c->stream>>>(plain, c->mask, c->staging, c->g, r0, rows);
         if ((s = check_launch(c, "population kernel launch"))) return s;
         for (int a = 0; a < 9; ++a) {
             if ((s = check_cuda(c, cudaMemcpyAsync(out + size_t(a) * n + size_t(r0) * nx,

@@ -30,9 +30,24 @@
 //  - every mbarrier wait is bounded: on timeout the kernel sets a flag in
 //    global memory, stops waiting and runs to completion, and the host
 //    reports LBM_ETIMEOUT.
+//
+// Storage forms (template parameter ST; the arithmetic is FP32 in all):
+//  - kF32:     plane a holds f*_a (plain populations);
+//  - kF32Dev:  plane 0 holds rho* = sum_a f*_a and planes 1..8 hold the
+//              deviations d_a = f*_a - w_a rho* from the node's weighted rest
+//              equilibrium, all FP32 (f*_0 = w_0 rho* - sum_a d_a). Small
+//              per-step changes of a slow flow are representable in d_a,
+//              where a plain FP32 f*_a of size ~w_a rho rounds them away;
+//  - kF16Dev / kBF16Dev: as kF32Dev with d_a stored in 16 bits (FP16 or
+//              BF16, rounded to nearest); 20 instead of 36 bytes per node.
+// In the deviation forms the pull rebuilds f_a = w_a rho*(src) + d_a(src),
+// and the kernel forms rho - rho*(x) and rho u from sums of small terms.
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace lbm {
@@ -47,9 +62,36 @@ constexpr int kStages = 6;                     // ring depth (rows)
 constexpr int kPartialStride = 8;              // doubles per CTA in the partials array
 constexpr uint32_t kWaitLimit = 1u << 22;      // try_wait rounds before giving up
 
-constexpr size_t kStageBytes = size_t(9) * kRowLen * sizeof(float);
-constexpr size_t kSmemBytes = kStages * kStageBytes + 4 * (kW + 2) * sizeof(float) +
-                              2 * kStages * sizeof(uint64_t) + 128;
+enum Storage { kF32 = 0, kF32Dev = 1, kF16Dev = 2, kBF16Dev = 3 };
+
+template <int ST> struct StoreT;
+template <> struct StoreT<kF32> { using T = float; static constexpr int halo = 4; };
+template <> struct StoreT<kF32Dev> { using T = float; static constexpr int halo = 4; };
+template <> struct StoreT<kF16Dev> { using T = __half; static constexpr int halo = 8; };
+template <> struct StoreT<kBF16Dev> { using T = __nv_bfloat16; static constexpr int halo = 8; };
+
+// staged row: plane 0 (FP32, row_len floats) then planes 1..8 (type T)
+template <int ST> __host__ __device__ constexpr int row_len() { return kW + 2 * StoreT<ST>::halo; }
+template <int ST> __host__ __device__ constexpr size_t stage_bytes()
+{
+    return size_t(row_len<ST>()) * (sizeof(float) + 8 * sizeof(typename StoreT<ST>::T));
+}
+template <int ST> __host__ __device__ constexpr size_t smem_bytes()
+{
+    return kStages * stage_bytes<ST>() + 4 * (kW + 2) * sizeof(float) + 2 * kStages * sizeof(uint64_t) + 128;
+}
+// bytes of one node's state in global memory (plane 0 + planes 1..8)
+template <int ST> __host__ __device__ constexpr int node_bytes() { return 4 + 8 * int(sizeof(typename StoreT<ST>::T)); }
+
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <typename T> __device__ __forceinline__ T from_f(float v);
+template <> __device__ __forceinline__ float from_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+constexpr size_t kSmemBytes = smem_bytes<kF32>();
 
 struct Geom {
     int nx, ny;
@@ -219,7 +261,8 @@ __device__ __forceinline__ void pull_smem(const float* __restrict__ sm, const fl
     n.jy = (v[2] - v[4]) + (v[5] - v[7]) + (v[6] - v[8]);
 }
 
-__device__ __forceinline__ float pseudopotential(const Phys& p, const Pulled& n)
+template <typename N>
+__device__ __forceinline__ float pseudopotential(const Phys& p, const N& n)
 {
     // psi = rho0 (1 - exp(-rho/rho0)), via expm1 to keep small-rho accuracy
     return n.solid ? 0.f : -p.rho0 * expm1f(-n.rho * p.inv_rho0);
@@ -247,11 +290,12 @@ struct ObsAcc {
 // Forces, velocity shift, collision and the mode's epilogue for one fluid node
 // (x, r) whose pulled populations are `n`; psi rows r-1, r, r+1 are pm, pc, pp
 // (indexed by ring column t = node column - x0 + 1).
-template <int MODE>
-__device__ __forceinline__ void collide_node(const Pulled& n, const float* pm, const float* pc,
-                                             const float* pp, int t, const Phys& p, const Geom& g,
-                                             float* __restrict__ fout, double* __restrict__ fields,
-                                             int x, int r, ObsAcc& acc)
+// Total force on one fluid node: Eq. 5 from the psi rows pm, pc, pp (ring
+// column t), Eq. 6 and the electric wall-layer force from the solid flags of
+// the pull sources (n.sb), and the body force. N has fields rho and sb.
+template <typename N>
+__device__ __forceinline__ void node_force(const N& n, const float* pm, const float* pc, const float* pp,
+                                           int t, const Phys& p, float& Fx_out, float& Fy_out)
 {
     const float psi = pc[t];
     // Eq. 5: sum_a G_a psi(x+e_a) e_a, axis and diagonal links
@@ -283,9 +327,49 @@ __device__ __forceinline__ void collide_node(const Pulled& n, const float* pm, c
         }
     }
     // body force on every fluid node
-    Fx += n.rho * p.bfx;
-    Fy += n.rho * p.bfy;
+    Fx_out = Fx + n.rho * p.bfx;
+    Fy_out = Fy + n.rho * p.bfy;
+}
 
+// Observables or fields epilogue of one fluid node (modes other than kStep).
+template <int MODE>
+__device__ __forceinline__ void node_observe(float rho, float jx, float jy, float Fx, float Fy,
+                                             const Geom& g, double* __restrict__ fields, int x, int r,
+                                             ObsAcc& acc)
+{
+    // physical velocity u = (rho u + F/2)/rho
+    const float mx = fmaf(0.5f, Fx, jx), my = fmaf(0.5f, Fy, jy);
+    const float vx = __fdiv_rn(mx, rho), vy = __fdiv_rn(my, rho);
+    if constexpr (MODE == kFields) {
+        const size_t i = (size_t)r * g.nx + x, nn = (size_t)g.nx * g.ny;
+        fields[i] = rho;
+        fields[nn + i] = vx;
+        fields[2 * nn + i] = vy;
+    } else {
+        if (isfinite(rho) && isfinite(vx) && isfinite(vy)) {
+            acc.mass.add(rho);
+            acc.q.add(vx);
+            acc.px.add(mx);
+            acc.py.add(my);
+            acc.umax2 = fmaxf(acc.umax2, vx * vx + vy * vy);
+            acc.rmin = fminf(acc.rmin, rho);
+        } else {
+            ++acc.bad;
+        }
+    }
+}
+
+// Forces, velocity shift, collision and the mode's epilogue for one fluid node
+// (x, r) in plain storage, whose pulled populations are `n`; psi rows r-1, r,
+// r+1 are pm, pc, pp (indexed by ring column t = node column - x0 + 1).
+template <int MODE>
+__device__ __forceinline__ void collide_node(const Pulled& n, const float* pm, const float* pc,
+                                             const float* pp, int t, const Phys& p, const Geom& g,
+                                             float* __restrict__ fout, double* __restrict__ fields,
+                                             int x, int r, ObsAcc& acc)
+{
+    float Fx, Fy;
+    node_force(n, pm, pc, pp, t, p, Fx, Fy);
     if constexpr (MODE == kStep || MODE == kStepObs) {
         // Eq. 10 velocity shift, Eq. 3 equilibrium, Eq. 1 relaxation.
         // FP32 care: u' by corrected quotients; the weights w_a rho all derive
@@ -323,42 +407,137 @@ __device__ __forceinline__ void collide_node(const Pulled& n, const float* pm, c
             }
         }
     }
-    if constexpr (MODE != kStep) {
-        // physical velocity u = (rho u + F/2)/rho
-        const float mx = fmaf(0.5f, Fx, n.jx), my = fmaf(0.5f, Fy, n.jy);
-        const float vx = __fdiv_rn(mx, n.rho), vy = __fdiv_rn(my, n.rho);
-        if constexpr (MODE == kFields) {
-            const size_t i = (size_t)r * g.nx + x, nn = (size_t)g.nx * g.ny;
-            fields[i] = n.rho;
-            fields[nn + i] = vx;
-            fields[2 * nn + i] = vy;
-        } else {
-            if (isfinite(n.rho) && isfinite(vx) && isfinite(vy)) {
-                acc.mass.add(n.rho);
-                acc.q.add(vx);
-                acc.px.add(mx);
-                acc.py.add(my);
-                acc.umax2 = fmaxf(acc.umax2, vx * vx + vy * vy);
-                acc.rmin = fminf(acc.rmin, n.rho);
-            } else {
-                ++acc.bad;
-            }
+    if constexpr (MODE != kStep) node_observe<MODE>(n.rho, n.jx, n.jy, Fx, Fy, g, fields, x, r, acc);
+}
+
+// ------------------------------------------------------------------ deviation storage
+
+struct PulledDev {
+    float rho, jx, jy;
+    float g[9];   // f_a - w_a rho (only a = 1..8 are used)
+    uint32_t sb;  // bit a set <=> the pull source x - e_a is solid
+    bool solid;
+};
+
+// Pull in deviation form: s0* are plane-0 rows (rho*) r-1, r, r+1; sd* the
+// same rows' deviation planes 1..8 (plane a at (a-1)*R); c the node column.
+// f_a(x) = w_a rho*(x - e_a) + d_a(x - e_a), or, if x - e_a is solid,
+// f*_opp(a)(x) = w_a rho*(x) + d_opp(a)(x); f_0 = w_0 rho*(x) - sum_b d_b(x).
+template <typename T, int R>
+__device__ __forceinline__ void pull_dev(const float* __restrict__ s0m, const float* __restrict__ s0c,
+                                         const float* __restrict__ s0p, const T* __restrict__ sdm,
+                                         const T* __restrict__ sdc, const T* __restrict__ sdp, int c,
+                                         PulledDev& n)
+{
+    const float r0 = s0c[c];
+    n.solid = is_solid(r0);
+    if (n.solid) {
+        n.rho = n.jx = n.jy = 0.f;
+        n.sb = 0;
+        return;
+    }
+    float rs[9], d[9], own[9];
+    rs[1] = s0c[c - 1];  d[1] = to_f(sdc[0 * R + c - 1]);  // e1: source (x-1, y)
+    rs[2] = s0m[c];      d[2] = to_f(sdm[1 * R + c]);      // e2: source (x, y-1)
+    rs[3] = s0c[c + 1];  d[3] = to_f(sdc[2 * R + c + 1]);  // e3: source (x+1, y)
+    rs[4] = s0p[c];      d[4] = to_f(sdp[3 * R + c]);      // e4: source (x, y+1)
+    rs[5] = s0m[c - 1];  d[5] = to_f(sdm[4 * R + c - 1]);  // e5: source (x-1, y-1)
+    rs[6] = s0m[c + 1];  d[6] = to_f(sdm[5 * R + c + 1]);  // e6: source (x+1, y-1)
+    rs[7] = s0p[c + 1];  d[7] = to_f(sdp[6 * R + c + 1]);  // e7: source (x+1, y+1)
+    rs[8] = s0p[c - 1];  d[8] = to_f(sdp[7 * R + c - 1]);  // e8: source (x-1, y+1)
+#pragma unroll
+    for (int b = 1; b < 9; ++b) own[b] = to_f(sdc[(b - 1) * R + c]);
+    constexpr int opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+    uint32_t sb = 0;
+#pragma unroll
+    for (int a = 1; a < 9; ++a) {
+        if (is_solid(rs[a])) {  // half-way bounce-back: the node's own f*_opp(a)
+            sb |= 1u << a;
+            rs[a] = r0;
+            d[a] = own[opp[a]];
         }
     }
+    constexpr float w1 = 1.f / 9.f, w2 = 1.f / 36.f;
+    // rho - rho*(x) = sum_a w_a (rho*_src - rho*(x)) + sum_a d_a(src) - sum_b d_b(x)
+    const float q1 = ((rs[1] - r0) + (rs[3] - r0)) + ((rs[2] - r0) + (rs[4] - r0));
+    const float q2 = ((rs[5] - r0) + (rs[7] - r0)) + ((rs[6] - r0) + (rs[8] - r0));
+    const float dsrc = ((d[1] + d[3]) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8]));
+    const float down = ((own[1] + own[3]) + (own[2] + own[4])) + ((own[5] + own[7]) + (own[6] + own[8]));
+    const float drho = fmaf(w1, q1, fmaf(w2, q2, dsrc - down));
+    const float rho = r0 + drho;
+    n.rho = rho;
+    n.jx = fmaf(w1, rs[1] - rs[3], fmaf(w2, (rs[5] - rs[7]) + (rs[8] - rs[6]),
+                                        (d[1] - d[3]) + (d[5] - d[7]) + (d[8] - d[6])));
+    n.jy = fmaf(w1, rs[2] - rs[4], fmaf(w2, (rs[5] - rs[7]) + (rs[6] - rs[8]),
+                                        (d[2] - d[4]) + (d[5] - d[7]) + (d[6] - d[8])));
+    // g_a = f_a - w_a rho = w_a ((rho*_src - rho*(x)) - drho) + d_a(src)
+#pragma unroll
+    for (int a = 1; a < 9; ++a) n.g[a] = fmaf(a <= 4 ? w1 : w2, (rs[a] - r0) - drho, d[a]);
+    n.g[0] = 0.f;
+    n.sb = sb;
+}
+
+// Collision in deviation form: stores rho in plane 0 and
+// d*_a = f*_a - w_a rho in planes 1..8 (the equilibrium's deviation part
+// w_a rho (3 c + 4.5 c^2 - 1.5 u^2) is formed without its leading 1).
+template <int MODE, typename T>
+__device__ __forceinline__ void collide_dev(const PulledDev& n, const float* pm, const float* pc,
+                                            const float* pp, int t, const Phys& p, const Geom& g,
+                                            float* __restrict__ fout0, T* __restrict__ foutd,
+                                            double* __restrict__ fields, int x, int r, ObsAcc& acc)
+{
+    float Fx, Fy;
+    node_force(n, pm, pc, pp, t, p, Fx, Fy);
+    if constexpr (MODE == kStep || MODE == kStepObs) {
+        const float rinv = rcp_approx(n.rho);
+        const float ux = div_corrected(fmaf(p.tau, Fx, n.jx), n.rho, rinv);
+        const float uy = div_corrected(fmaf(p.tau, Fy, n.jy), n.rho, rinv);
+        const float usq = 1.5f * fmaf(ux, ux, uy * uy);
+        const float r9 = div_corrected(n.rho, 9.f, 1.f / 9.f);
+        const float w1r = r9, w2r = 0.25f * r9;
+        const float d5 = ux + uy, d6 = uy - ux;
+        auto dpoly = [usq](float c) { return fmaf(c, fmaf(4.5f, c, 3.f), -usq); };
+        float dq[9];
+        dq[1] = w1r * dpoly(ux);
+        dq[2] = w1r * dpoly(uy);
+        dq[3] = w1r * dpoly(-ux);
+        dq[4] = w1r * dpoly(-uy);
+        dq[5] = w2r * dpoly(d5);
+        dq[6] = w2r * dpoly(d6);
+        dq[7] = w2r * dpoly(-d5);
+        dq[8] = w2r * dpoly(-d6);
+        const int o = r * g.pitch + x;
+        fout0[o] = n.rho;
+        if (p.tau == 1.f) {
+#pragma unroll
+            for (int a = 1; a < 9; ++a) foutd[(a - 1) * g.plane + o] = from_f<T>(dq[a]);
+        } else {
+#pragma unroll
+            for (int a = 1; a < 9; ++a)
+                foutd[(a - 1) * g.plane + o] = from_f<T>(fmaf(dq[a] - n.g[a], p.inv_tau, n.g[a]));
+        }
+    }
+    if constexpr (MODE != kStep) node_observe<MODE>(n.rho, n.jx, n.jy, Fx, Fy, g, fields, x, r, acc);
 }
 
 // ------------------------------------------------------------------ kernel
 
-template <int MODE>
+template <int MODE, int ST = kF32>
 __global__ void __launch_bounds__(kThreads, 3)
     step_kernel(const float* __restrict__ fin, float* __restrict__ fout, Geom g, Phys p,
                 double* __restrict__ partials, double* __restrict__ fields, int* __restrict__ err)
 {
+    using T = typename StoreT<ST>::T;
+    constexpr int H = StoreT<ST>::halo;  // staged halo columns per side
+    constexpr int R = row_len<ST>();     // staged columns per plane row
+    constexpr size_t SB = stage_bytes<ST>();
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    float* ring = reinterpret_cast<float*>(smem_raw);                       // [kStages][9][kRowLen]
-    float* psi_ring = ring + size_t(kStages) * 9 * kRowLen;                 // [4][kW + 2]
+    // ring stage s: plane 0 (FP32, R) then planes 1..8 (T, R each)
+    float* psi_ring = reinterpret_cast<float*>(smem_raw + kStages * SB);    // [4][kW + 2]
     uint64_t* full = reinterpret_cast<uint64_t*>(psi_ring + 4 * (kW + 2));  // [kStages]
     uint64_t* empty = full + kStages;                                       // [kStages]
+    auto stage0 = [&](int s) { return reinterpret_cast<float*>(smem_raw + size_t(s) * SB); };
+    auto staged = [&](int s) { return reinterpret_cast<T*>(smem_raw + size_t(s) * SB + R * sizeof(float)); };
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -391,44 +570,86 @@ __global__ void __launch_bounds__(kThreads, 3)
 
     if (warp == kConsumerWarps) {
         // ---------------- producer warp: fill ring stages with rows y0-2 .. y1+1
-        // Interior strips (halos inside [0, nx) and a 16-byte multiple wide)
-        // take one bulk copy per plane row covering columns x0-4 .. x0+nint+4.
-        // Edge and ragged strips copy the aligned body in bulk and fetch the
-        // remaining <= 11 columns per plane with 4-byte cp.async; each lane's
-        // column is fixed for the whole segment.
-        const bool whole = (x0 >= kHalo) && (x0 + nint + kHalo <= g.nx) && ((nint & 3) == 0);
-        const int b_col = whole ? -kHalo : 0;                   // first bulk column (rel. x0)
-        const int b_len = whole ? nint + 2 * kHalo : nbody;     // bulk columns
-        const uint32_t b_bytes = uint32_t(b_len) * sizeof(float);
-        const int n_right = nint + kHalo - nbody;               // columns [x0+nbody, x0+nint+4)
-        const int n_scalar = whole ? 0 : kHalo + n_right;       // <= 11
-        int my_sc = 0, my_gx = 0;
-        const bool has_scalar = lane < n_scalar;
-        if (has_scalar) {
-            const int col = (lane < kHalo) ? (lane - kHalo) : (nbody + (lane - kHalo));
-            my_sc = kHalo + col;
-            my_gx = wrap_x(x0 + col);
-        }
         bool ok = true;
-        for (int k = 0; k < nrows; ++k) {
-            const int s = k % kStages;
-            if (k >= kStages) ok = mbar_wait(&empty[s], ((k / kStages) - 1) & 1, err) && ok;
-            const int row = wrap_y(y0 - 2 + k);
-            float* st = ring + size_t(s) * 9 * kRowLen;
-            const float* src = fin + size_t(row) * g.pitch;
-            if (lane == 0 && b_len > 0) {
-                mbar_expect_tx(&full[s], 9 * b_bytes);
-#pragma unroll 1
-                for (int a = 0; a < 9; ++a)
-                    bulk_g2s(st + a * kRowLen + kHalo + b_col, src + size_t(a) * g.plane + x0 + b_col, b_bytes,
-                             &full[s]);
-            }
+        if constexpr (sizeof(T) == 4) {
+            // FP32 planes. Interior strips (halos inside [0, nx) and a 16-byte
+            // multiple wide) take one bulk copy per plane row covering columns
+            // x0-4 .. x0+nint+4. Edge and ragged strips copy the aligned body in
+            // bulk and fetch the remaining <= 11 columns per plane with 4-byte
+            // cp.async; each lane's column is fixed for the whole segment.
+            const bool whole = (x0 >= H) && (x0 + nint + H <= g.nx) && ((nint & 3) == 0);
+            const int b_col = whole ? -H : 0;                   // first bulk column (rel. x0)
+            const int b_len = whole ? nint + 2 * H : nbody;     // bulk columns
+            const uint32_t b_bytes = uint32_t(b_len) * sizeof(float);
+            const int n_right = nint + H - nbody;               // columns [x0+nbody, x0+nint+4)
+            const int n_scalar = whole ? 0 : H + n_right;       // <= 11
+            int my_sc = 0, my_gx = 0;
+            const bool has_scalar = lane < n_scalar;
             if (has_scalar) {
-#pragma unroll
-                for (int a = 0; a < 9; ++a)
-                    async_g2s_4(st + a * kRowLen + my_sc, src + size_t(a) * g.plane + my_gx);
+                const int col = (lane < H) ? (lane - H) : (nbody + (lane - H));
+                my_sc = H + col;
+                my_gx = wrap_x(x0 + col);
             }
-            async_arrive_noinc(&full[s]);
+            for (int k = 0; k < nrows; ++k) {
+                const int s = k % kStages;
+                if (k >= kStages) ok = mbar_wait(&empty[s], ((k / kStages) - 1) & 1, err) && ok;
+                const int row = wrap_y(y0 - 2 + k);
+                float* st = stage0(s);
+                const float* src = fin + size_t(row) * g.pitch;
+                if (lane == 0 && b_len > 0) {
+                    mbar_expect_tx(&full[s], 9 * b_bytes);
+#pragma unroll 1
+                    for (int a = 0; a < 9; ++a)
+                        bulk_g2s(st + a * R + H + b_col, src + size_t(a) * g.plane + x0 + b_col, b_bytes,
+                                 &full[s]);
+                }
+                if (has_scalar) {
+#pragma unroll
+                    for (int a = 0; a < 9; ++a) async_g2s_4(st + a * R + my_sc, src + size_t(a) * g.plane + my_gx);
+                }
+                async_arrive_noinc(&full[s]);
+            }
+        } else {
+            // 16-bit deviation planes (nx % 8 == 0, so every piece below starts
+            // and ends on a 16-byte boundary): one bulk copy per plane row for
+            // interior strips, else body + left halo + right halo (wrapped).
+            const bool whole = (x0 >= H) && (x0 + nint + H <= g.nx);
+            const uint32_t row_elems = uint32_t(nint + 2 * H);
+            const uint32_t tx = row_elems * uint32_t(sizeof(float) + 8 * sizeof(T));
+            const int xl = wrap_x(x0 - H), xr = wrap_x(x0 + nint);
+            const T* dbase = reinterpret_cast<const T*>(fin + g.plane);
+            for (int k = 0; k < nrows; ++k) {
+                const int s = k % kStages;
+                if (k >= kStages) ok = mbar_wait(&empty[s], ((k / kStages) - 1) & 1, err) && ok;
+                const int row = wrap_y(y0 - 2 + k);
+                if (lane == 0) {
+                    mbar_expect_tx(&full[s], tx);
+                    float* s0 = stage0(s);
+                    T* sd = staged(s);
+                    const float* g0 = fin + size_t(row) * g.pitch;
+                    const T* gd = dbase + size_t(row) * g.pitch;
+                    if (whole) {
+                        bulk_g2s(s0, g0 + x0 - H, row_elems * sizeof(float), &full[s]);
+#pragma unroll 1
+                        for (int a = 1; a < 9; ++a)
+                            bulk_g2s(sd + (a - 1) * R, gd + size_t(a - 1) * g.plane + x0 - H,
+                                     row_elems * sizeof(T), &full[s]);
+                    } else {
+                        bulk_g2s(s0 + H, g0 + x0, nint * sizeof(float), &full[s]);
+                        bulk_g2s(s0, g0 + xl, H * sizeof(float), &full[s]);
+                        bulk_g2s(s0 + H + nint, g0 + xr, H * sizeof(float), &full[s]);
+#pragma unroll 1
+                        for (int a = 1; a < 9; ++a) {
+                            const T* pl = gd + size_t(a - 1) * g.plane;
+                            T* dl = sd + (a - 1) * R;
+                            bulk_g2s(dl + H, pl + x0, nint * sizeof(T), &full[s]);
+                            bulk_g2s(dl, pl + xl, H * sizeof(T), &full[s]);
+                            bulk_g2s(dl + H + nint, pl + xr, H * sizeof(T), &full[s]);
+                        }
+                    }
+                }
+                async_arrive_noinc(&full[s]);
+            }
         }
         // drain: every armed fill has been waited on by the consumers in the
         // normal path; wait (bounded) for the last phase of each stage anyway
@@ -442,38 +663,44 @@ __global__ void __launch_bounds__(kThreads, 3)
     }
 
     // ---------------- consumer warps
+    using PT = std::conditional_t<ST == kF32, Pulled, PulledDev>;
     const int t = tid;                  // column x0 + t
     const bool interior = t < nint;
-    const int c = t + kHalo;            // staged column of this node
+    const int c = t + H;                // staged column of this node
     const int x = x0 + t;
     float* psi_w = psi_ring;            // ring row stride kW + 2, column t + 1
     ObsAcc acc;
-    Pulled cur, nxt;
+    PT cur, nxt;
     bool ok = true;
     // prologue: the two oldest staged rows (y0-2, y0-1) must be present
     ok = mbar_wait(&full[0], 0, err) && ok;
     if (nrows > 1) ok = mbar_wait(&full[1 % kStages], (1 / kStages) & 1, err) && ok;
+
+    auto pull = [&](int sm, int sc, int sp, int col, PT& n) {
+        if constexpr (ST == kF32)
+            pull_smem(stage0(sm), stage0(sc), stage0(sp), col, n);
+        else
+            pull_dev<T, R>(stage0(sm), stage0(sc), stage0(sp), staged(sm), staged(sc), staged(sp), col, n);
+    };
 
     for (int k = 1; k <= nrows - 2; ++k) {
         // pull row r = y0 - 2 + k, which needs staged rows k-1, k, k+1
         const int r = y0 - 2 + k;
         const int kn = k + 1;
         ok = mbar_wait(&full[kn % kStages], (kn / kStages) & 1, err) && ok;
-        const float* sm = ring + size_t((k - 1) % kStages) * 9 * kRowLen;
-        const float* sc = ring + size_t(k % kStages) * 9 * kRowLen;
-        const float* sp = ring + size_t(kn % kStages) * 9 * kRowLen;
+        const int sm = (k - 1) % kStages, sc = k % kStages, sp = kn % kStages;
         float* prow = psi_w + ((r + 4) & 3) * (kW + 2);
         if (interior) {
-            pull_smem(sm, sc, sp, c, nxt);
+            pull(sm, sc, sp, c, nxt);
             prow[t + 1] = pseudopotential(p, nxt);
             if (t == 0) {  // left halo column x0 - 1
-                Pulled h;
-                pull_smem(sm, sc, sp, c - 1, h);
+                PT h;
+                pull(sm, sc, sp, c - 1, h);
                 prow[0] = pseudopotential(p, h);
             }
             if (t == nint - 1) {  // right halo column x0 + nint
-                Pulled h;
-                pull_smem(sm, sc, sp, c + 1, h);
+                PT h;
+                pull(sm, sc, sp, c + 1, h);
                 prow[nint + 1] = pseudopotential(p, h);
             }
         }
@@ -487,7 +714,11 @@ __global__ void __launch_bounds__(kThreads, 3)
             const float* pm = psi_w + ((rc + 3) & 3) * (kW + 2);
             const float* pc = psi_w + ((rc + 4) & 3) * (kW + 2);
             const float* pp = psi_w + ((rc + 5) & 3) * (kW + 2);
-            collide_node<MODE>(cur, pm, pc, pp, t + 1, p, g, fout, fields, x, rc, acc);
+            if constexpr (ST == kF32)
+                collide_node<MODE>(cur, pm, pc, pp, t + 1, p, g, fout, fields, x, rc, acc);
+            else
+                collide_dev<MODE, T>(cur, pm, pc, pp, t + 1, p, g, fout, reinterpret_cast<T*>(fout + g.plane),
+                                     fields, x, rc, acc);
         } else if constexpr (MODE == kFields) {
             if (k >= 3 && interior) {
                 const size_t i = (size_t)(r - 1) * g.nx + x, nn = (size_t)g.nx * g.ny;

@@ -23,7 +23,7 @@ from . import build as _build
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENAN, LBM_ETIMEOUT, LBM_ESTATE = range(7)
 LBM_GREEN_MC, LBM_GREEN_PRINTED = 0, 1
-LBM_FP32 = 0
+LBM_FP32, LBM_FP32_DEV, LBM_FP16_DEV, LBM_BF16_DEV = 0, 1, 2, 3
 LBM_RHO_U, LBM_POPS = 0, 1
 
 

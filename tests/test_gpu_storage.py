@@ -1,0 +1,112 @@
+"""Population storage forms against the FP64 oracle (the precision study).
+
+LBM_FP32_DEV stores rho* and the FP32 deviations d_a = f*_a - w_a rho*; it
+meets the same population gates as plain FP32 storage. LBM_FP16_DEV and
+LBM_BF16_DEV keep d_a in 16 bits; for them the error against the oracle is
+measured for every observable and held to the stated bounds below (about
+twice the values measured on a GB300).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0708_4182_gb300 import workloads as wl
+from tests.test_gpu_parity import assert_pops, check_obs, pop_err, run_both
+
+pytestmark = pytest.mark.gpu
+
+# stated bounds for the 16-bit forms after 100 steps:
+# (relative L2 of populations, relative mass error, |dQ| / sum|u_x|/nx, rel. max|u|)
+BOUNDS16 = {
+    "fp16": (3e-4, 2e-5, 5e-3, 5e-3),
+    "bf16": (3e-3, 2e-4, 5e-2, 5e-2),
+}
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0708_4182_gb300 import lbm as L
+    L.load()
+    return L
+
+
+CASES = [
+    ("droplet f=0", lambda: wl.droplet_128x64(0.0)),
+    ("droplet f=0.25", lambda: wl.droplet_128x64(0.25)),
+    ("rough channel", lambda: wl.rough_channel(nx=304, ny=48, amp=6, level=12, seed=5, body_fx=1e-5)),
+]
+
+
+@pytest.mark.parametrize("name,make", CASES)
+def test_fp32_deviation_storage_meets_population_gates(lbm, name, make):
+    w = make()
+    p, f_ref, lat = run_both(lbm, w.mask, w.rho, w.params, 100, storage=lbm.LBM_FP32_DEV)
+    assert_pops(lat.populations(), f_ref, w.mask)
+    check_obs(lat, p, w.mask, f_ref)
+
+
+def test_fp32_deviation_storage_tau_not_one(lbm):
+    w = wl.droplet_128x64(0.15)
+    params = dict(w.params, tau=0.95)
+    p, f_ref, lat = run_both(lbm, w.mask, w.rho, params, 100, storage=lbm.LBM_FP32_DEV)
+    assert_pops(lat.populations(), f_ref, w.mask)
+
+
+@pytest.mark.parametrize("form", ["fp16", "bf16"])
+@pytest.mark.parametrize("name,make", CASES)
+def test_16bit_storage_errors_within_stated_bounds(lbm, form, name, make):
+    w = make()
+    storage = lbm.LBM_FP16_DEV if form == "fp16" else lbm.LBM_BF16_DEV
+    p, f_ref, lat = run_both(lbm, w.mask, w.rho, w.params, 100, storage=storage)
+    _, _, l2 = pop_err(lat.populations(), f_ref, w.mask)
+    o = lat.observables()
+    r = oracle.observables(p, w.mask, f_ref)
+    _, ux, _ = oracle.fields(p, w.mask, f_ref)
+    q_scale = np.abs(ux[w.mask == 0]).sum() / p.nx
+    errs = (l2, abs(o["mass"] / r["mass"] - 1), abs(o["flux_Q"] - r["flux_Q"]) / q_scale,
+            abs(o["max_u"] / r["max_u"] - 1))
+    print(f"{form} {name}: L2 {errs[0]:.2e} mass {errs[1]:.2e} Q {errs[2]:.2e} max_u {errs[3]:.2e}")
+    for e, b in zip(errs, BOUNDS16[form]):
+        assert e <= b, (form, name, errs)
+
+
+@pytest.mark.parametrize("storage", [1, 2, 3])
+def test_deviation_storage_round_trip_and_tiling(lbm, storage):
+    w = wl.rough_channel(nx=304, ny=48, amp=6, level=15, seed=9, body_fx=1e-5)
+    p = oracle.Params(w.nx, w.ny, **w.params)
+    f0 = oracle.step(p, w.mask, oracle.equilibrium(p, w.mask, w.rho, 0, 0), 20)
+    outs = []
+    for tr in (4, 16, 0):
+        lat = lbm.Lattice(w.nx, w.ny, storage=storage, tile_rows=tr, **w.params)
+        lat.set_geometry(w.mask)
+        lat.set_populations(f0)
+        if tr == 4:
+            back = lat.populations()
+            tol = 1e-6 if storage == 1 else (2e-3 if storage == 2 else 2e-2)
+            _, _, l2 = pop_err(back, f0, w.mask)
+            assert l2 <= tol
+        lat.step(25)
+        outs.append(lat.populations())
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+
+
+@pytest.mark.parametrize("storage", [1, 2, 3])
+def test_deviation_storage_conserves_mass(lbm, storage):
+    w = wl.rough_channel(nx=304, ny=48, amp=6, level=12, seed=5, body_fx=1e-5)
+    lat = lbm.Lattice(w.nx, w.ny, storage=storage, **w.params)
+    lat.set_geometry(w.mask)
+    lat.set_rho_u(w.rho)
+    m0 = lat.observables()["mass"]
+    lat.step(1000)
+    o = lat.observables()
+    assert o["nonfinite"] == 0
+    assert abs(o["mass"] / m0 - 1) <= 1e-5
+
+
+def test_16bit_storage_rejects_ragged_width(lbm):
+    assert lbm.lbm_workspace_bytes(lbm.make_params(300, 48, storage=lbm.LBM_FP16_DEV)) == 0
+    assert lbm.lbm_workspace_bytes(lbm.make_params(304, 48, storage=lbm.LBM_FP16_DEV)) > 0
