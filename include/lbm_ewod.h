@@ -60,7 +60,8 @@ typedef enum {
     LBM_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed */
     LBM_ENAN = 4,     /* observables found non-finite density or velocity */
     LBM_ETIMEOUT = 5, /* a bounded device-side wait gave up */
-    LBM_ESTATE = 6    /* call out of order (e.g. step before geometry and field) */
+    LBM_ESTATE = 6,   /* call out of order (e.g. step before geometry and field) */
+    LBM_ENOTCONV = 7  /* lbm_run_to_steady reached max_steps before the criterion */
 } lbm_status;
 
 /* Green-function magnitudes for Eq. 4-6. LBM_GREEN_MC (the default) uses
@@ -158,6 +159,16 @@ lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps);
  * LBM_ENAN (with *out filled) if any fluid node is non-finite. */
 lbm_status lbm_observables(lbm_ctx *ctx, lbm_obs *out);
 
+/* Step until the flux of Eq. 11 is steady: every check_every steps compute
+ * Q (an observables pass) and stop once |Q(t) - Q(t - check_every)| <=
+ * rel_tol * |Q(t)|, or after max_steps more steps. *out receives the
+ * observables of the last check (out->step is the time index reached).
+ * Returns LBM_OK when the criterion was met, LBM_ENOTCONV when max_steps ran
+ * out first (with *out filled), LBM_ENAN as lbm_observables, LBM_EINVAL for
+ * check_every < 1 or rel_tol < 0. Synchronises the stream at every check. */
+lbm_status lbm_run_to_steady(lbm_ctx *ctx, double rel_tol, int64_t check_every, int64_t max_steps,
+                             lbm_obs *out);
+
 /* The most recent observables fused into lbm_step (params.obs_every > 0):
  * those of the last state t < current time with t % obs_every == 0.
  * Synchronises the stream. LBM_ESTATE if none has been recorded yet;
@@ -176,6 +187,65 @@ const char *lbm_status_string(int status);
 /* Destroy a context. Frees only what the library allocated (host-side
  * bookkeeping); the caller's workspace is untouched. NULL is a no-op. */
 void lbm_destroy(lbm_ctx *ctx);
+
+/* ------------------------------------------------------------------------
+ * Batches: many domains (different sizes, geometries and forces, one
+ * storage form) advanced together, one persistent kernel launch per step.
+ * Not in the paper, which runs its sweeps (over f and channel width) one
+ * domain at a time; a batch runs such a sweep as one job.
+ */
+typedef struct lbm_batch lbm_batch;
+
+/* Device workspace for count domains with parameters params[0..count-1]
+ * (0 if any parameter set is invalid or the storage forms differ). */
+size_t lbm_batch_workspace_bytes(const lbm_params *params, int32_t count);
+
+/* Create a batch in the caller's workspace (256-byte aligned, owned by the
+ * caller, kept alive until lbm_batch_destroy). Every domain gets an ordinary
+ * context carved from it; fetch it with lbm_batch_domain and use the
+ * single-domain calls (lbm_set_geometry, lbm_set_field, lbm_get_field,
+ * lbm_observables, ...) on it. */
+lbm_status lbm_batch_create(const lbm_params *params, int32_t count, void *d_workspace, size_t bytes,
+                            void *cuda_stream, lbm_batch **out);
+
+/* The context of domain i (owned by the batch; NULL if i is out of range). */
+lbm_ctx *lbm_batch_domain(lbm_batch *b, int32_t i);
+
+/* Advance every active domain by nsteps. Each step is one launch of a
+ * persistent kernel whose CTAs walk a tile list (domain, strip, row segment)
+ * covering all active domains; pairs of steps run as one CUDA graph. */
+lbm_status lbm_batch_step(lbm_batch *b, int64_t nsteps);
+
+/* Observables of every domain (one batched pass), out[count]. */
+lbm_status lbm_batch_observables(lbm_batch *b, lbm_obs *out);
+
+/* active[count]: nonzero = stepped by lbm_batch_step (all start active). */
+lbm_status lbm_batch_set_active(lbm_batch *b, const uint8_t *active);
+
+/* Row-segment height of the tiles (>= 4; 0 = each domain's own default). */
+lbm_status lbm_batch_set_tile_rows(lbm_batch *b, int32_t rows);
+int32_t lbm_batch_tile_rows(const lbm_batch *b);
+
+/* Time candidates[0..n-1] as tile heights over `steps` steps each (after 2
+ * warm-up steps) with CUDA events, keep the fastest (*chosen) and report
+ * ms_per_step[n] (may be NULL). Advances every active domain by
+ * n * (steps + 2) steps. */
+lbm_status lbm_batch_autotune(lbm_batch *b, const int32_t *candidates, int32_t n, int32_t steps,
+                              int32_t *chosen, double *ms_per_step);
+
+/* Step the active domains until each one's flux is steady (criterion as in
+ * lbm_run_to_steady, checked every check_every steps); a domain stops being
+ * stepped once it is steady. steps_to_steady[count] gets each domain's time
+ * index at convergence (-1 if inactive or not converged), out[count] its
+ * last observables. LBM_ENOTCONV if some active domain did not converge
+ * within max_steps. The caller's active set is restored on return. */
+lbm_status lbm_batch_run_to_steady(lbm_batch *b, double rel_tol, int64_t check_every, int64_t max_steps,
+                                   int64_t *steps_to_steady, lbm_obs *out);
+
+const char *lbm_batch_last_error(const lbm_batch *b);
+
+/* Destroy the batch and its domain contexts (not the caller's workspace). */
+void lbm_batch_destroy(lbm_batch *b);
 
 /* Observables without a context and without any allocation. The paper has
  * no counterpart to this entry point: it exists for callers that cannot

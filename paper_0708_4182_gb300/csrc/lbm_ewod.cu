@@ -20,6 +20,8 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <algorithm>
+#include <vector>
 
 namespace lbm {
 namespace {
@@ -319,6 +321,52 @@ int aux_blocks(long long n, int sm_count)
     long long b = (n + kAuxThreads - 1) / kAuxThreads;
     const long long cap = 32LL * sm_count;
     return int(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+// One CTA per domain: sum domain d's nctas[d] partials in a fixed order into
+// rec[d]; domains with want[d] == 0 are skipped.
+__global__ void finalize_batch_kernel(double* const* __restrict__ partials, const int* __restrict__ nctas,
+                                      const double* __restrict__ inv_nx, const long long* __restrict__ step,
+                                      const unsigned char* __restrict__ want, lbm_obs* __restrict__ rec)
+{
+    const int d = blockIdx.x;
+    if (!want[d]) return;
+    __shared__ double s[4][kAuxThreads];
+    __shared__ double mx[kAuxThreads], mn[kAuxThreads], bd[kAuxThreads];
+    const int t = threadIdx.x;
+    double a[4] = {0, 0, 0, 0}, um = 0.0, rm = INFINITY, b = 0.0;
+    for (int c = t; c < nctas[d]; c += kAuxThreads) {
+        const double* q = partials[d] + (size_t)c * kPartialStride;
+        for (int k = 0; k < 4; ++k) a[k] += q[k];
+        um = fmax(um, q[4]);
+        rm = fmin(rm, q[5]);
+        b += q[6];
+    }
+    for (int k = 0; k < 4; ++k) s[k][t] = a[k];
+    mx[t] = um;
+    mn[t] = rm;
+    bd[t] = b;
+    __syncthreads();
+    for (int h = kAuxThreads / 2; h > 0; h >>= 1) {
+        if (t < h) {
+            for (int k = 0; k < 4; ++k) s[k][t] += s[k][t + h];
+            mx[t] = fmax(mx[t], mx[t + h]);
+            mn[t] = fmin(mn[t], mn[t + h]);
+            bd[t] += bd[t + h];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        lbm_obs& r = rec[d];
+        r.step = step[d];
+        r.mass = s[0][0];
+        r.flux_Q = s[1][0] * inv_nx[d];
+        r.mom_x = s[2][0];
+        r.mom_y = s[3][0];
+        r.max_u = sqrt(mx[0]);
+        r.min_rho = mn[0];
+        r.nonfinite = (long long)bd[0];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -828,6 +876,29 @@ lbm_status lbm_observables(lbm_ctx* c, lbm_obs* out)
     return read_record(c, rec, out);
 }
 
+lbm_status lbm_run_to_steady(lbm_ctx* c, double rel_tol, int64_t check_every, int64_t max_steps,
+                             lbm_obs* out)
+{
+    lbm_status s = ready(c);
+    if (s) return s;
+    if (!out) return fail(c, LBM_EINVAL, "output is NULL");
+    if (check_every < 1 || !(rel_tol >= 0.0) || max_steps < 0)
+        return fail(c, LBM_EINVAL, "need check_every >= 1, rel_tol >= 0, max_steps >= 0");
+    bool have_prev = false;
+    double q_prev = 0.0;
+    for (int64_t done = 0; done < max_steps;) {
+        const int64_t n = (max_steps - done < check_every) ? max_steps - done : check_every;
+        if ((s = lbm_step(c, n))) return s;
+        done += n;
+        if ((s = lbm_observables(c, out))) return s;
+        const double q = out->flux_Q;
+        if (have_prev && n == check_every && std::fabs(q - q_prev) <= rel_tol * std::fabs(q)) return LBM_OK;
+        q_prev = q;
+        have_prev = true;
+    }
+    return fail(c, LBM_ENOTCONV, "flux not steady after %lld steps", (long long)max_steps);
+}
+
 lbm_status lbm_obs_latest(lbm_ctx* c, lbm_obs* out)
 {
     lbm_status s = ready(c);
@@ -851,6 +922,7 @@ const char* lbm_status_string(int s)
     case LBM_ENAN: return "LBM_ENAN";
     case LBM_ETIMEOUT: return "LBM_ETIMEOUT";
     case LBM_ESTATE: return "LBM_ESTATE";
+    case LBM_ENOTCONV: return "LBM_ENOTCONV";
     default: return "unknown status";
     }
 }
@@ -934,5 +1006,499 @@ lbm_status lbm_observables_noalloc(const lbm_params* p, const double* d_pops, co
 }
 
 const char* lbm_noalloc_last_error(void) { return g_noalloc_err; }
+
+}  // extern "C"
+
+
+// ===========================================================================
+// Batches: many domains of different sizes stepped by one launch per step.
+
+struct lbm_batch {
+    int count = 0;
+    int storage = 0;
+    std::vector<lbm_ctx*> ctx;
+    std::vector<unsigned char> active;   // host flags
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    int tile_rows = 0;                   // 0 = each domain's own choice
+    // device tables (in the batch's own workspace region)
+    DomainDev* d_dom = nullptr;
+    int4* d_tiles = nullptr;
+    int* d_status = nullptr;
+    lbm_obs* d_rec = nullptr;
+    double** d_partials = nullptr;
+    int* d_nctas = nullptr;
+    double* d_inv_nx = nullptr;
+    long long* d_step = nullptr;
+    unsigned char* d_want = nullptr;
+    int max_tiles = 0;
+    // host mirrors
+    std::vector<DomainDev> h_dom;
+    std::vector<int4> h_tiles;
+    int ntiles = 0;
+    bool tiles_dirty = true;
+    int tiles_for_all = -1;              // 1 if h_tiles covers every domain
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int graph_ntiles = -1, graph_grid = -1;
+    char err[512] = {0};
+};
+
+namespace {
+
+lbm_status bfail(lbm_batch* b, lbm_status s, const char* fmt, ...)
+{
+    if (b) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(b->err, sizeof(b->err), fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+lbm_status bcheck(lbm_batch* b, cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) return LBM_OK;
+    return bfail(b, LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+struct BatchLayout {
+    std::vector<size_t> off;  // per-domain workspace offsets
+    size_t off_dom, off_tiles, off_status, off_rec, off_ptrs, off_nctas, off_invnx, off_step, off_want, total;
+    int max_tiles;
+};
+
+bool batch_layout(const lbm_params* p, int count, BatchLayout* L, const char** why)
+{
+    if (!p || count < 1) { *why = "need at least one domain"; return false; }
+    size_t o = 0;
+    L->off.resize(count);
+    L->max_tiles = 0;
+    for (int i = 0; i < count; ++i) {
+        if (!params_valid(&p[i], why)) return false;
+        if (p[i].storage != p[0].storage) { *why = "all domains of a batch share one storage form"; return false; }
+        L->off[i] = o;
+        o = align_up(o + layout_of(&p[i]).total, 256);
+        L->max_tiles += ctas_x(p[i].nx) * ((p[i].ny + 3) / 4);
+    }
+    L->off_dom = o; o = align_up(o + count * sizeof(DomainDev), 256);
+    L->off_tiles = o; o = align_up(o + size_t(L->max_tiles) * sizeof(int4), 256);
+    L->off_status = o; o = align_up(o + sizeof(int), 256);
+    L->off_rec = o; o = align_up(o + count * sizeof(lbm_obs), 256);
+    L->off_ptrs = o; o = align_up(o + count * sizeof(double*), 256);
+    L->off_nctas = o; o = align_up(o + count * sizeof(int), 256);
+    L->off_invnx = o; o = align_up(o + count * sizeof(double), 256);
+    L->off_step = o; o = align_up(o + count * sizeof(long long), 256);
+    L->off_want = o; o = align_up(o + count, 256);
+    L->total = o;
+    return true;
+}
+
+int domain_tile_rows(const lbm_batch* b, const lbm_ctx* c) { return b->tile_rows ? b->tile_rows : c->g.tile_rows; }
+
+// Tile list of the active domains (or of all domains), largest domains first
+// so that the strided walk of the persistent grid ends evenly.
+void build_tiles(lbm_batch* b, bool all)
+{
+    std::vector<int> order;
+    for (int d = 0; d < b->count; ++d)
+        if (all || b->active[d]) order.push_back(d);
+    std::sort(order.begin(), order.end(), [&](int x, int y) {
+        return (long long)b->ctx[x]->g.nx * b->ctx[x]->g.ny > (long long)b->ctx[y]->g.nx * b->ctx[y]->g.ny;
+    });
+    b->h_tiles.clear();
+    for (int d : order) {
+        const lbm_ctx* c = b->ctx[d];
+        const int rows = domain_tile_rows(b, c);
+        const int tx = ctas_x(c->g.nx), ty = (c->g.ny + rows - 1) / rows;
+        for (int by = 0; by < ty; ++by)
+            for (int bx = 0; bx < tx; ++bx) b->h_tiles.push_back(make_int4(d, bx, by, by * tx + bx));
+    }
+    b->ntiles = int(b->h_tiles.size());
+    b->tiles_for_all = all ? 1 : 0;
+}
+
+lbm_status upload_tables(lbm_batch* b, bool all)
+{
+    for (int d = 0; d < b->count; ++d) {
+        lbm_ctx* c = b->ctx[d];
+        DomainDev& dd = b->h_dom[d];
+        dd.g = c->g;
+        dd.g.tile_rows = domain_tile_rows(b, c);
+        dd.p = c->ph;
+        dd.buf[0] = c->cur;
+        dd.buf[1] = c->nxt;
+        dd.partials = c->partials;
+    }
+    lbm_status s = bcheck(b, cudaMemcpyAsync(b->d_dom, b->h_dom.data(), b->count * sizeof(DomainDev),
+                                             cudaMemcpyHostToDevice, b->stream), "domain table upload");
+    if (s) return s;
+    if (b->tiles_dirty || b->tiles_for_all != (all ? 1 : 0)) {
+        build_tiles(b, all);
+        if (b->ntiles > 0 &&
+            (s = bcheck(b, cudaMemcpyAsync(b->d_tiles, b->h_tiles.data(), b->ntiles * sizeof(int4),
+                                           cudaMemcpyHostToDevice, b->stream), "tile list upload")))
+            return s;
+        b->tiles_dirty = false;  // tiles_for_all records which list is on the device
+    }
+    // pageable H2D copies return once the host buffers are consumed; the
+    // kernels that read the tables follow on the same stream
+    return LBM_OK;
+}
+
+template <int ST>
+const void* batch_kernel_ptr(int mode)
+{
+    switch (mode) {
+    case kObs: return reinterpret_cast<const void*>(&batch_step_kernel<kObs, ST>);
+    default: return reinterpret_cast<const void*>(&batch_step_kernel<kStep, ST>);
+    }
+}
+
+const void* batch_kernel(int storage, int mode)
+{
+    switch (storage) {
+    case LBM_FP32_DEV: return batch_kernel_ptr<kF32Dev>(mode);
+    case LBM_FP16_DEV: return batch_kernel_ptr<kF16Dev>(mode);
+    case LBM_BF16_DEV: return batch_kernel_ptr<kBF16Dev>(mode);
+    default: return batch_kernel_ptr<kF32>(mode);
+    }
+}
+
+size_t batch_smem(int storage)
+{
+    switch (storage) {
+    case LBM_FP32_DEV: return smem_bytes<kF32Dev>();
+    case LBM_FP16_DEV: return smem_bytes<kF16Dev>();
+    case LBM_BF16_DEV: return smem_bytes<kBF16Dev>();
+    default: return smem_bytes<kF32>();
+    }
+}
+
+int batch_grid(const lbm_batch* b) { return b->ntiles < 3 * b->sm_count ? b->ntiles : 3 * b->sm_count; }
+
+lbm_status launch_batch(lbm_batch* b, int mode, int parity)
+{
+    if (b->ntiles == 0) return LBM_OK;
+    int nt = b->ntiles;
+    void* args[] = {&b->d_dom, &b->d_tiles, &nt, &parity, &b->d_status};
+    return bcheck(b, cudaLaunchKernel(batch_kernel(b->storage, mode), dim3(batch_grid(b)), dim3(kThreads), args,
+                                      batch_smem(b->storage), b->stream),
+                  "batch step launch");
+}
+
+// Two steps (parity 0 then 1) as one explicitly built graph; rebuilt when
+// the tile list or grid changes.
+lbm_status batch_graph(lbm_batch* b)
+{
+    const int grid = batch_grid(b);
+    if (b->exec && b->graph_ntiles == b->ntiles && b->graph_grid == grid) return LBM_OK;
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    lbm_status s = bcheck(b, cudaGraphCreate(&b->graph, 0), "graph create");
+    if (s) return s;
+    static int parities[2] = {0, 1};
+    int nt = b->ntiles;
+    cudaGraphNode_t prev = nullptr;
+    for (int k = 0; k < 2; ++k) {
+        void* args[] = {&b->d_dom, &b->d_tiles, &nt, &parities[k], &b->d_status};
+        cudaKernelNodeParams kp{};
+        kp.func = const_cast<void*>(batch_kernel(b->storage, kStep));
+        kp.gridDim = dim3(grid);
+        kp.blockDim = dim3(kThreads);
+        kp.sharedMemBytes = unsigned(batch_smem(b->storage));
+        kp.kernelParams = args;
+        cudaGraphNode_t node;
+        if ((s = bcheck(b, cudaGraphAddKernelNode(&node, b->graph, prev ? &prev : nullptr, prev ? 1 : 0, &kp),
+                        "graph node")))
+            return s;
+        prev = node;
+    }
+    if ((s = bcheck(b, cudaGraphInstantiate(&b->exec, b->graph, 0), "graph instantiate"))) return s;
+    b->graph_ntiles = b->ntiles;
+    b->graph_grid = grid;
+    return LBM_OK;
+}
+
+lbm_status batch_ready(lbm_batch* b)
+{
+    if (!b) return LBM_EINVAL;
+    for (int d = 0; d < b->count; ++d)
+        if (b->active[d] && (!b->ctx[d]->has_geometry || !b->ctx[d]->has_field))
+            return bfail(b, LBM_ESTATE, "domain %d has no geometry or field yet", d);
+    return LBM_OK;
+}
+
+lbm_status batch_check_status(lbm_batch* b)
+{
+    int flag = 0;
+    lbm_status s = bcheck(b, cudaMemcpy(&flag, b->d_status, sizeof(int), cudaMemcpyDeviceToHost), "status download");
+    if (s) return s;
+    if (flag) {
+        cudaMemset(b->d_status, 0, sizeof(int));
+        return bfail(b, LBM_ETIMEOUT, "a bounded device-side wait gave up (flag %d)", flag);
+    }
+    return LBM_OK;
+}
+
+// Observables of the domains with want[d] into rec (device) and out (host);
+// the pass covers every domain (all) or only the active ones.
+lbm_status batch_observe(lbm_batch* b, const std::vector<unsigned char>& want, lbm_obs* out, bool all)
+{
+    lbm_status s = upload_tables(b, all);
+    if (s) return s;
+    if ((s = launch_batch(b, kObs, 0))) return s;
+    std::vector<double*> parts(b->count);
+    std::vector<int> nct(b->count);
+    std::vector<double> invnx(b->count);
+    std::vector<long long> steps(b->count);
+    for (int d = 0; d < b->count; ++d) {
+        const lbm_ctx* c = b->ctx[d];
+        const int rows = domain_tile_rows(b, c);
+        parts[d] = c->partials;
+        nct[d] = ctas_x(c->g.nx) * ((c->g.ny + rows - 1) / rows);
+        invnx[d] = 1.0 / c->g.nx;
+        steps[d] = c->t;
+    }
+    cudaStream_t st = b->stream;
+    if ((s = bcheck(b, cudaMemcpyAsync(b->d_partials, parts.data(), b->count * sizeof(double*), cudaMemcpyHostToDevice, st), "upload")) ||
+        (s = bcheck(b, cudaMemcpyAsync(b->d_nctas, nct.data(), b->count * sizeof(int), cudaMemcpyHostToDevice, st), "upload")) ||
+        (s = bcheck(b, cudaMemcpyAsync(b->d_inv_nx, invnx.data(), b->count * sizeof(double), cudaMemcpyHostToDevice, st), "upload")) ||
+        (s = bcheck(b, cudaMemcpyAsync(b->d_step, steps.data(), b->count * sizeof(long long), cudaMemcpyHostToDevice, st), "upload")) ||
+        (s = bcheck(b, cudaMemcpyAsync(b->d_want, want.data(), b->count, cudaMemcpyHostToDevice, st), "upload")))
+        return s;
+    finalize_batch_kernel<<<b->count, kAuxThreads, 0, st>>>(b->d_partials, b->d_nctas, b->d_inv_nx, b->d_step,
+                                                            b->d_want, b->d_rec);
+    if ((s = bcheck(b, cudaGetLastError(), "finalize launch"))) return s;
+    if ((s = bcheck(b, cudaMemcpyAsync(out, b->d_rec, b->count * sizeof(lbm_obs), cudaMemcpyDeviceToHost, st),
+                    "observables download")))
+        return s;
+    if ((s = bcheck(b, cudaStreamSynchronize(st), "observables sync"))) return s;
+    return batch_check_status(b);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lbm_batch_workspace_bytes(const lbm_params* params, int32_t count)
+{
+    BatchLayout L;
+    const char* why;
+    if (!batch_layout(params, count, &L, &why)) return 0;
+    return L.total;
+}
+
+lbm_status lbm_batch_create(const lbm_params* params, int32_t count, void* d_workspace, size_t bytes,
+                            void* cuda_stream, lbm_batch** out)
+{
+    if (!out) return LBM_EINVAL;
+    *out = nullptr;
+    BatchLayout L;
+    const char* why = "";
+    if (!batch_layout(params, count, &L, &why)) return LBM_EINVAL;
+    if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) & 255u)) return LBM_EINVAL;
+    if (bytes < L.total) return LBM_ENOMEM;
+    lbm_batch* b = new (std::nothrow) lbm_batch;
+    if (!b) return LBM_ENOMEM;
+    unsigned char* ws = static_cast<unsigned char*>(d_workspace);
+    b->count = count;
+    b->storage = params[0].storage;
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    b->ctx.assign(count, nullptr);
+    b->active.assign(count, 1);
+    b->h_dom.resize(count);
+    for (int d = 0; d < count; ++d) {
+        const size_t need = layout_of(&params[d]).total;
+        lbm_status s = lbm_create(&params[d], ws + L.off[d], need, cuda_stream, &b->ctx[d]);
+        if (s) {
+            for (int e = 0; e < d; ++e) lbm_destroy(b->ctx[e]);
+            delete b;
+            return s;
+        }
+    }
+    b->sm_count = b->ctx[0]->sm_count;
+    b->d_dom = reinterpret_cast<DomainDev*>(ws + L.off_dom);
+    b->d_tiles = reinterpret_cast<int4*>(ws + L.off_tiles);
+    b->d_status = reinterpret_cast<int*>(ws + L.off_status);
+    b->d_rec = reinterpret_cast<lbm_obs*>(ws + L.off_rec);
+    b->d_partials = reinterpret_cast<double**>(ws + L.off_ptrs);
+    b->d_nctas = reinterpret_cast<int*>(ws + L.off_nctas);
+    b->d_inv_nx = reinterpret_cast<double*>(ws + L.off_invnx);
+    b->d_step = reinterpret_cast<long long*>(ws + L.off_step);
+    b->d_want = ws + L.off_want;
+    b->max_tiles = L.max_tiles;
+    cudaError_t e = cudaSuccess;
+    for (int st = 0; st < 4 && e == cudaSuccess; ++st) {
+        e = cudaFuncSetAttribute(batch_kernel(st, kStep), cudaFuncAttributeMaxDynamicSharedMemorySize, int(batch_smem(st)));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(batch_kernel(st, kObs), cudaFuncAttributeMaxDynamicSharedMemorySize, int(batch_smem(st)));
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        for (int d = 0; d < count; ++d) lbm_destroy(b->ctx[d]);
+        delete b;
+        return LBM_ECUDA;
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+lbm_ctx* lbm_batch_domain(lbm_batch* b, int32_t i)
+{
+    if (!b || i < 0 || i >= b->count) return nullptr;
+    return b->ctx[i];
+}
+
+lbm_status lbm_batch_set_active(lbm_batch* b, const uint8_t* active)
+{
+    if (!b || !active) return LBM_EINVAL;
+    for (int d = 0; d < b->count; ++d) b->active[d] = active[d] ? 1 : 0;
+    b->tiles_dirty = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_tile_rows(lbm_batch* b, int32_t rows)
+{
+    if (!b) return LBM_EINVAL;
+    if (rows != 0 && rows < 4) return bfail(b, LBM_EINVAL, "tile rows must be 0 or >= 4");
+    b->tile_rows = rows;
+    b->tiles_dirty = true;
+    return LBM_OK;
+}
+
+int32_t lbm_batch_tile_rows(const lbm_batch* b) { return b ? b->tile_rows : -1; }
+
+lbm_status lbm_batch_step(lbm_batch* b, int64_t nsteps)
+{
+    lbm_status s = batch_ready(b);
+    if (s) return s;
+    if (nsteps < 0) return bfail(b, LBM_EINVAL, "nsteps must be >= 0");
+    if (nsteps == 0) return LBM_OK;
+    if ((s = upload_tables(b, false))) return s;
+    if (b->ntiles == 0) return LBM_OK;
+    if ((s = batch_graph(b))) return s;
+    for (int64_t k = 0; k + 1 < nsteps; k += 2)
+        if ((s = bcheck(b, cudaGraphLaunch(b->exec, b->stream), "graph launch"))) return s;
+    if (nsteps & 1)
+        if ((s = launch_batch(b, kStep, 0))) return s;
+    for (int d = 0; d < b->count; ++d) {
+        if (!b->active[d]) continue;
+        lbm_ctx* c = b->ctx[d];
+        c->t += nsteps;
+        if (nsteps & 1) {
+            float* tmp = c->cur;
+            c->cur = c->nxt;
+            c->nxt = tmp;
+        }
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_observables(lbm_batch* b, lbm_obs* out)
+{
+    if (!b || !out) return LBM_EINVAL;
+    for (int d = 0; d < b->count; ++d)
+        if (!b->ctx[d]->has_geometry || !b->ctx[d]->has_field)
+            return bfail(b, LBM_ESTATE, "domain %d has no geometry or field yet", d);
+    std::vector<unsigned char> want(b->count, 1);
+    lbm_status s = batch_observe(b, want, out, true);
+    if (s) return s;
+    for (int d = 0; d < b->count; ++d)
+        if (out[d].nonfinite > 0) return bfail(b, LBM_ENAN, "domain %d has %lld non-finite nodes", d, (long long)out[d].nonfinite);
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_run_to_steady(lbm_batch* b, double rel_tol, int64_t check_every, int64_t max_steps,
+                                   int64_t* steps_to_steady, lbm_obs* out)
+{
+    lbm_status s = batch_ready(b);
+    if (s) return s;
+    if (!steps_to_steady || !out || check_every < 1 || !(rel_tol >= 0.0) || max_steps < 0)
+        return bfail(b, LBM_EINVAL, "bad arguments");
+    std::vector<double> q_prev(b->count, 0.0);
+    std::vector<unsigned char> have_prev(b->count, 0);
+    std::vector<unsigned char> start_active = b->active;
+    for (int d = 0; d < b->count; ++d) steps_to_steady[d] = -1;
+    std::vector<lbm_obs> rec(b->count);
+    for (int64_t done = 0; done < max_steps;) {
+        bool any = false;
+        for (int d = 0; d < b->count; ++d) any = any || b->active[d];
+        if (!any) break;
+        const int64_t n = (max_steps - done < check_every) ? max_steps - done : check_every;
+        if ((s = lbm_batch_step(b, n))) return s;
+        done += n;
+        std::vector<unsigned char> want = b->active;
+        if ((s = batch_observe(b, want, rec.data(), false))) return s;
+        bool changed = false;
+        for (int d = 0; d < b->count; ++d) {
+            if (!want[d]) continue;
+            out[d] = rec[d];
+            if (rec[d].nonfinite > 0) return bfail(b, LBM_ENAN, "domain %d became non-finite", d);
+            const double q = rec[d].flux_Q;
+            if (have_prev[d] && n == check_every && std::fabs(q - q_prev[d]) <= rel_tol * std::fabs(q)) {
+                steps_to_steady[d] = b->ctx[d]->t;
+                b->active[d] = 0;
+                changed = true;
+            }
+            q_prev[d] = q;
+            have_prev[d] = 1;
+        }
+        if (changed) b->tiles_dirty = true;
+    }
+    // restore the caller's active set
+    b->active = start_active;
+    b->tiles_dirty = true;
+    for (int d = 0; d < b->count; ++d)
+        if (start_active[d] && steps_to_steady[d] < 0) return bfail(b, LBM_ENOTCONV, "domain %d not steady", d);
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_autotune(lbm_batch* b, const int32_t* candidates, int32_t n, int32_t steps, int32_t* chosen,
+                              double* ms_per_step)
+{
+    lbm_status s = batch_ready(b);
+    if (s) return s;
+    if (!candidates || n < 1 || steps < 1 || !chosen) return bfail(b, LBM_EINVAL, "bad arguments");
+    cudaEvent_t e0, e1;
+    if ((s = bcheck(b, cudaEventCreate(&e0), "event")) || (s = bcheck(b, cudaEventCreate(&e1), "event"))) return s;
+    double best = 1e300;
+    int32_t pick = b->tile_rows;
+    for (int i = 0; i < n; ++i) {
+        if ((s = lbm_batch_set_tile_rows(b, candidates[i]))) break;
+        if ((s = lbm_batch_step(b, 2))) break;  // warm-up (and graph build)
+        cudaEventRecord(e0, b->stream);
+        if ((s = lbm_batch_step(b, steps))) break;
+        cudaEventRecord(e1, b->stream);
+        if ((s = bcheck(b, cudaEventSynchronize(e1), "event sync"))) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = double(ms) / steps;
+        if (ms_per_step) ms_per_step[i] = per;
+        if (per < best) {
+            best = per;
+            pick = candidates[i];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s) return s;
+    *chosen = pick;
+    if ((s = lbm_batch_set_tile_rows(b, pick))) return s;
+    return batch_check_status(b);
+}
+
+const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err : "null batch"; }
+
+void lbm_batch_destroy(lbm_batch* b)
+{
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (lbm_ctx* c : b->ctx) lbm_destroy(c);
+    delete b;
+}
 
 }  // extern "C"

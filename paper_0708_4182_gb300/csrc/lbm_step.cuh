@@ -522,16 +522,24 @@ __device__ __forceinline__ void collide_dev(const PulledDev& n, const float* pm,
 
 // ------------------------------------------------------------------ kernel
 
-template <int MODE, int ST = kF32>
-__global__ void __launch_bounds__(kThreads, 3)
-    step_kernel(const float* __restrict__ fin, float* __restrict__ fout, Geom g, Phys p,
-                double* __restrict__ partials, double* __restrict__ fields, int* __restrict__ err)
+__device__ __forceinline__ void mbar_inval(uint64_t* bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// One CTA's work: the strip of columns [bx*kW, bx*kW + kW) and the segment
+// of rows [by*tile_rows, (by+1)*tile_rows) of one domain; per-CTA
+// observables go to partials[slot]. smem_raw is the dynamic shared memory.
+template <int MODE, int ST>
+__device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* __restrict__ fout, const Geom& g,
+                                         const Phys& p, double* __restrict__ partials,
+                                         double* __restrict__ fields, int* __restrict__ err, int bx, int by,
+                                         int slot, unsigned char* smem_raw)
 {
     using T = typename StoreT<ST>::T;
     constexpr int H = StoreT<ST>::halo;  // staged halo columns per side
     constexpr int R = row_len<ST>();     // staged columns per plane row
     constexpr size_t SB = stage_bytes<ST>();
-    extern __shared__ __align__(128) unsigned char smem_raw[];
     // ring stage s: plane 0 (FP32, R) then planes 1..8 (T, R each)
     float* psi_ring = reinterpret_cast<float*>(smem_raw + kStages * SB);    // [4][kW + 2]
     uint64_t* full = reinterpret_cast<uint64_t*>(psi_ring + 4 * (kW + 2));  // [kStages]
@@ -541,10 +549,10 @@ __global__ void __launch_bounds__(kThreads, 3)
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int x0 = blockIdx.x * kW;
+    const int x0 = bx * kW;
     const int nint = min(kW, g.nx - x0);     // interior columns of this strip
     const int nbody = nint & ~3;             // columns moved by the bulk copies
-    const int y0 = blockIdx.y * g.tile_rows;
+    const int y0 = by * g.tile_rows;
     const int y1 = min(y0 + g.tile_rows, g.ny);
     const int nrows = (y1 - y0) + 4;         // staged rows y0-2 .. y1+1
 
@@ -766,7 +774,7 @@ __global__ void __launch_bounds__(kThreads, 3)
                 rm = fminf(rm, red_f[1][w]);
                 b += red_u[w];
             }
-            double* out = partials + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * kPartialStride;
+            double* out = partials + (size_t)slot * kPartialStride;
             out[0] = s[0];
             out[1] = s[1];
             out[2] = s[2];
@@ -776,6 +784,52 @@ __global__ void __launch_bounds__(kThreads, 3)
             out[6] = b;
             out[7] = 0.0;
         }
+    }
+}
+
+template <int MODE, int ST = kF32>
+__global__ void __launch_bounds__(kThreads, 3)
+    step_kernel(const float* __restrict__ fin, float* __restrict__ fout, Geom g, Phys p,
+                double* __restrict__ partials, double* __restrict__ fields, int* __restrict__ err)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    run_tile<MODE, ST>(fin, fout, g, p, partials, fields, err, blockIdx.x, blockIdx.y,
+                       blockIdx.y * gridDim.x + blockIdx.x, smem_raw);
+}
+
+// One domain of a batch: geometry, model parameters, its two population
+// buffers and its per-CTA partials.
+struct DomainDev {
+    Geom g;
+    Phys p;
+    float* buf[2];
+    double* partials;
+};
+
+// Persistent batched step: every CTA walks the tile list (domain, strip,
+// segment, partial slot) with stride gridDim.x, so domains of any size share
+// one launch; buffers alternate with `parity`. Between tiles the CTA
+// invalidates and re-arms its mbarriers.
+template <int MODE, int ST = kF32>
+__global__ void __launch_bounds__(kThreads, 3)
+    batch_step_kernel(const DomainDev* __restrict__ doms, const int4* __restrict__ tiles, int ntiles,
+                      int parity, int* __restrict__ err)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    for (int i = blockIdx.x; i < ntiles; i += gridDim.x) {
+        const int4 tl = tiles[i];
+        const DomainDev& d = doms[tl.x];
+        const Geom g = d.g;
+        const Phys p = d.p;
+        run_tile<MODE, ST>(d.buf[parity], d.buf[parity ^ 1], g, p, d.partials, nullptr, err, tl.y, tl.z, tl.w,
+                           smem_raw);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + kStages * stage_bytes<ST>() +
+                                                         4 * (kW + 2) * sizeof(float));
+            for (int s = 0; s < 2 * kStages; ++s) mbar_inval(&bars[s]);
+        }
+        __syncthreads();
     }
 }
 

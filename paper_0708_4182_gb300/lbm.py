@@ -21,7 +21,7 @@ import numpy as np
 
 from . import build as _build
 
-LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENAN, LBM_ETIMEOUT, LBM_ESTATE = range(7)
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENAN, LBM_ETIMEOUT, LBM_ESTATE, LBM_ENOTCONV = range(8)
 LBM_GREEN_MC, LBM_GREEN_PRINTED = 0, 1
 LBM_FP32, LBM_FP32_DEV, LBM_FP16_DEV, LBM_BF16_DEV = 0, 1, 2, 3
 LBM_RHO_U, LBM_POPS = 0, 1
@@ -86,6 +86,7 @@ def load():
             "lbm_step": (ctypes.c_int, [vp, ctypes.c_int64]),
             "lbm_observables": (ctypes.c_int, [vp, O]),
             "lbm_obs_latest": (ctypes.c_int, [vp, O]),
+            "lbm_run_to_steady": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int64, ctypes.c_int64, O]),
             "lbm_time": (ctypes.c_int64, [vp]),
             "lbm_last_error": (ctypes.c_char_p, [vp]),
             "lbm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -99,7 +100,8 @@ def load():
 
 
 def status_name(status: int) -> str:
-    names = ["LBM_OK", "LBM_EINVAL", "LBM_ENOMEM", "LBM_ECUDA", "LBM_ENAN", "LBM_ETIMEOUT", "LBM_ESTATE"]
+    names = ["LBM_OK", "LBM_EINVAL", "LBM_ENOMEM", "LBM_ECUDA", "LBM_ENAN", "LBM_ETIMEOUT", "LBM_ESTATE",
+             "LBM_ENOTCONV"]
     return names[status] if 0 <= status < len(names) else f"status {status}"
 
 
@@ -162,6 +164,15 @@ def lbm_obs_latest(ctx, check_finite: bool = True) -> dict:
     return o.as_dict()
 
 
+def lbm_run_to_steady(ctx, rel_tol: float, check_every: int, max_steps: int) -> tuple[dict, bool]:
+    """Step until the flux is steady; returns (observables, converged)."""
+    o = lbm_obs()
+    st = load().lbm_run_to_steady(ctx, float(rel_tol), int(check_every), int(max_steps), ctypes.byref(o))
+    if st not in (LBM_OK, LBM_ENOTCONV):
+        _check(ctx, st)
+    return o.as_dict(), st == LBM_OK
+
+
 def lbm_time(ctx) -> int:
     return int(load().lbm_time(ctx))
 
@@ -194,10 +205,19 @@ class Lattice:
     all work goes to ``stream`` (default: torch's current stream). Host
     arrays are numpy; device arrays may be torch CUDA tensors."""
 
-    def __init__(self, nx: int, ny: int, stream=None, **params):
+    def __init__(self, nx: int, ny: int, stream=None, _ctx=None, _owner=None, **params):
         import torch
 
         self.nx, self.ny = int(nx), int(ny)
+        if _ctx is not None:
+            # a view on a context owned by a Batch
+            self.params = make_params(nx, ny, **params)
+            self.stream = stream
+            self.workspace = None
+            self.ctx = _ctx
+            self._owner = _owner
+            return
+        self._owner = None
         self.params = make_params(nx, ny, **params)
         nbytes = lbm_workspace_bytes(self.params)
         if nbytes == 0:
@@ -271,14 +291,17 @@ class Lattice:
     def obs_latest(self, check_finite: bool = True) -> dict:
         return lbm_obs_latest(self.ctx, check_finite)
 
+    def run_to_steady(self, rel_tol: float = 1e-7, check_every: int = 1000, max_steps: int = 10 ** 6):
+        return lbm_run_to_steady(self.ctx, rel_tol, check_every, max_steps)
+
     @property
     def time(self) -> int:
         return lbm_time(self.ctx)
 
     def close(self):
-        if getattr(self, "ctx", None):
+        if getattr(self, "ctx", None) and getattr(self, "_owner", None) is None:
             lbm_destroy(self.ctx)
-            self.ctx = None
+        self.ctx = None
 
     def __del__(self):
         try:
@@ -311,3 +334,120 @@ def lbm_observables_noalloc(params: lbm_params, d_pops: int, d_solid: int, step:
     if st != LBM_OK and not (st == LBM_ENAN and not check_finite):
         raise LbmError(st, lib.lbm_noalloc_last_error().decode())
     return o.as_dict()
+
+
+
+# ------------------------------------------------------------------- batches
+
+def _batch_lib():
+    lib = load()
+    if not getattr(lib, "_batch_sigs", False):
+        vp, P, O = ctypes.c_void_p, ctypes.POINTER(lbm_params), ctypes.POINTER(lbm_obs)
+        sig = {
+            "lbm_batch_workspace_bytes": (ctypes.c_size_t, [P, ctypes.c_int32]),
+            "lbm_batch_create": (ctypes.c_int, [P, ctypes.c_int32, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]),
+            "lbm_batch_domain": (vp, [vp, ctypes.c_int32]),
+            "lbm_batch_step": (ctypes.c_int, [vp, ctypes.c_int64]),
+            "lbm_batch_observables": (ctypes.c_int, [vp, O]),
+            "lbm_batch_set_active": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_uint8)]),
+            "lbm_batch_set_tile_rows": (ctypes.c_int, [vp, ctypes.c_int32]),
+            "lbm_batch_tile_rows": (ctypes.c_int32, [vp]),
+            "lbm_batch_autotune": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                                                  ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                                  ctypes.POINTER(ctypes.c_double)]),
+            "lbm_batch_run_to_steady": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int64, ctypes.c_int64,
+                                                       ctypes.POINTER(ctypes.c_int64), O]),
+            "lbm_batch_last_error": (ctypes.c_char_p, [vp]),
+            "lbm_batch_destroy": (None, [vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype, fn.argtypes = res, args
+        lib._batch_sigs = True
+    return lib
+
+
+class Batch:
+    """Many domains advanced together (one persistent launch per step).
+
+    ``specs`` is a list of dicts of ``make_params`` arguments (nx, ny and the
+    model parameters of each domain; one storage form for all). ``domains``
+    holds a ``Lattice`` view per domain for set-up, read-back and per-domain
+    observables."""
+
+    def __init__(self, specs, stream=None):
+        import torch
+        lib = _batch_lib()
+        self.count = len(specs)
+        arr = (lbm_params * self.count)(*[make_params(**sp) for sp in specs])
+        self._params = arr
+        nbytes = int(lib.lbm_batch_workspace_bytes(arr, self.count))
+        if nbytes == 0:
+            raise LbmError(LBM_EINVAL, "invalid batch parameters")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.stream.device)
+        h = ctypes.c_void_p()
+        st = lib.lbm_batch_create(arr, self.count, ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                                  ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if st != LBM_OK:
+            raise LbmError(st, "lbm_batch_create failed")
+        self.handle = h
+        self.domains = []
+        for i, sp in enumerate(specs):
+            ctx = ctypes.c_void_p(lib.lbm_batch_domain(h, i))
+            sp = dict(sp)
+            nx, ny = sp.pop("nx"), sp.pop("ny")
+            self.domains.append(Lattice(nx, ny, stream=self.stream, _ctx=ctx, _owner=self, **sp))
+
+    def _check(self, st):
+        if st != LBM_OK:
+            raise LbmError(st, _batch_lib().lbm_batch_last_error(self.handle).decode())
+
+    def step(self, n: int = 1):
+        self._check(_batch_lib().lbm_batch_step(self.handle, int(n)))
+
+    def observables(self) -> list:
+        out = (lbm_obs * self.count)()
+        self._check(_batch_lib().lbm_batch_observables(self.handle, out))
+        return [o.as_dict() for o in out]
+
+    def set_active(self, flags):
+        a = (ctypes.c_uint8 * self.count)(*[1 if f else 0 for f in flags])
+        self._check(_batch_lib().lbm_batch_set_active(self.handle, a))
+
+    def set_tile_rows(self, rows: int):
+        self._check(_batch_lib().lbm_batch_set_tile_rows(self.handle, int(rows)))
+
+    @property
+    def tile_rows(self) -> int:
+        return int(_batch_lib().lbm_batch_tile_rows(self.handle))
+
+    def autotune(self, candidates=(8, 16, 32, 64), steps: int = 10):
+        c = (ctypes.c_int32 * len(candidates))(*candidates)
+        ms = (ctypes.c_double * len(candidates))()
+        chosen = ctypes.c_int32()
+        self._check(_batch_lib().lbm_batch_autotune(self.handle, c, len(candidates), int(steps),
+                                                    ctypes.byref(chosen), ms))
+        return int(chosen.value), list(ms)
+
+    def run_to_steady(self, rel_tol=1e-7, check_every=1000, max_steps=10 ** 6):
+        steps = (ctypes.c_int64 * self.count)()
+        out = (lbm_obs * self.count)()
+        st = _batch_lib().lbm_batch_run_to_steady(self.handle, float(rel_tol), int(check_every),
+                                                  int(max_steps), steps, out)
+        if st not in (LBM_OK, LBM_ENOTCONV):
+            self._check(st)
+        return list(steps), [o.as_dict() for o in out], st == LBM_OK
+
+    def close(self):
+        if getattr(self, "handle", None):
+            for d in self.domains:
+                d.ctx = None
+            _batch_lib().lbm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,125 @@
+"""Batched sweeps: many uneven domains advanced by one persistent launch.
+
+The batch runs the same per-node arithmetic as a single domain, and the
+result does not depend on the tiling, so every domain of a batch must be
+bitwise identical to the same domain stepped alone, which is itself checked
+against the FP64 oracle. Also covered: batched observables, the active set,
+the tile-height autotuner and run-to-steady against the oracle's steady flux.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0708_4182_gb300 import workloads as wl
+from tests.test_gpu_parity import assert_pops
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0708_4182_gb300 import lbm as L
+    L.load()
+    return L
+
+
+def sweep_workloads(count=6, seed=11, storage=0):
+    """A small sweep of uneven channels in the batched-sweep recipe."""
+    out = []
+    for k, ch in enumerate(wl.batched_channels(count, seed)):
+        nx = max(64, ch["nx"] // 4 // 8 * 8)
+        ny = max(2 * ch["amp"] + 8, ch["ny"] // 3)
+        w = wl.rough_channel(nx=nx, ny=ny, amp=min(ch["amp"], (ny - 3) // 2), level=ch["level"],
+                             seed=ch["seed"], body_fx=1e-5)
+        out.append(w)
+    return out
+
+
+def specs_of(ws, storage=0):
+    return [dict(nx=w.nx, ny=w.ny, storage=storage, **w.params) for w in ws]
+
+
+@pytest.mark.parametrize("storage", [0, 1, 2])
+def test_batch_equals_single_domain_runs(lbm, storage):
+    ws = sweep_workloads(storage=storage)
+    b = lbm.Batch(specs_of(ws, storage))
+    b.set_tile_rows(16)
+    for w, d in zip(ws, b.domains):
+        d.set_geometry(w.mask)
+        d.set_rho_u(w.rho)
+    b.step(37)  # odd: graph pairs plus one single launch
+    for w, d in zip(ws, b.domains):
+        lat = lbm.Lattice(w.nx, w.ny, storage=storage, **w.params)
+        lat.set_geometry(w.mask)
+        lat.set_rho_u(w.rho)
+        lat.step(37)
+        assert np.array_equal(d.populations(), lat.populations())
+        assert d.time == 37
+    obs = b.observables()
+    for w, d, o in zip(ws, b.domains, obs):
+        single = d.observables()
+        for k in ("mass", "flux_Q", "mom_x", "mom_y", "max_u", "min_rho"):
+            assert o[k] == pytest.approx(single[k], rel=1e-12, abs=1e-15), k
+    b.close()
+
+
+def test_batch_domain_matches_oracle(lbm):
+    ws = sweep_workloads(4, seed=5)
+    b = lbm.Batch(specs_of(ws))
+    for w, d in zip(ws, b.domains):
+        d.set_geometry(w.mask)
+        d.set_rho_u(w.rho)
+    b.step(60)
+    for w, d in zip(ws, b.domains):
+        p = oracle.Params(w.nx, w.ny, **w.params)
+        f_ref = oracle.step(p, w.mask, oracle.equilibrium(p, w.mask, w.rho, 0, 0), 60)
+        assert_pops(d.populations(), f_ref, w.mask)
+    b.close()
+
+
+def test_batch_active_set_and_autotune(lbm):
+    ws = sweep_workloads(5, seed=3)
+    b = lbm.Batch(specs_of(ws))
+    for w, d in zip(ws, b.domains):
+        d.set_geometry(w.mask)
+        d.set_rho_u(w.rho)
+    frozen = b.domains[2].populations()
+    b.set_active([1, 1, 0, 1, 1])
+    b.step(10)
+    assert np.array_equal(b.domains[2].populations(), frozen)
+    assert b.domains[2].time == 0 and b.domains[0].time == 10
+    chosen, ms = b.autotune((8, 16, 32), steps=4)
+    assert chosen in (8, 16, 32) and all(m > 0 for m in ms)
+    assert b.tile_rows == chosen
+    assert b.domains[0].time == 10 + 3 * 6 and b.domains[2].time == 0
+    b.close()
+
+
+def test_batch_run_to_steady_matches_oracle(lbm):
+    """Three smooth channels at levels 0, 10, 15 in one batch (FP32
+    deviation storage), each run to steady flux; the steady Q match the
+    oracle's within 1e-4."""
+    from tests.test_gpu_steady import oracle_steady_cached, smooth_channel
+    ws = [smooth_channel(lv) for lv in (0, 10, 15)]
+    b = lbm.Batch(specs_of(ws, storage=1))
+    for w, d in zip(ws, b.domains):
+        d.set_geometry(w.mask)
+        d.set_rho_u(w.rho)
+    steps, obs, ok = b.run_to_steady(1e-7, 1000, 80000)
+    assert ok, steps
+    for lv, o, st in zip((0, 10, 15), obs, steps):
+        qr, tr = oracle_steady_cached(lv)
+        assert o["flux_Q"] == pytest.approx(qr, rel=1e-4), (lv, o["flux_Q"], qr)
+        assert 0 < st <= tr + 3000
+    b.close()
+
+
+def test_batch_rejects_mixed_storage(lbm):
+    ws = sweep_workloads(2)
+    sp = specs_of(ws)
+    sp[1]["storage"] = 1
+    with pytest.raises(lbm.LbmError):
+        lbm.Batch(sp)

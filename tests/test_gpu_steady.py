@@ -57,17 +57,14 @@ def oracle_steady(w, max_steps=80000):
 
 
 def gpu_steady(lbm, w, max_steps=80000, storage=0):
+    """Through the library's own convergence loop (lbm_run_to_steady)."""
     lat = lbm.Lattice(w.nx, w.ny, storage=storage, **w.params)
     lat.set_geometry(w.mask)
     lat.set_rho_u(w.rho)
-    q_prev = None
-    while lat.time < max_steps:
-        lat.step(1000)
-        q = lat.observables()["flux_Q"]
-        if q_prev is not None and abs(q - q_prev) <= CRITERION * abs(q):
-            return q, lat.time
-        q_prev = q
-    raise AssertionError("GPU run did not reach steady flux")
+    obs, converged = lat.run_to_steady(CRITERION, 1000, max_steps)
+    assert converged, "GPU run did not reach steady flux"
+    assert obs["step"] == lat.time
+    return obs["flux_Q"], lat.time
 
 
 _ORACLE = {}
