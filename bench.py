@@ -59,6 +59,8 @@ def parse():
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched-sweep throughput and time-to-steady measurements")
     return ap.parse_args()
 
 
@@ -285,6 +287,12 @@ def run_ours(args, rank, world, local_rank):
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, w, params, lbm, stream, world)
+    extra = {}
+    if not args.no_batch and world == 1:
+        lat.close()
+        del lat
+        torch.cuda.empty_cache()
+        extra = run_batch_measurements(lbm, stream)
 
     line = {"metric": "MLUPS", "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 5),
@@ -301,12 +309,13 @@ def run_ours(args, rank, world, local_rank):
             "final_obs": {k: obs[k] for k in ("step", "mass", "flux_Q", "max_u", "nonfinite")}}
     if e2e:
         line["e2e"] = e2e
+    line.update(extra)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds, os.cpu_count() or 1)
     return line
 
 
-KERNEL_VERSION = "step-v2-bulk-ring"
+KERNEL_VERSION = "step-v5"
 
 
 def run_e2e(args, w, params, lbm, stream, world):
@@ -339,6 +348,104 @@ def run_e2e(args, w, params, lbm, stream, world):
             "h2d_bytes_per_step": int((rho_u.nbytes + mask.nbytes) / steps),
             "d2h_bytes_per_step": 64,
             "what": "host mask + FP64 (rho,u) upload, then per step lbm_step + fused observables read-back"}
+
+
+# ----------------------------------------------------------------- batched sweep
+
+def batched_sweep(count=256, seed=0):
+    """The batched-sweep recipe: channels of width 32-256, length 512-2048
+    (rounded down to a multiple of 8), roughness 0-8, force level 0-15."""
+    from paper_0708_4182_gb300 import workloads as wl
+    ws = []
+    for ch in wl.batched_channels(count, seed):
+        ws.append(wl.rough_channel(nx=ch["nx"] // 8 * 8, ny=ch["ny"], amp=ch["amp"], level=ch["level"],
+                                   seed=ch["seed"], body_fx=1e-6))
+    return ws
+
+
+def steady_sweep(count=32, seed=1, scale=4):
+    """Reduced sweep for time-to-steady: the first `count` channels of the
+    batched-sweep recipe with width and length divided by `scale` (width >= 24,
+    length >= 128), half the roughness, body force 1e-5."""
+    from paper_0708_4182_gb300 import workloads as wl
+    ws = []
+    for ch in wl.batched_channels(count, seed):
+        ny = max(24, ch["ny"] // scale)
+        nx = max(128, ch["nx"] // scale // 8 * 8)
+        amp = max(0, min(ch["amp"] // 2, (ny - 3) // 2 - 4))
+        ws.append(wl.rough_channel(nx=nx, ny=ny, amp=amp, level=ch["level"], seed=ch["seed"], body_fx=1e-5))
+    return ws
+
+
+def run_batch_measurements(lbm, stream):
+    import torch
+    out = {}
+    ws = batched_sweep()
+    nodes = sum(w.nx * w.ny for w in ws)
+    b = lbm.Batch([dict(nx=w.nx, ny=w.ny, **w.params) for w in ws], stream=stream)
+    for w, d in zip(ws, b.domains):
+        d.set_geometry(w.mask)
+        d.set_rho_u(w.rho)
+    cands = (8, 16, 32, 64, 128)
+    chosen, ms = b.autotune(cands, steps=10)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    b.step(100)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_step = e0.elapsed_time(e1) / 100
+    # the same domains one at a time (first 32, 20 steps each)
+    seq_t, seq_nodes = 0.0, 0
+    for w, d in zip(ws[:32], b.domains[:32]):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        d.step(20)
+        torch.cuda.synchronize()
+        seq_t += time.perf_counter() - t
+        seq_nodes += 20 * w.nx * w.ny
+    b.close()
+    out["batched"] = {
+        "workload": f"{len(ws)} rough channels (width 32-256, length 512-2048, roughness 0-8, level 0-15, "
+                    f"seed 0), FP32 populations, one persistent launch per step",
+        "nodes": nodes, "mlups": round(nodes / ms_step / 1e3, 1), "ms_per_step": round(ms_step, 4),
+        "tile_rows": chosen, "autotune_ms_per_step": {str(c): round(m, 4) for c, m in zip(cands, ms)},
+        "one_domain_at_a_time_mlups": round(seq_nodes / seq_t / 1e6, 1)}
+
+    # time to steady flux: plain one domain at a time vs one batch
+    ws = steady_sweep()
+    kw = dict(storage=lbm.LBM_FP32_DEV)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    plain = []
+    for w in ws:
+        lat = lbm.Lattice(w.nx, w.ny, stream=stream, **kw, **w.params)
+        lat.set_geometry(w.mask)
+        lat.set_rho_u(w.rho)
+        o, ok = lat.run_to_steady(1e-7, 1000, 60000)
+        plain.append((o["flux_Q"], o["step"] if ok else -1))
+        lat.close()
+    t_plain = time.perf_counter() - t
+    t = time.perf_counter()
+    b = lbm.Batch([dict(nx=w.nx, ny=w.ny, **kw, **w.params) for w in ws], stream=stream)
+    for w, d in zip(ws, b.domains):
+        d.set_geometry(w.mask)
+        d.set_rho_u(w.rho)
+    b.set_tile_rows(16)
+    steps, obs, _ = b.run_to_steady(1e-7, 1000, 60000)
+    t_batch = time.perf_counter() - t
+    b.close()
+    dq = max(abs(o["flux_Q"] / q - 1) for (q, _), o in zip(plain, obs) if q != 0)
+    out["time_to_steady"] = {
+        "workload": "32 channels of the batched-sweep recipe (seed 1) at 1/4 width and length "
+                    "(width >= 24, length >= 128), half roughness, body force 1e-5, FP32 deviation "
+                    "storage; steady when |dQ|/|Q| < 1e-7 per 1000 steps, cap 60000 steps",
+        "plain_one_domain_at_a_time_s": round(t_plain, 3), "batched_s": round(t_batch, 3),
+        "speedup": round(t_plain / t_batch, 2),
+        "converged": sum(1 for s_ in steps if s_ > 0), "domains": len(ws),
+        "max_rel_flux_difference_batched_vs_plain": dq,
+        "warm_start": None}
+    return out
 
 
 def main():
