@@ -19,6 +19,9 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "liblbm_ewod.so")
 SOURCES = [os.path.join(CSRC, "lbm_ewod.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, "lbm_step.cuh"), os.path.join(ROOT, "include", "lbm_ewod.h")]
+UNET_LIB = os.path.join(BUILD, "libunet_bf16.so")
+UNET_SOURCES = [os.path.join(CSRC, "unet_bf16.cu")]
+UNET_DEPS = UNET_SOURCES + [os.path.join(ROOT, "include", "unet_bf16.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -29,32 +32,48 @@ def nvcc() -> str:
     return cand
 
 
-def command(out: str = LIB, verbose_ptxas: bool = False) -> list[str]:
+def command(out: str = LIB, verbose_ptxas: bool = False, sources=None) -> list[str]:
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-shared",
-           "-cudart", "shared", "-I", os.path.join(ROOT, "include"), "-o", out, *SOURCES]
+           "-cudart", "shared", "-I", os.path.join(ROOT, "include"), "-o", out, *(sources or SOURCES)]
     if verbose_ptxas:
         cmd.insert(1, "-Xptxas=-v")
     return cmd
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib=LIB, deps=DEPS) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(d) <= t for d in DEPS)
+    t = os.path.getmtime(lib)
+    return all(os.path.getmtime(d) <= t for d in deps)
+
+
+def _start(lib, sources, verbose_ptxas):
+    tmp = lib + f".{os.getpid()}.tmp"
+    proc = subprocess.Popen(command(tmp, verbose_ptxas, sources), stdout=subprocess.PIPE,
+                            stderr=subprocess.PIPE, text=True)
+    return proc, tmp, lib
 
 
 def build(force: bool = False, verbose_ptxas: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
+    """Build both libraries (the lattice Boltzmann step and the U-Net
+    kernels), compiling them in parallel; returns the step library's path."""
     os.makedirs(BUILD, exist_ok=True)
-    tmp = LIB + f".{os.getpid()}.tmp"
-    res = subprocess.run(command(tmp, verbose_ptxas), capture_output=True, text=True)
-    if res.returncode != 0:
-        raise RuntimeError("nvcc failed:\n" + res.stdout + res.stderr)
-    if verbose_ptxas:
-        sys.stderr.write(res.stderr)
-    os.replace(tmp, LIB)
+    jobs = []
+    if force or not up_to_date(LIB, DEPS):
+        jobs.append(_start(LIB, SOURCES, verbose_ptxas))
+    if force or not up_to_date(UNET_LIB, UNET_DEPS):
+        jobs.append(_start(UNET_LIB, UNET_SOURCES, verbose_ptxas))
+    errors = []
+    for proc, tmp, lib in jobs:
+        out, err = proc.communicate()
+        if proc.returncode != 0:
+            errors.append(out + err)
+            continue
+        if verbose_ptxas:
+            sys.stderr.write(err)
+        os.replace(tmp, lib)
+    if errors:
+        raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
     return LIB
 
 

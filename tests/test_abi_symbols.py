@@ -1,6 +1,6 @@
-"""The C ABI library builds for sm_103a, loads, and exports every entry point
-that include/lbm_ewod.h declares (no GPU needed: nothing is called that
-touches a device)."""
+"""The C ABI libraries build for sm_103a, load, and export every entry point
+that include/lbm_ewod.h and include/unet_bf16.h declare (no GPU needed:
+nothing is called that touches a device)."""
 import ctypes
 import os
 import re
@@ -9,12 +9,13 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "lbm_ewod.h")
+UNET_HEADER = os.path.join(ROOT, "include", "unet_bf16.h")
 
 
-def declared_functions():
-    src = open(HEADER).read()
+def declared_functions(header=HEADER, prefix="lbm_"):
+    src = open(header).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(" + prefix + r"[a-z0-9_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
@@ -37,6 +38,15 @@ def test_header_declares_the_boundary():
 def test_every_declared_symbol_is_exported(lib):
     for name in declared_functions():
         assert hasattr(lib, name), name
+
+
+def test_every_unet_symbol_is_exported(lib):
+    from paper_0708_4182_gb300 import build
+    unet = ctypes.CDLL(build.UNET_LIB)
+    names = declared_functions(UNET_HEADER, "unet_")
+    assert "unet_conv3x3_fwd" in names and "unet_adam" in names
+    for name in names:
+        assert hasattr(unet, name), name
 
 
 def test_host_only_entry_points(lib):
