@@ -84,8 +84,8 @@ enum { LBM_GREEN_MC = 0, LBM_GREEN_PRINTED = 1 };
  *               node, rounded to nearest); nx must be a multiple of 8. */
 enum { LBM_FP32 = 0, LBM_FP32_DEV = 1, LBM_FP16_DEV = 2, LBM_BF16_DEV = 3 };
 
-/* Field selectors for lbm_set_field / lbm_get_field. */
-enum { LBM_RHO_U = 0, LBM_POPS = 1 };
+/* Field selectors for lbm_set_field / lbm_get_field (LBM_RHO_U_PHYS: set only). */
+enum { LBM_RHO_U = 0, LBM_POPS = 1, LBM_RHO_U_PHYS = 2 };
 
 typedef struct {
     int32_t nx, ny;    /* lattice size; x and y are periodic, walls come
@@ -138,6 +138,14 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const uint8_t *solid, int on_device);
 /* Set the state at the current time index.
  * LBM_RHO_U: data = double[3][ny][nx] (rho, ux, uy); every fluid node gets
  *            f_a = f_a^eq(rho, u) of Eq. 3. Values on solid nodes are ignored.
+ * LBM_RHO_U_PHYS: data as for LBM_RHO_U, with u the physical velocity
+ *            (sum_a f_a e_a + F/2)/rho that lbm_get_field(LBM_RHO_U) and the
+ *            observables report: f_a = f_a^eq(rho, u - F/(2 rho)), F the
+ *            total force (Eqs. 5 and 6, the electric force, the body force)
+ *            of the given density field, in FP64. Reading the field back
+ *            returns (rho, u) up to storage rounding, so a run restarted
+ *            from a (rho, u) snapshot does not receive the momentum kick
+ *            F/2 per node that LBM_RHO_U gives at interfaces.
  * LBM_POPS:  data = double[9][ny][nx], the populations f_a(x, t) after
  *            streaming (the f of Eq. 2). Values on solid nodes are ignored.
  * Populations are rounded to the storage type. Needs lbm_set_geometry first
@@ -236,9 +244,11 @@ lbm_status lbm_batch_autotune(lbm_batch *b, const int32_t *candidates, int32_t n
 /* Step the active domains until each one's flux is steady (criterion as in
  * lbm_run_to_steady, checked every check_every steps); a domain stops being
  * stepped once it is steady. steps_to_steady[count] gets each domain's time
- * index at convergence (-1 if inactive or not converged), out[count] its
- * last observables. LBM_ENOTCONV if some active domain did not converge
- * within max_steps. The caller's active set is restored on return. */
+ * index at convergence (-1 if inactive or not converged, -2 if it became
+ * non-finite: such a domain is dropped and the others run on), out[count]
+ * its last observables. LBM_ENAN if some domain became non-finite, else
+ * LBM_ENOTCONV if some active domain did not converge within max_steps.
+ * The caller's active set is restored on return. */
 lbm_status lbm_batch_run_to_steady(lbm_batch *b, double rel_tol, int64_t check_every, int64_t max_steps,
                                    int64_t *steps_to_steady, lbm_obs *out);
 

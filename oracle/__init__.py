@@ -170,6 +170,21 @@ def forces(p: Params, solid, f: np.ndarray):
     return rho, jx, jy, terms
 
 
+def equilibrium_physical(p: Params, solid, rho, ux, uy) -> np.ndarray:
+    """State whose density is rho and whose physical velocity (j + F/2)/rho
+    (the velocity of Eq. 11's flux) is u: Eq. 3 evaluated at
+    u - F/(2 rho), F the total force that the density field rho exerts
+    (Eq. 5, Eq. 6, the electric force, the body force). The force depends on
+    the density and the mask only, so it is read off the state f_eq(rho, 0)."""
+    s = _mask(p, solid)
+    r = np.ascontiguousarray(np.broadcast_to(rho, (p.ny, p.nx)), dtype=np.float64)
+    _, _, _, t = forces(p, s, equilibrium(p, s, r, 0.0, 0.0))
+    fx = t[0] + t[2] + t[4] + t[6]
+    fy = t[1] + t[3] + t[5] + t[7]
+    safe = np.where(s == 0, r, 1.0)
+    return equilibrium(p, s, r, ux - 0.5 * fx / safe, uy - 0.5 * fy / safe)
+
+
 def observables(p: Params, solid, f: np.ndarray) -> dict:
     """mass, flux Q (Eq. 11), momentum, max |u|, min rho, non-finite count."""
     s = _mask(p, solid)

@@ -25,10 +25,10 @@ C = (32, 64, 128, 256)
 IN_CH, OUT_CH = 3, 3
 
 
-def shapes() -> dict:
+def shapes(in_ch: int = IN_CH) -> dict:
     """name -> (out_channels, in_channels, kernel size) for every layer."""
     s = {}
-    cin = IN_CH
+    cin = in_ch
     for l, c in enumerate(C):
         s[f"e{l}a"] = (c, cin, 3)
         s[f"e{l}b"] = (c, c, 3)

@@ -158,6 +158,63 @@ __global__ void feq_kernel(const double* __restrict__ ru, const uint8_t* __restr
     }
 }
 
+// Model constants in FP64 for the force-corrected initial state.
+struct PhysD {
+    double rho0, rho_c, f_elec, bfx, bfy;
+    double g_axis, g_diag, w_axis, w_diag;
+};
+
+__device__ __forceinline__ double psi_in(const double* __restrict__ rho, const uint8_t* __restrict__ mask,
+                                         long long i, double rho0)
+{
+    return mask[i] ? 0.0 : rho0 * (1.0 - exp(-rho[i] / rho0));
+}
+
+// Initial state from (rho, u) with u the physical velocity (sum_a f_a e_a +
+// F/2)/rho: f_a = f_a^eq(rho, u - F/(2 rho)) of Eq. 3, F the total force of
+// the given density field (Eq. 5 fluid-fluid, Eq. 6 wall, the electric force
+// on conductive wall-layer nodes, the body force), all in FP64.
+__global__ void feq_phys_kernel(const double* __restrict__ ru, const uint8_t* __restrict__ mask,
+                                float* __restrict__ f, Geom g, PhysD p)
+{
+    const long long n = (long long)g.nx * g.ny;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int y = int(i / g.nx), x = int(i % g.nx);
+        const int o = y * g.pitch + x;
+        if (mask[i]) {
+#pragma unroll
+            for (int a = 0; a < 9; ++a) f[a * g.plane + o] = __uint_as_float(kSolidBits);
+            continue;
+        }
+        const int xe = x + 1 == g.nx ? 0 : x + 1, xw = x == 0 ? g.nx - 1 : x - 1;
+        const int yn = y + 1 == g.ny ? 0 : y + 1, ys = y == 0 ? g.ny - 1 : y - 1;
+        const long long rn = (long long)yn * g.nx, rc = (long long)y * g.nx, rs = (long long)ys * g.nx;
+        const double pE = psi_in(ru, mask, rc + xe, p.rho0), pW = psi_in(ru, mask, rc + xw, p.rho0);
+        const double pN = psi_in(ru, mask, rn + x, p.rho0), pS = psi_in(ru, mask, rs + x, p.rho0);
+        const double pNE = psi_in(ru, mask, rn + xe, p.rho0), pNW = psi_in(ru, mask, rn + xw, p.rho0);
+        const double pSE = psi_in(ru, mask, rs + xe, p.rho0), pSW = psi_in(ru, mask, rs + xw, p.rho0);
+        const double sE = mask[rc + xe] ? 1.0 : 0.0, sW = mask[rc + xw] ? 1.0 : 0.0;
+        const double sN = mask[rn + x] ? 1.0 : 0.0, sS = mask[rs + x] ? 1.0 : 0.0;
+        const double sNE = mask[rn + xe] ? 1.0 : 0.0, sNW = mask[rn + xw] ? 1.0 : 0.0;
+        const double sSE = mask[rs + xe] ? 1.0 : 0.0, sSW = mask[rs + xw] ? 1.0 : 0.0;
+        const double rho = ru[i], ux = ru[n + i], uy = ru[2 * n + i];
+        const double psi = p.rho0 * (1.0 - exp(-rho / p.rho0));
+        const double gx = p.g_axis * (pE - pW) + p.g_diag * ((pNE - pNW) + (pSE - pSW)) +
+                          p.w_axis * (sE - sW) + p.w_diag * ((sNE - sNW) + (sSE - sSW));
+        const double gy = p.g_axis * (pN - pS) + p.g_diag * ((pNE + pNW) - (pSE + pSW)) +
+                          p.w_axis * (sN - sS) + p.w_diag * ((sNE + sNW) - (sSE + sSW));
+        double Fx = -psi * gx + rho * p.bfx, Fy = -psi * gy + rho * p.bfy;
+        if (rho >= p.rho_c) {
+            Fx += p.f_elec * (sE - sW);
+            Fy += p.f_elec * (sN - sS);
+        }
+        const double vx = ux - 0.5 * Fx / rho, vy = uy - 0.5 * Fy / rho;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) f[a * g.plane + o] = float(feq_d(a, rho, vx, vy));
+    }
+}
+
 // Rows [r0, r0 + rows) of dense FP64 populations laid out [9][rows][nx]
 // -> FP32 post-streaming planes of buffer `f` (pitch layout).
 __global__ void pops_in_kernel(const double* __restrict__ src, float* __restrict__ f, Geom g,
@@ -726,7 +783,7 @@ lbm_status lbm_set_field(lbm_ctx* c, int which, const double* data, int on_devic
     if (!c->has_geometry) return fail(c, LBM_ESTATE, "lbm_set_geometry must come before lbm_set_field");
     const size_t n = size_t(c->g.nx) * c->g.ny;
     lbm_status s;
-    if (which == LBM_RHO_U) {
+    if (which == LBM_RHO_U || which == LBM_RHO_U_PHYS) {
         // (rho, u) -> f_eq into the current buffer -> un-streamed into the
         // spare one, which becomes current; both end with solid sentinels
         const double* src = data;
@@ -738,7 +795,17 @@ lbm_status lbm_set_field(lbm_ctx* c, int which, const double* data, int on_devic
                 return s;
             src = tmp;
         }
-        feq_kernel<<<aux_blocks(n, c->sm_count), kAuxThreads, 0, c->stream>>>(src, c->mask, c->cur, c->g);
+        if (which == LBM_RHO_U) {
+            feq_kernel<<<aux_blocks(n, c->sm_count), kAuxThreads, 0, c->stream>>>(src, c->mask, c->cur, c->g);
+        } else {
+            const lbm_params& q = c->prm;
+            const double ka = q.green == LBM_GREEN_PRINTED ? 2.0 : 1.0;
+            const double kd = q.green == LBM_GREEN_PRINTED ? 1.0 : 0.5;
+            const PhysD pd{q.rho0, q.rho_c, q.f_elec, q.body_fx, q.body_fy,
+                           ka * q.G, kd * q.G, ka * q.G_wall, kd * q.G_wall};
+            feq_phys_kernel<<<aux_blocks(n, c->sm_count), kAuxThreads, 0, c->stream>>>(src, c->mask, c->cur, c->g,
+                                                                                     pd);
+        }
         if ((s = check_launch(c, "field kernel launch"))) return s;
         unstream_kernel<<<aux_blocks(n, c->sm_count), kAuxThreads, 0, c->stream>>>(c->cur, c->mask, c->nxt, c->g);
         if ((s = check_launch(c, "unstream kernel launch"))) return s;
@@ -1423,6 +1490,7 @@ lbm_status lbm_batch_run_to_steady(lbm_batch* b, double rel_tol, int64_t check_e
     std::vector<unsigned char> start_active = b->active;
     for (int d = 0; d < b->count; ++d) steps_to_steady[d] = -1;
     std::vector<lbm_obs> rec(b->count);
+    int first_nan = -1;
     for (int64_t done = 0; done < max_steps;) {
         bool any = false;
         for (int d = 0; d < b->count; ++d) any = any || b->active[d];
@@ -1436,7 +1504,14 @@ lbm_status lbm_batch_run_to_steady(lbm_batch* b, double rel_tol, int64_t check_e
         for (int d = 0; d < b->count; ++d) {
             if (!want[d]) continue;
             out[d] = rec[d];
-            if (rec[d].nonfinite > 0) return bfail(b, LBM_ENAN, "domain %d became non-finite", d);
+            if (rec[d].nonfinite > 0) {
+                // drop it; the sweep goes on with the others
+                steps_to_steady[d] = -2;
+                b->active[d] = 0;
+                changed = true;
+                if (first_nan < 0) first_nan = d;
+                continue;
+            }
             const double q = rec[d].flux_Q;
             if (have_prev[d] && n == check_every && std::fabs(q - q_prev[d]) <= rel_tol * std::fabs(q)) {
                 steps_to_steady[d] = b->ctx[d]->t;
@@ -1451,6 +1526,7 @@ lbm_status lbm_batch_run_to_steady(lbm_batch* b, double rel_tol, int64_t check_e
     // restore the caller's active set
     b->active = start_active;
     b->tiles_dirty = true;
+    if (first_nan >= 0) return bfail(b, LBM_ENAN, "domain %d became non-finite", first_nan);
     for (int d = 0; d < b->count; ++d)
         if (start_active[d] && steps_to_steady[d] < 0) return bfail(b, LBM_ENOTCONV, "domain %d not steady", d);
     return LBM_OK;

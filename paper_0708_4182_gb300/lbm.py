@@ -24,7 +24,7 @@ from . import build as _build
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENAN, LBM_ETIMEOUT, LBM_ESTATE, LBM_ENOTCONV = range(8)
 LBM_GREEN_MC, LBM_GREEN_PRINTED = 0, 1
 LBM_FP32, LBM_FP32_DEV, LBM_FP16_DEV, LBM_BF16_DEV = 0, 1, 2, 3
-LBM_RHO_U, LBM_POPS = 0, 1
+LBM_RHO_U, LBM_POPS, LBM_RHO_U_PHYS = 0, 1, 2
 
 
 class LbmUnavailable(RuntimeError):
@@ -251,7 +251,10 @@ class Lattice:
                 raise ValueError(f"field shape {a.shape} != {(comps, self.ny, self.nx)}")
             lbm_set_field(self.ctx, which, p, False)
 
-    def set_rho_u(self, rho, ux=0.0, uy=0.0):
+    def set_rho_u(self, rho, ux=0.0, uy=0.0, physical=False):
+        """State f = f_eq(rho, u). With physical=True, u is the physical
+        velocity that fields() reports and the equilibrium takes u - F/(2 rho)
+        (LBM_RHO_U_PHYS), so a (rho, u) snapshot restarts without a kick."""
         if hasattr(rho, "is_cuda") and rho.is_cuda:
             import torch
             data = torch.stack([torch.broadcast_to(torch.as_tensor(v, dtype=torch.float64, device=rho.device),
@@ -259,7 +262,7 @@ class Lattice:
         else:
             data = np.stack([np.broadcast_to(np.asarray(v, np.float64), (self.ny, self.nx))
                              for v in (rho, ux, uy)])
-        self._set(LBM_RHO_U, data, 3)
+        self._set(LBM_RHO_U_PHYS if physical else LBM_RHO_U, data, 3)
 
     def set_populations(self, f):
         self._set(LBM_POPS, f, 9)
@@ -277,8 +280,15 @@ class Lattice:
 
     def populations_device(self):
         import torch
-        out = torch.empty((9, self.ny, self.nx), dtype=torch.float64, device=self.workspace.device)
+        out = torch.empty((9, self.ny, self.nx), dtype=torch.float64, device=self.stream.device)
         lbm_get_field(self.ctx, LBM_POPS, out.data_ptr(), True)
+        return out
+
+    def fields_device(self):
+        """(rho, u_x, u_y) as one FP64 device tensor [3, ny, nx]."""
+        import torch
+        out = torch.empty((3, self.ny, self.nx), dtype=torch.float64, device=self.stream.device)
+        lbm_get_field(self.ctx, LBM_RHO_U, out.data_ptr(), True)
         return out
 
     # -- time stepping
@@ -406,9 +416,13 @@ class Batch:
     def step(self, n: int = 1):
         self._check(_batch_lib().lbm_batch_step(self.handle, int(n)))
 
-    def observables(self) -> list:
+    def observables(self, check_finite: bool = True) -> list:
+        """Per-domain observables; a non-finite domain raises unless
+        check_finite is False (its ``nonfinite`` count then tells)."""
         out = (lbm_obs * self.count)()
-        self._check(_batch_lib().lbm_batch_observables(self.handle, out))
+        st = _batch_lib().lbm_batch_observables(self.handle, out)
+        if not (st == LBM_ENAN and not check_finite):
+            self._check(st)
         return [o.as_dict() for o in out]
 
     def set_active(self, flags):
@@ -435,8 +449,9 @@ class Batch:
         out = (lbm_obs * self.count)()
         st = _batch_lib().lbm_batch_run_to_steady(self.handle, float(rel_tol), int(check_every),
                                                   int(max_steps), steps, out)
-        if st not in (LBM_OK, LBM_ENOTCONV):
+        if st not in (LBM_OK, LBM_ENOTCONV, LBM_ENAN):
             self._check(st)
+        # steps: -1 not steady within max_steps, -2 became non-finite
         return list(steps), [o.as_dict() for o in out], st == LBM_OK
 
     def close(self):

@@ -66,9 +66,9 @@ def _call(fn, *args):
         raise RuntimeError(f"{fn.__name__} failed with {rc}")
 
 
-def layer_shapes() -> dict:
+def layer_shapes(in_ch: int = IN_CH) -> dict:
     s = {}
-    cin = IN_CH
+    cin = in_ch
     for l, c in enumerate(C):
         s[f"e{l}a"] = (c, cin, 3)
         s[f"e{l}b"] = (c, c, 3)
@@ -100,11 +100,13 @@ class View:
 class UNet:
     """Parameters, optimizer state and activation buffers for batch size B."""
 
-    def __init__(self, batch=16, height=64, width=256, seed=0, stream=None):
+    def __init__(self, batch=16, height=64, width=256, seed=0, stream=None, in_ch=IN_CH):
         import torch
         self.torch = torch
         self.lib = load_unet()
         self.B, self.H, self.W = batch, height, width
+        self.in_ch = in_ch
+        self.shapes = layer_shapes(in_ch)
         if height % 32 or width % 256:
             raise ValueError("height must be a multiple of 32 and width of 256")
         self.dev = "cuda"
@@ -112,7 +114,7 @@ class UNet:
         self.s = ctypes.c_void_p(self.stream.cuda_stream)
         g = torch.Generator().manual_seed(seed)
         self.params = {}
-        for name, (co, ci, k) in layer_shapes().items():
+        for name, (co, ci, k) in self.shapes.items():
             std = (2.0 / (ci * k * k)) ** 0.5
             wm = (torch.randn((co, ci, k, k), generator=g, dtype=torch.float64) * std).float().to(self.dev)
             self.params[name] = self._param(wm, torch.zeros(co, device=self.dev))
@@ -146,7 +148,7 @@ class UNet:
         H, W = self.H, self.W
         bf = dict(dtype=t.bfloat16, device=self.dev)
         hw = [(H >> l, W >> l) for l in range(4)]
-        self.x0 = t.zeros((B, IN_CH, H, W), **bf)
+        self.x0 = t.zeros((B, self.in_ch, H, W), **bf)
         self.A = [t.zeros((B, C[l], *hw[l]), **bf) for l in range(4)]
         self.B3 = t.zeros((B, C[3], *hw[3]), **bf)
         self.cat = [t.zeros((B, C[l + 1] + C[l], *hw[l]), **bf) for l in range(3)]
@@ -168,7 +170,7 @@ class UNet:
     # -------------------------------------------------------------- layers
     def _conv(self, name, x: View, y: View, h, w, relu=True):
         p = self.params[name]
-        co, ci, _ = layer_shapes()[name]
+        co, ci, _ = self.shapes[name]
         _call(self.lib.unet_conv3x3_fwd, ctypes.c_void_p(x.ptr), ci, x.bs, ctypes.c_void_p(p["wb"].data_ptr()),
               ctypes.c_void_p(p["b"].data_ptr()), ctypes.c_void_p(y.ptr), co, y.bs, self.batch, h, w,
               1 if relu else 0, self.s)
@@ -177,7 +179,7 @@ class UNet:
         """Through relu(conv(x)): gy *= (y > 0); accumulate weight/bias grads;
         gx = conv^T(gy) if gx is given."""
         p = self.params[name]
-        co, ci, _ = layer_shapes()[name]
+        co, ci, _ = self.shapes[name]
         lib, n = self.lib, self.batch
         _call(lib.unet_relu_bwd, ctypes.c_void_p(y.ptr), y.bs, ctypes.c_void_p(gy.ptr), gy.bs, co * h * w, n, self.s)
         _call(lib.unet_conv3x3_bwd_weight, ctypes.c_void_p(x.ptr), ci, x.bs, ctypes.c_void_p(gy.ptr), co, gy.bs,
@@ -193,7 +195,7 @@ class UNet:
         xs = x_planes.contiguous().float()
         _call(lib.unet_f32_to_bf16, ctypes.c_void_p(xs.data_ptr()), ctypes.c_void_p(self.x0.data_ptr()),
               xs.numel(), s)
-        h = View(self.x0, 0, IN_CH)
+        h = View(self.x0, 0, self.in_ch)
         for l in range(4):
             hh, ww = H >> l, W >> l
             a = View(self.A[l], 0, C[l])
@@ -220,9 +222,10 @@ class UNet:
               ctypes.c_void_p(hp["b"].data_ptr()), ctypes.c_void_p(self.out.data_ptr()), OUT_CH, n, H * W, s)
         return self.out
 
-    def loss_backward(self, target, wc):
+    def loss_backward(self, target, wc, sync=True):
         """MSE against target [B, 3, H, W] (FP32) with channel weights wc;
-        fills every parameter gradient (zeroed first); returns the loss."""
+        fills every parameter gradient (zeroed first); returns the loss
+        (a float, or with sync=False the FP64 device scalar)."""
         t, lib, n, s = self.torch, self.lib, self.batch, self.s
         H, W = self.H, self.W
         for p in self.params.values():
@@ -267,10 +270,10 @@ class UNet:
                   ctypes.c_void_p(gskip.ptr), gskip.bs, C[l], n, hh, ww, 1, s)
             self._conv_bwd(f"e{l}b", View(self.A[l], 0, C[l]), View(self.cat[l], C[l + 1], C[l]), gskip,
                            View(self.gA[l], 0, C[l]), hh, ww)
-            below = View(self.x0, 0, IN_CH) if l == 0 else View(self.P[l - 1], 0, C[l - 1])
+            below = View(self.x0, 0, self.in_ch) if l == 0 else View(self.P[l - 1], 0, C[l - 1])
             self._conv_bwd(f"e{l}a", below, View(self.A[l], 0, C[l]), View(self.gA[l], 0, C[l]),
                            None if l == 0 else View(self.gP[l - 1], 0, C[l - 1]), hh, ww)
-        return float(self.loss_acc.item())
+        return float(self.loss_acc.item()) if sync else self.loss_acc.clone()
 
     def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0):
         self.step_count += 1
@@ -302,3 +305,196 @@ class UNet:
         nm = self.norm
         rho = out[:, 0] * nm["rho_std"] + nm["rho_mean"]
         return rho, out[:, 1] * nm["u_scale"], out[:, 2] * nm["u_scale"]
+
+    def predict(self, planes):
+        """Decoded (rho, u_x, u_y) device tensors [N, H, W] for input planes
+        [N, 3, H, W], N any size (run in batches of the network's batch)."""
+        t = self.torch
+        n = planes.shape[0]
+        outs = []
+        for i in range(0, n, self.batch):
+            chunk = planes[i:i + self.batch]
+            k = chunk.shape[0]
+            if k < self.batch:
+                chunk = t.cat([chunk, chunk[-1:].expand(self.batch - k, -1, -1, -1)])
+            outs.append(self.forward(chunk)[:k].clone())
+        out = t.cat(outs)
+        return self.decode(out)
+
+
+# ---------------------------------------------------------------- warm start
+def channel_planes(net, ws):
+    """Input planes of the surrogate for channel workloads (mask, level, fill)."""
+    return net.planes(np.stack([w.mask for w in ws]), [w.meta["level"] for w in ws],
+                      [w.meta["fill"] for w in ws])
+
+
+def flat_walls(mask) -> bool:
+    """True if the walls run parallel to x (every column has the same solid
+    rows): the steady state of such a channel does not depend on the start.
+    Rough walls hold vapor pockets in their grooves, and where the pockets
+    settle depends on the path to the steady state, so a warm start could
+    converge to another steady flux than the cold start."""
+    m = np.asarray(mask)
+    return bool(np.all(m == m[:, :1]))
+
+
+def steady_states(ws, stream=None, rel_tol=1e-7, check_every=1000, max_steps=60000, chunk=1024, storage=None):
+    """Run every workload from its cold start to steady flux (batched) and
+    return a dict of device tensors: fields [N, 3, ny, nx] FP32 (rho, u_x,
+    u_y), steps [N] (-1: not steady within max_steps, -2: non-finite) and
+    flux Q [N] (FP64)."""
+    import torch
+    from . import lbm as L
+    storage = L.LBM_FP32_DEV if storage is None else storage
+    fields, steps, flux = [], [], []
+    for i in range(0, len(ws), chunk):
+        part = ws[i:i + chunk]
+        b = L.Batch([dict(nx=w.nx, ny=w.ny, storage=storage, **w.params) for w in part], stream=stream)
+        try:
+            for w, d in zip(part, b.domains):
+                d.set_geometry(w.mask)
+                d.set_rho_u(w.rho)
+            st, obs, _ = b.run_to_steady(rel_tol, check_every, max_steps)
+            for d in b.domains:
+                fields.append(d.fields_device().float())
+        finally:
+            b.close()
+        steps += st
+        flux += [o["flux_Q"] for o in obs]
+    return dict(fields=torch.stack(fields), steps=torch.tensor(steps), flux=torch.tensor(flux, dtype=torch.float64))
+
+
+def fit_normalisation(net, fields, mask):
+    """Density mean/std over fluid nodes and the velocity scale (largest |u_x|)."""
+    fl = mask == 0
+    rho = fields[:, 0][fl]
+    net.norm = dict(rho_mean=float(rho.mean()), rho_std=float(rho.std()),
+                    u_scale=float(fields[:, 1][fl].abs().max()))
+    return net.norm
+
+
+def train(net, planes, targets, epochs=20, lr=2e-3, wc=(1.0, 1.0, 0.25), seed=0, lr_final=1e-4):
+    """Adam over shuffled mini-batches (the network's batch size) with a
+    cosine learning-rate decay from lr to lr_final; returns the mean loss of
+    every epoch."""
+    import math
+    t = net.torch
+    g = t.Generator().manual_seed(seed)
+    n = planes.shape[0]
+    per_epoch = n // net.batch
+    total = epochs * per_epoch
+    history = []
+    k = 0
+    for _ in range(epochs):
+        perm = t.randperm(n, generator=g).to(planes.device)
+        acc = t.zeros(1, dtype=t.float64, device=planes.device)
+        for j in range(per_epoch):
+            idx = perm[j * net.batch:(j + 1) * net.batch]
+            net.forward(planes[idx])
+            acc += net.loss_backward(targets[idx], wc, sync=False)
+            rate = lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * k / max(1, total - 1)))
+            net.adam(lr=rate)
+            k += 1
+        history.append(float(acc.item()) / per_epoch)
+    return history
+
+
+def fit(ws, epochs=40, lr=2e-3, batch=16, seed=0, stream=None, wc=(1.0, 1.0, 0.25), **steady_kw):
+    """Generate the steady states of ``ws`` with the method itself, then
+    train a surrogate on them with the hand-written kernels. Returns the
+    network (norm set) and a dict of timings and the loss history."""
+    import time
+    import torch
+    info = {}
+    t0 = time.perf_counter()
+    data = steady_states(ws, stream=stream, **steady_kw)
+    torch.cuda.synchronize()
+    info["generate_s"] = time.perf_counter() - t0
+    keep = data["steps"] > 0
+    info["samples"] = int(keep.sum())
+    net = UNet(batch=batch, height=ws[0].ny, width=ws[0].nx, seed=seed, stream=stream)
+    fields = data["fields"][keep.to(data["fields"].device)]
+    masks = torch.as_tensor(np.stack([w.mask for w, k in zip(ws, keep.tolist()) if k]), device=fields.device)
+    fit_normalisation(net, fields, masks)
+    planes = channel_planes(net, [w for w, k in zip(ws, keep.tolist()) if k])
+    targets = fields.clone()
+    targets[:, 0] = (targets[:, 0] - net.norm["rho_mean"]) / net.norm["rho_std"]
+    targets[:, 1:] /= net.norm["u_scale"]
+    targets = torch.where(masks[:, None] == 0, targets, 0.0)
+    t0 = time.perf_counter()
+    info["loss"] = train(net, planes, targets, epochs=epochs, lr=lr, wc=wc, seed=seed)
+    torch.cuda.synchronize()
+    info["train_s"] = time.perf_counter() - t0
+    return net, info
+
+
+def warm_fields(pred, w):
+    """Prediction -> (rho, u_x, u_y) FP64 device tensors for lbm_set_field
+    (LBM_RHO_U_PHYS): densities clipped to the coexistence range, zero on
+    solid nodes, and scaled so that the mass equals that of the cold start
+    (the steady state the method reaches depends on the mass it conserves)."""
+    import torch
+    from . import workloads as wl
+    rho, ux, uy = pred
+    fluid = torch.as_tensor(w.mask == 0, device=rho.device)
+    rho = torch.where(fluid, rho.double().clamp(0.5 * wl.RHO_V, 1.1 * wl.RHO_L), 0.0)
+    m0 = float(np.sum(np.where(w.mask == 0, w.rho, 0.0)))
+    rho = rho * (m0 / float(rho.sum()))
+    z = torch.zeros((), dtype=torch.float64, device=rho.device)
+    return rho, torch.where(fluid, ux.double(), z), torch.where(fluid, uy.double(), z)
+
+
+def batch_run_to_steady(ws, net=None, stream=None, rel_tol=1e-7, check_every=1000, max_steps=60000,
+                        storage=None, policy=flat_walls, probe_checks=2, fallback_tol=0.05):
+    """All workloads in one batch, run to steady flux; with a surrogate
+    ``net``, the domains that ``policy`` accepts start from its prediction.
+
+    A warm-started domain is set through LBM_RHO_U_PHYS (the predicted u is
+    the physical velocity). After ``probe_checks`` convergence intervals, a
+    warm-started domain restarts from its cold start if it went non-finite,
+    or if its flux residual |dQ|/|Q| per interval is still above
+    ``fallback_tol`` and did not drop over the probe (a cold start's
+    residual after two intervals is of order 1, a useful warm start's
+    1e-2 or less); the run then goes on
+    to convergence as lbm_batch_run_to_steady defines it. Returns (steps [N]
+    counted from the first step, including any probe before a restart, obs
+    list, info) with info = {warm, restarted: [N] flags, probe_residuals:
+    [N] lists}."""
+    from . import lbm as L
+    storage = L.LBM_FP32_DEV if storage is None else storage
+    warm = [net is not None and bool(policy(w.mask)) for w in ws]
+    pred = None
+    if any(warm):
+        sel = [w for w, f in zip(ws, warm) if f]
+        pred = net.predict(channel_planes(net, sel))
+    b = L.Batch([dict(nx=w.nx, ny=w.ny, storage=storage, **w.params) for w in ws], stream=stream)
+    info = dict(warm=warm, restarted=[False] * len(ws), probe_residuals=[[] for _ in ws])
+    try:
+        k = 0
+        for w, d, f in zip(ws, b.domains, warm):
+            d.set_geometry(w.mask)
+            if f:
+                d.set_rho_u(*warm_fields((pred[0][k], pred[1][k], pred[2][k]), w), physical=True)
+                k += 1
+            else:
+                d.set_rho_u(w.rho)
+        if any(warm) and probe_checks > 0:
+            q = [[o["flux_Q"] for o in b.observables(check_finite=False)]]
+            for _ in range(probe_checks):
+                b.step(check_every)
+                q.append([o["flux_Q"] if o["nonfinite"] == 0 else float("nan")
+                          for o in b.observables(check_finite=False)])
+            for i, (w, d) in enumerate(zip(ws, b.domains)):
+                if not warm[i]:
+                    continue
+                res = [abs(q[j + 1][i] - q[j][i]) / max(abs(q[j + 1][i]), 1e-300) for j in range(probe_checks)]
+                info["probe_residuals"][i] = res
+                stuck = res[-1] > fallback_tol and res[-1] >= res[0]
+                if not all(np.isfinite(res)) or stuck:
+                    d.set_rho_u(w.rho)
+                    info["restarted"][i] = True
+        steps, obs, _ = b.run_to_steady(rel_tol, check_every, max_steps)
+    finally:
+        b.close()
+    return steps, obs, info

@@ -139,6 +139,7 @@ class Workload:
     mask: np.ndarray
     rho: np.ndarray
     params: dict
+    meta: dict = dataclasses.field(default_factory=dict)
 
     @property
     def ux(self):
@@ -184,7 +185,8 @@ def rough_channel(nx=1024, ny=128, amp=8, level=0, seed=0, fill=None, body_fx=1e
         fill = max(0.1, 1.0 - 2.0 * (amp + 1) / (ny - 2))
     rho = slab_field(nx, ny, fill, mask=mask)
     return Workload(f"rough_channel_{nx}x{ny}", nx, ny, mask, rho,
-                    dict(PAPER, tau=1.0, f_elec=f_level(level), body_fx=body_fx, body_fy=0.0))
+                    dict(PAPER, tau=1.0, f_elec=f_level(level), body_fx=body_fx, body_fy=0.0),
+                    dict(amp=amp, level=level, fill=fill, seed=seed))
 
 
 def droplet_row_channel(nx=16384, ny=4096, amp=6, seed=0, radius=20.0, pitch=128,
@@ -219,4 +221,49 @@ def batched_channels(count=256, seed=0):
         amp = min(rng.randint(0, 8), (ny - 3) // 2)
         level = rng.randint(0, 15)
         out.append(dict(nx=nx, ny=ny, amp=amp, level=level, seed=rng.next()))
+    return out
+
+
+def warm_start_channels(count, seed=0, nx=256, ny=64, body_fx=1e-5):
+    """Channels of the warm-start surrogate: nx x ny rough channels of the
+    rough-channel recipe with roughness amplitude 0-8, electric-force level
+    0-15 and a fill fraction drawn between the crest fill (liquid up to the
+    tallest roughness elements) and halfway from there to a full channel,
+    from one seed. A lower fill leaves the liquid floating on vapor layers,
+    where the body force accelerates it without bound."""
+    rng = SplitMix64(seed)
+    out = []
+    for _ in range(count):
+        amp = rng.randint(0, 8)
+        level = rng.randint(0, 15)
+        crest = 1.0 - 2.0 * (amp + 1) / (ny - 2)
+        fill = crest + 0.5 * (1.0 - crest) * rng.uniform()
+        out.append(rough_channel(nx=nx, ny=ny, amp=amp, level=level, seed=rng.next(), fill=fill,
+                                 body_fx=body_fx))
+    return out
+
+
+def smooth_channels(count, seed=0, nx=256, ny=64, body_fx=1e-5):
+    """Flat-wall channels (the smooth-channel geometry) of varying height:
+    bottom and top walls 1 + U{0..8} rows thick, electric-force level 0-15,
+    a centred liquid slab whose fill fraction of the free gap is drawn
+    between the crest fill 1 - 2/gap and 1, from one seed."""
+    rng = SplitMix64(seed)
+    out = []
+    for _ in range(count):
+        tb, tt = rng.randint(0, 8), rng.randint(0, 8)
+        level = rng.randint(0, 15)
+        mask = np.zeros((ny, nx), dtype=np.uint8)
+        mask[:1 + tb] = 1
+        mask[ny - 1 - tt:] = 1
+        gap = ny - 2 - tb - tt
+        crest = 1.0 - 2.0 / gap
+        fill = crest + (1.0 - crest) * rng.uniform()
+        ys = np.arange(ny, dtype=np.float64)
+        centre = 0.5 * ((1 + tb) + (ny - 2 - tt))
+        prof = tanh_profile(np.abs(ys - centre) - 0.5 * fill * gap, RHO_L, RHO_V, 4.0)
+        rho = np.where(mask != 0, 0.0, np.broadcast_to(prof[:, None], (ny, nx)))
+        out.append(Workload(f"smooth_channel_{nx}x{ny}", nx, ny, mask, rho,
+                            dict(PAPER, tau=1.0, f_elec=f_level(level), body_fx=body_fx, body_fy=0.0),
+                            dict(amp=0, level=level, fill=fill, seed=seed, walls=(tb, tt))))
     return out

@@ -123,3 +123,24 @@ def test_batch_rejects_mixed_storage(lbm):
     sp[1]["storage"] = 1
     with pytest.raises(lbm.LbmError):
         lbm.Batch(sp)
+
+
+def test_batch_run_to_steady_drops_non_finite_domain(lbm):
+    """A domain that turns non-finite (here: a NaN density planted in its
+    initial field on the host) is dropped with steps -2; the others still
+    run to steady flux, and the call reports LBM_ENAN."""
+    from tests.test_gpu_steady import smooth_channel
+    ws = [smooth_channel(0), smooth_channel(10)]
+    b = lbm.Batch(specs_of(ws, storage=1))
+    for w, d in zip(ws, b.domains):
+        d.set_geometry(w.mask)
+    rho = ws[0].rho.copy()
+    rho[20, 64] = np.nan
+    b.domains[0].set_rho_u(rho)
+    b.domains[1].set_rho_u(ws[1].rho)
+    steps, obs, ok = b.run_to_steady(1e-7, 1000, 80000)
+    assert not ok
+    assert steps[0] == -2 and obs[0]["nonfinite"] > 0
+    assert steps[1] > 0 and np.isfinite(obs[1]["flux_Q"])
+    assert "non-finite" in lbm._batch_lib().lbm_batch_last_error(b.handle).decode()
+    b.close()

@@ -182,6 +182,35 @@ def test_fields_match_oracle(lbm):
     assert np.abs(uy_g - uy_r).max() <= 1e-5 * umax
 
 
+def test_physical_velocity_state_matches_oracle(lbm):
+    """LBM_RHO_U_PHYS: the state built from (rho, u), u the physical
+    velocity, equals the oracle's equilibrium_physical populations, reads
+    back as (rho, u) and steps like the oracle."""
+    w = wl.rough_channel(nx=200, ny=48, amp=6, level=15, seed=4, body_fx=1e-5)
+    p = oracle.Params(w.nx, w.ny, **w.params)
+    f = oracle.step(p, w.mask, oracle.equilibrium(p, w.mask, w.rho, 0, 0), 200)
+    rho, ux, uy = oracle.fields(p, w.mask, f)
+    f_phys = oracle.equilibrium_physical(p, w.mask, rho, ux, uy)
+    lat = lbm.Lattice(w.nx, w.ny, **w.params)
+    lat.set_geometry(w.mask)
+    lat.set_rho_u(rho, ux, uy, physical=True)
+    assert_pops(lat.populations(), f_phys, w.mask)
+    r2, u2, v2 = lat.fields()
+    _, jx, jy, t = oracle.forces(p, w.mask, f_phys)
+    fl = w.mask == 0
+    scale = (rho + np.abs(jx) + np.abs(jy) + 0.5 * (np.abs(t[0::2].sum(0)) + np.abs(t[1::2].sum(0))))[fl] / rho[fl]
+    np.testing.assert_allclose(r2[fl], rho[fl], rtol=2e-6)
+    assert np.all(np.abs(u2[fl] - ux[fl]) <= 2e-6 * scale)
+    assert np.all(np.abs(v2[fl] - uy[fl]) <= 2e-6 * scale)
+    # the plain (rho, u) state differs by the F/2 shift at interfaces
+    lat_plain = lbm.Lattice(w.nx, w.ny, **w.params)
+    lat_plain.set_geometry(w.mask)
+    lat_plain.set_rho_u(rho, ux, uy)
+    assert np.abs(lat_plain.fields()[2] - uy)[fl].max() > 1e3 * np.abs(v2 - uy)[fl].max()
+    lat.step(100)
+    assert_pops(lat.populations(), oracle.step(p, w.mask, f_phys, 100), w.mask)
+
+
 def test_population_round_trip_and_resume(lbm):
     """set/get of populations is exact in FP32, and a run resumed from a
     checkpoint is bitwise identical to an uninterrupted one."""

@@ -89,3 +89,39 @@ def test_fields_of_equilibrium_state():
     np.testing.assert_allclose(rho, 0.85, rtol=1e-15)
     np.testing.assert_allclose(ux, 0.0, atol=1e-16)
     np.testing.assert_allclose(uy, 0.0, atol=1e-16)
+
+
+def test_equilibrium_physical_round_trip():
+    """The state built for a physical velocity u reads back, through the
+    separately pinned fields() (u = (j + F/2)/rho), as exactly (rho, u):
+    random density with a liquid/vapor mix, rough walls, electric and body
+    force all active."""
+    rng = np.random.default_rng(3)
+    ny, nx = 12, 16
+    mask = np.zeros((ny, nx), np.uint8)
+    mask[0, :] = mask[-1, :] = 1
+    mask[1, 3:6] = 1
+    p = oracle.Params(nx, ny, tau=1.0, G=-0.52, G_wall=-0.14, f_elec=0.2, body_fx=1e-3, body_fy=-2e-4)
+    rho = np.where(rng.random((ny, nx)) < 0.5, 2.8, 0.07) * (1 + 0.05 * rng.standard_normal((ny, nx)))
+    ux = 0.02 * rng.standard_normal((ny, nx))
+    uy = 0.02 * rng.standard_normal((ny, nx))
+    f = oracle.equilibrium_physical(p, mask, rho, ux, uy)
+    r2, u2, v2 = oracle.fields(p, mask, f)
+    fl = mask == 0
+    np.testing.assert_allclose(r2[fl], rho[fl], rtol=1e-14)
+    np.testing.assert_allclose(u2[fl], ux[fl], rtol=0, atol=1e-13)
+    np.testing.assert_allclose(v2[fl], uy[fl], rtol=0, atol=1e-13)
+    # and the force shift is not trivial here
+    plain = oracle.equilibrium(p, mask, rho, ux, uy)
+    assert np.max(np.abs(plain - f)) > 1e-3
+
+
+def test_equilibrium_physical_body_force_only():
+    """With only a body force, F = rho f_b and the equilibrium velocity is
+    u - f_b/2 at every node (no walls)."""
+    ny, nx = 4, 6
+    p = oracle.Params(nx, ny, G=0.0, G_wall=0.0, body_fx=4e-3, body_fy=-1e-3)
+    mask = np.zeros((ny, nx), np.uint8)
+    f = oracle.equilibrium_physical(p, mask, 1.3, 0.01, 0.02)
+    ref = oracle.equilibrium(p, mask, 1.3, 0.01 - 2e-3, 0.02 + 5e-4)
+    np.testing.assert_allclose(f, ref, rtol=1e-15, atol=1e-17)
