@@ -81,7 +81,8 @@ enum { LBM_GREEN_MC = 0, LBM_GREEN_PRINTED = 1 };
  *               evolving in this form (plain FP32 stalls short of the steady
  *               state, e.g. 0.4% low in the flux of a channel driven by 1e-6).
  * LBM_FP16_DEV / LBM_BF16_DEV: as LBM_FP32_DEV with d_a in 16 bits (20 B per
- *               node, rounded to nearest); nx must be a multiple of 8. */
+ *               node, rounded to nearest; FP16 holds 2^12 d_a, so |d_a| must
+ *               stay below 16); nx must be a multiple of 8. */
 enum { LBM_FP32 = 0, LBM_FP32_DEV = 1, LBM_FP16_DEV = 2, LBM_BF16_DEV = 3 };
 
 /* Field selectors for lbm_set_field / lbm_get_field (LBM_RHO_U_PHYS: set only). */

@@ -83,12 +83,19 @@ template <int ST> __host__ __device__ constexpr size_t smem_bytes()
 // bytes of one node's state in global memory (plane 0 + planes 1..8)
 template <int ST> __host__ __device__ constexpr int node_bytes() { return 4 + 8 * int(sizeof(typename StoreT<ST>::T)); }
 
+// FP16 deviations are stored scaled by 2^12 (an exact scaling): |d| up to 16
+// stays below the FP16 maximum 65504, and deviations down to 2^-26 stay in
+// FP16's normal range. Unscaled, the deviations of slowly moving vapor
+// (~1e-7) would be subnormal, with a few correct bits at most, and the flux
+// of a body-force-driven channel would be off by percents.
+constexpr float kF16Scale = 4096.f, kF16Unscale = 1.f / 4096.f;
+
 __device__ __forceinline__ float to_f(float v) { return v; }
-__device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_f(__half v) { return __half2float(v) * kF16Unscale; }
 __device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
 template <typename T> __device__ __forceinline__ T from_f(float v);
 template <> __device__ __forceinline__ float from_f<float>(float v) { return v; }
-template <> __device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v * kF16Scale); }
 template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 
 constexpr size_t kSmemBytes = smem_bytes<kF32>();

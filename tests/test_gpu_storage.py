@@ -18,8 +18,8 @@ pytestmark = pytest.mark.gpu
 # stated bounds for the 16-bit forms after 100 steps:
 # (relative L2 of populations, relative mass error, |dQ| / sum|u_x|/nx, rel. max|u|)
 BOUNDS16 = {
-    "fp16": (3e-4, 2e-5, 5e-3, 5e-3),
-    "bf16": (3e-3, 2e-4, 5e-2, 5e-2),
+    "fp16": (1e-4, 5e-8, 1e-3, 1e-3),
+    "bf16": (6e-4, 5e-8, 1e-3, 5e-3),
 }
 
 
