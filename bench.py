@@ -227,7 +227,7 @@ def run_reference(args, rank, world):
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
-    from paper_0708_4182_gb300 import lbm
+    from paper_0708_4182_gb300 import lbm, replicas
 
     torch.cuda.set_device(local_rank)
     w = workload(args.nx, args.ny)
@@ -260,12 +260,11 @@ def run_ours(args, rank, world, local_rank):
     ck = clocks.stop()
     ms = e0.elapsed_time(e1)
     obs = lat.obs_latest()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    # every rank advanced its own replica: all ranks' node updates over the
+    # slowest rank's time
+    ms = replicas.max_over_ranks(ms, device="cuda")
     ms_step = ms / args.steps
-    mlups = world * n_nodes * args.steps / (ms * 1e-3) / 1e6
+    mlups = replicas.sum_over_ranks(n_nodes * args.steps, device="cuda") / (ms * 1e-3) / 1e6
     # one fused step kernel per step, plus one finalize kernel per observed step
     launches = args.steps + sum(1 for t in range(args.warmup, args.warmup + args.steps)
                                 if args.obs_every and t % args.obs_every == 0)
@@ -288,11 +287,11 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_e2e:
         e2e = run_e2e(args, w, params, lbm, stream, world)
     extra = {}
-    if not args.no_batch and world == 1:
+    if not args.no_batch:
         lat.close()
         del lat
         torch.cuda.empty_cache()
-        extra = run_batch_measurements(lbm, stream)
+        extra = run_batch_measurements(lbm, stream, rank, world)
 
     line = {"metric": "MLUPS", "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 5),
@@ -321,6 +320,7 @@ KERNEL_VERSION = "step-v5"
 def run_e2e(args, w, params, lbm, stream, world):
     import torch
     import torch.distributed as dist
+    from paper_0708_4182_gb300 import replicas
     p = dict(params, obs_every=1)
     rho_u = np.stack([w.rho, np.zeros_like(w.rho), np.zeros_like(w.rho)])
     mask = np.ascontiguousarray(w.mask)
@@ -339,12 +339,9 @@ def run_e2e(args, w, params, lbm, stream, world):
         lbm.lbm_obs_latest(lat.ctx)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([dt], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dt = float(t.item())
     lat.close()
-    return {"value": round(world * w.nx * w.ny * steps / dt / 1e6, 1), "unit": "MLUPS",
+    thr = replicas.job_throughput(w.nx * w.ny * steps, dt, device="cuda")
+    return {"value": round(thr / 1e6, 1), "unit": "MLUPS",
             "h2d_bytes_per_step": int((rho_u.nbytes + mask.nbytes) / steps),
             "d2h_bytes_per_step": 64,
             "what": "host mask + FP64 (rho,u) upload, then per step lbm_step + fused observables read-back"}
@@ -377,10 +374,17 @@ def steady_sweep(count=32, seed=1, scale=4):
     return ws
 
 
-def run_batch_measurements(lbm, stream):
+def run_batch_measurements(lbm, stream, rank=0, world=1):
+    """Batched-sweep throughput (its domains split over the ranks, no
+    collective in the data path) and, on a single GPU, the time-to-steady
+    comparisons."""
     import torch
+    import torch.distributed as dist
+    from paper_0708_4182_gb300 import replicas
     out = {}
-    ws = batched_sweep()
+    all_ws = batched_sweep()
+    mine = replicas.partition([w.nx * w.ny for w in all_ws], rank, world)
+    ws = [all_ws[i] for i in mine]
     nodes = sum(w.nx * w.ny for w in ws)
     b = lbm.Batch([dict(nx=w.nx, ny=w.ny, **w.params) for w in ws], stream=stream)
     for w, d in zip(ws, b.domains):
@@ -389,12 +393,15 @@ def run_batch_measurements(lbm, stream):
     cands = (8, 16, 32, 64, 128)
     chosen, ms = b.autotune(cands, steps=10)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
     torch.cuda.synchronize()
     e0.record(stream)
     b.step(100)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms_step = e0.elapsed_time(e1) / 100
+    ms_step = replicas.max_over_ranks(e0.elapsed_time(e1) / 100, device="cuda")
+    nodes = int(replicas.sum_over_ranks(nodes, device="cuda"))
     # the same domains one at a time (first 32, 20 steps each)
     seq_t, seq_nodes = 0.0, 0
     for w, d in zip(ws[:32], b.domains[:32]):
@@ -406,11 +413,14 @@ def run_batch_measurements(lbm, stream):
         seq_nodes += 20 * w.nx * w.ny
     b.close()
     out["batched"] = {
-        "workload": f"{len(ws)} rough channels (width 32-256, length 512-2048, roughness 0-8, level 0-15, "
-                    f"seed 0), FP32 populations, one persistent launch per step",
+        "workload": f"{len(all_ws)} rough channels (width 32-256, length 512-2048, roughness 0-8, level 0-15, "
+                    f"seed 0), FP32 populations, one persistent launch per step"
+                    + (f", split over {world} ranks by node count" if world > 1 else ""),
         "nodes": nodes, "mlups": round(nodes / ms_step / 1e3, 1), "ms_per_step": round(ms_step, 4),
         "tile_rows": chosen, "autotune_ms_per_step": {str(c): round(m, 4) for c, m in zip(cands, ms)},
         "one_domain_at_a_time_mlups": round(seq_nodes / seq_t / 1e6, 1)}
+    if world > 1:
+        return out
 
     # time to steady flux: plain one domain at a time vs one batch
     ws = steady_sweep()
