@@ -434,7 +434,7 @@ template <typename T, int R>
 __device__ __forceinline__ void pull_dev(const float* __restrict__ s0m, const float* __restrict__ s0c,
                                          const float* __restrict__ s0p, const T* __restrict__ sdm,
                                          const T* __restrict__ sdc, const T* __restrict__ sdp, int c,
-                                         PulledDev& n)
+                                         bool need_g, PulledDev& n)
 {
     const float r0 = s0c[c];
     n.solid = is_solid(r0);
@@ -477,9 +477,12 @@ __device__ __forceinline__ void pull_dev(const float* __restrict__ s0m, const fl
                                         (d[1] - d[3]) + (d[5] - d[7]) + (d[8] - d[6])));
     n.jy = fmaf(w1, rs[2] - rs[4], fmaf(w2, (rs[5] - rs[7]) + (rs[6] - rs[8]),
                                         (d[2] - d[4]) + (d[5] - d[7]) + (d[6] - d[8])));
-    // g_a = f_a - w_a rho = w_a ((rho*_src - rho*(x)) - drho) + d_a(src)
+    // g_a = f_a - w_a rho = w_a ((rho*_src - rho*(x)) - drho) + d_a(src);
+    // only the relaxation with tau != 1 reads it
+    if (need_g) {
 #pragma unroll
-    for (int a = 1; a < 9; ++a) n.g[a] = fmaf(a <= 4 ? w1 : w2, (rs[a] - r0) - drho, d[a]);
+        for (int a = 1; a < 9; ++a) n.g[a] = fmaf(a <= 4 ? w1 : w2, (rs[a] - r0) - drho, d[a]);
+    }
     n.g[0] = 0.f;
     n.sb = sb;
 }
@@ -695,7 +698,8 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
         if constexpr (ST == kF32)
             pull_smem(stage0(sm), stage0(sc), stage0(sp), col, n);
         else
-            pull_dev<T, R>(stage0(sm), stage0(sc), stage0(sp), staged(sm), staged(sc), staged(sp), col, n);
+            pull_dev<T, R>(stage0(sm), stage0(sc), stage0(sp), staged(sm), staged(sc), staged(sp), col,
+                           p.tau != 1.f, n);
     };
 
     for (int k = 1; k <= nrows - 2; ++k) {
