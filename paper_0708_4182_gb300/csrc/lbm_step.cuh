@@ -276,6 +276,10 @@ __device__ __forceinline__ float pseudopotential(const Phys& p, const N& n)
 }
 
 // Error-free accumulation s + c of FP32 terms (Knuth's TwoSum).
+// FP32 sum with the exact rounding error of every addition (TwoSum)
+// collected in c: s + c carries about twice FP32's precision, so the sums of
+// cancelling quantities (momentum) do not depend on how nodes are split
+// among threads and tiles.
 struct Acc {
     float s = 0.f, c = 0.f;
     __device__ __forceinline__ void add(float v)
@@ -339,21 +343,23 @@ __device__ __forceinline__ void node_force(const N& n, const float* pm, const fl
 }
 
 // Observables or fields epilogue of one fluid node (modes other than kStep).
+// rinv is rcp_approx(rho); the quotients are corrected by one residual step.
 template <int MODE>
-__device__ __forceinline__ void node_observe(float rho, float jx, float jy, float Fx, float Fy,
+__device__ __forceinline__ void node_observe(float rho, float rinv, float jx, float jy, float Fx, float Fy,
                                              const Geom& g, double* __restrict__ fields, int x, int r,
                                              ObsAcc& acc)
 {
     // physical velocity u = (rho u + F/2)/rho
     const float mx = fmaf(0.5f, Fx, jx), my = fmaf(0.5f, Fy, jy);
-    const float vx = __fdiv_rn(mx, rho), vy = __fdiv_rn(my, rho);
+    const float vx = div_corrected(mx, rho, rinv), vy = div_corrected(my, rho, rinv);
     if constexpr (MODE == kFields) {
         const size_t i = (size_t)r * g.nx + x, nn = (size_t)g.nx * g.ny;
         fields[i] = rho;
         fields[nn + i] = vx;
         fields[2 * nn + i] = vy;
     } else {
-        if (isfinite(rho) && isfinite(vx) && isfinite(vy)) {
+        // a NaN or infinity in any of the three makes the sum non-finite
+        if (isfinite(rho + vx + vy)) {
             acc.mass.add(rho);
             acc.q.add(vx);
             acc.px.add(mx);
@@ -377,13 +383,13 @@ __device__ __forceinline__ void collide_node(const Pulled& n, const float* pm, c
 {
     float Fx, Fy;
     node_force(n, pm, pc, pp, t, p, Fx, Fy);
+    const float rinv = rcp_approx(n.rho);
     if constexpr (MODE == kStep || MODE == kStepObs) {
         // Eq. 10 velocity shift, Eq. 3 equilibrium, Eq. 1 relaxation.
         // FP32 care: u' by corrected quotients; the weights w_a rho all derive
         // from one corrected rho/9 by exact power-of-two scalings, so
         // sum_a f_eq = rho has no systematic bias (1/9 in FP32 is 7.5e-9 too
         // large, which would add mass every step); at tau = 1 f* = f_eq.
-        const float rinv = rcp_approx(n.rho);
         const float ux = div_corrected(fmaf(p.tau, Fx, n.jx), n.rho, rinv);
         const float uy = div_corrected(fmaf(p.tau, Fy, n.jy), n.rho, rinv);
         const float om = 1.f - 1.5f * fmaf(ux, ux, uy * uy);
@@ -414,7 +420,7 @@ __device__ __forceinline__ void collide_node(const Pulled& n, const float* pm, c
             }
         }
     }
-    if constexpr (MODE != kStep) node_observe<MODE>(n.rho, n.jx, n.jy, Fx, Fy, g, fields, x, r, acc);
+    if constexpr (MODE != kStep) node_observe<MODE>(n.rho, rinv, n.jx, n.jy, Fx, Fy, g, fields, x, r, acc);
 }
 
 // ------------------------------------------------------------------ deviation storage
@@ -498,8 +504,8 @@ __device__ __forceinline__ void collide_dev(const PulledDev& n, const float* pm,
 {
     float Fx, Fy;
     node_force(n, pm, pc, pp, t, p, Fx, Fy);
+    const float rinv = rcp_approx(n.rho);
     if constexpr (MODE == kStep || MODE == kStepObs) {
-        const float rinv = rcp_approx(n.rho);
         const float ux = div_corrected(fmaf(p.tau, Fx, n.jx), n.rho, rinv);
         const float uy = div_corrected(fmaf(p.tau, Fy, n.jy), n.rho, rinv);
         const float usq = 1.5f * fmaf(ux, ux, uy * uy);
@@ -527,7 +533,7 @@ __device__ __forceinline__ void collide_dev(const PulledDev& n, const float* pm,
                 foutd[(a - 1) * g.plane + o] = from_f<T>(fmaf(dq[a] - n.g[a], p.inv_tau, n.g[a]));
         }
     }
-    if constexpr (MODE != kStep) node_observe<MODE>(n.rho, n.jx, n.jy, Fx, Fy, g, fields, x, r, acc);
+    if constexpr (MODE != kStep) node_observe<MODE>(n.rho, rinv, n.jx, n.jy, Fx, Fy, g, fields, x, r, acc);
 }
 
 // ------------------------------------------------------------------ kernel
