@@ -127,8 +127,9 @@ def test_one_step_matches_exact_arithmetic(name, tau):
 
 
 def test_bruteforce_detects_a_planted_error():
-    """A wrong diagonal Green weight (G instead of G/2) in the restatement is
-    far outside the agreement bound, so the bound has teeth."""
+    """A planted weight error in the oracle (the printed 2G/G Green weights
+    instead of G/G/2) lands far outside the agreement bound, so the bound
+    has teeth."""
     nx, ny, solids = CASES["4x4 solid bottom row"]
     solid = np.zeros((ny, nx), np.uint8)
     for x, y in solids:
