@@ -300,7 +300,8 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": workload_name(w.nx, w.ny), "nx": w.nx, "ny": w.ny,
                        "fluid_nodes": n_fluid, "obs_every": args.obs_every, "storage": args.storage,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "l2": "inputs larger than L2 (2 x 2.4 GB population buffers)",
+                       "l2": f"inputs larger than L2 (2 x {9 * 4 * w.nx * w.ny / 1e9:.2f} GB population buffers)"
+                             if 2 * 36 * w.nx * w.ny > 129e6 else "inputs fit in L2 (small case)",
                        "fluid_mlups": round(world * n_fluid * args.steps / (ms * 1e-3) / 1e6, 1)},
             "roofline": roof,
             "clocks": ck,
