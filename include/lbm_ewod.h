@@ -85,8 +85,9 @@ enum { LBM_GREEN_MC = 0, LBM_GREEN_PRINTED = 1 };
  *               stay below 16); nx must be a multiple of 8. */
 enum { LBM_FP32 = 0, LBM_FP32_DEV = 1, LBM_FP16_DEV = 2, LBM_BF16_DEV = 3 };
 
-/* Field selectors for lbm_set_field / lbm_get_field (LBM_RHO_U_PHYS: set only). */
-enum { LBM_RHO_U = 0, LBM_POPS = 1, LBM_RHO_U_PHYS = 2 };
+/* Field selectors for lbm_set_field / lbm_get_field (LBM_RHO_U_PHYS: set
+ * only; LBM_UX_PROFILE: get only). */
+enum { LBM_RHO_U = 0, LBM_POPS = 1, LBM_RHO_U_PHYS = 2, LBM_UX_PROFILE = 3 };
 
 typedef struct {
     int32_t nx, ny;    /* lattice size; x and y are periodic, walls come
@@ -156,6 +157,10 @@ lbm_status lbm_set_field(lbm_ctx *ctx, int which, const double *data, int on_dev
 /* Read the current state into out (layouts as for lbm_set_field).
  * LBM_RHO_U: rho and the velocity u = (sum_a f_a e_a + F/2)/rho, 0 on solids.
  * LBM_POPS:  post-streaming populations f_a(x, t), 0 on solids.
+ * LBM_UX_PROFILE: double[ny], the mean velocity profile across the channel
+ *            u_x(y) averaged over x, (1/nx) sum_x u_x(x, y), solid nodes
+ *            counting 0 (the channel velocity profiles of the paper's
+ *            rough-channel figures; summed over y it is Eq. 11's Q).
  * Synchronises the context's stream when out is host memory. */
 lbm_status lbm_get_field(lbm_ctx *ctx, int which, double *out, int on_device);
 

@@ -332,6 +332,26 @@ __global__ void dev_to_plain_kernel(const float* __restrict__ in, const uint8_t*
     }
 }
 
+// Mean velocity profile across the channel: out[y] = (1/nx) sum_x u_x(x, y)
+// from a kFields array (solid nodes hold 0), one block per row, FP64 tree sum.
+__global__ void ux_profile_kernel(const double* __restrict__ fields, Geom g, double* __restrict__ out)
+{
+    __shared__ double red[kAuxThreads];
+    const size_t nn = (size_t)g.nx * g.ny;
+    for (int y = blockIdx.x; y < g.ny; y += gridDim.x) {
+        double s = 0.0;
+        for (int x = threadIdx.x; x < g.nx; x += kAuxThreads) s += fields[nn + (size_t)y * g.nx + x];
+        red[threadIdx.x] = s;
+        __syncthreads();
+        for (int h = kAuxThreads / 2; h > 0; h >>= 1) {
+            if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[y] = red[0] / g.nx;
+        __syncthreads();
+    }
+}
+
 // Sum the per-CTA partials in a fixed order and write one lbm_obs record.
 __global__ void finalize_obs_kernel(const double* __restrict__ partials, int nctas, double inv_nx,
                                     long long step, lbm_obs* __restrict__ rec)
@@ -870,6 +890,25 @@ lbm_status lbm_get_field(lbm_ctx* c, int which, double* out, int on_device)
             if ((s = check_launch(c, "geometry kernel launch"))) return s;
         }
         return LBM_OK;
+    }
+    if (which == LBM_UX_PROFILE) {
+        // fields into the spare buffer (3n doubles), the profile after them
+        double* fld = reinterpret_cast<double*>(c->nxt);
+        double* dst = on_device ? out : fld + 3 * n;
+        if ((s = launch_step<kFields>(c, c->cur, nullptr, fld))) return s;
+        const int blocks = c->g.ny < 4 * c->sm_count ? c->g.ny : 4 * c->sm_count;
+        ux_profile_kernel<<<blocks, kAuxThreads, 0, c->stream>>>(fld, c->g, dst);
+        if ((s = check_launch(c, "profile kernel launch"))) return s;
+        if (!on_device) {
+            if ((s = check_cuda(c, cudaMemcpyAsync(out, dst, size_t(c->g.ny) * sizeof(double), cudaMemcpyDeviceToHost,
+                                                   c->stream), "profile download")))
+                return s;
+            if ((s = check_cuda(c, cudaStreamSynchronize(c->stream), "profile download sync"))) return s;
+            if ((s = check_status(c))) return s;
+        }
+        // the spare buffer served as scratch: restore its solid sentinels
+        geometry_kernel<<<aux_blocks(n, c->sm_count), kAuxThreads, 0, c->stream>>>(c->mask, c->nxt, c->nxt, c->g);
+        return check_launch(c, "geometry kernel launch");
     }
     if (which != LBM_POPS) return fail(c, LBM_EINVAL, "unknown field selector %d", which);
     const int nx = c->g.nx, ny = c->g.ny;

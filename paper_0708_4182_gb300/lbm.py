@@ -24,7 +24,7 @@ from . import build as _build
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENAN, LBM_ETIMEOUT, LBM_ESTATE, LBM_ENOTCONV = range(8)
 LBM_GREEN_MC, LBM_GREEN_PRINTED = 0, 1
 LBM_FP32, LBM_FP32_DEV, LBM_FP16_DEV, LBM_BF16_DEV = 0, 1, 2, 3
-LBM_RHO_U, LBM_POPS, LBM_RHO_U_PHYS = 0, 1, 2
+LBM_RHO_U, LBM_POPS, LBM_RHO_U_PHYS, LBM_UX_PROFILE = 0, 1, 2, 3
 
 
 class LbmUnavailable(RuntimeError):
@@ -282,6 +282,12 @@ class Lattice:
         import torch
         out = torch.empty((9, self.ny, self.nx), dtype=torch.float64, device=self.stream.device)
         lbm_get_field(self.ctx, LBM_POPS, out.data_ptr(), True)
+        return out
+
+    def ux_profile(self) -> np.ndarray:
+        """Mean velocity profile across the channel, (1/nx) sum_x u_x(x, y)."""
+        out = np.empty(self.ny)
+        lbm_get_field(self.ctx, LBM_UX_PROFILE, out.ctypes.data, False)
         return out
 
     def fields_device(self):

@@ -182,6 +182,24 @@ def test_fields_match_oracle(lbm):
     assert np.abs(uy_g - uy_r).max() <= 1e-5 * umax
 
 
+def test_ux_profile_matches_oracle(lbm):
+    """LBM_UX_PROFILE: the x-averaged u_x(y) of a rough channel against the
+    oracle's fields; summed over y it is the flux Q; the read-back leaves
+    the state intact (stepping on still matches the oracle)."""
+    w = wl.rough_channel(nx=256, ny=64, amp=6, level=10, seed=3, body_fx=1e-5)
+    p, f_ref, lat = run_both(lbm, w.mask, w.rho, w.params, 100)
+    prof = lat.ux_profile()
+    _, ux, _ = oracle.fields(p, w.mask, f_ref)
+    ref = np.where(w.mask == 0, ux, 0.0).mean(axis=1)
+    assert prof.shape == (w.ny,)
+    assert np.abs(prof - ref).max() <= 1e-5 * np.abs(ux).max()
+    assert np.all(prof[0] == 0.0) and np.all(prof[-1] == 0.0)  # wall rows
+    q = lat.observables()["flux_Q"]
+    assert prof.sum() == pytest.approx(q, rel=1e-9, abs=1e-12)
+    lat.step(50)
+    assert_pops(lat.populations(), oracle.step(p, w.mask, f_ref, 50), w.mask)
+
+
 def test_physical_velocity_state_matches_oracle(lbm):
     """LBM_RHO_U_PHYS: the state built from (rho, u), u the physical
     velocity, equals the oracle's equilibrium_physical populations, reads
