@@ -1201,7 +1201,18 @@ bool batch_layout(const lbm_params* p, int count, BatchLayout* L, const char** w
     return true;
 }
 
-int domain_tile_rows(const lbm_batch* b, const lbm_ctx* c) { return b->tile_rows ? b->tile_rows : c->g.tile_rows; }
+// Segment height of a domain's tiles: the requested height, evened out so
+// that the ceil(ny / height) segments differ by at most one row (a 40-row
+// channel at height 32 gets two segments of 20 rows, not 32 + 8: a short
+// last segment pays the pipeline start and the 4 re-staged halo rows for
+// few rows). The segment count is unchanged.
+int domain_tile_rows(const lbm_batch* b, const lbm_ctx* c)
+{
+    const int want = b->tile_rows ? b->tile_rows : c->g.tile_rows;
+    const int nseg = (c->g.ny + want - 1) / want;
+    const int even = (c->g.ny + nseg - 1) / nseg;
+    return even >= 4 ? even : want;
+}
 
 // Tile list of the active domains (or of all domains), largest domains first
 // so that the strided walk of the persistent grid ends evenly.
