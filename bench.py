@@ -315,7 +315,7 @@ def run_ours(args, rank, world, local_rank):
     return line
 
 
-KERNEL_VERSION = "step-v5"
+KERNEL_VERSION = "step-v6"
 
 
 def run_e2e(args, w, params, lbm, stream, world):

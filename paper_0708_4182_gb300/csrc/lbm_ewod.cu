@@ -93,11 +93,15 @@ int auto_tile_rows(int nx, int ny, int sm_count)
     // strips and hide the pipeline start of each CTA. Measured on the
     // 16384x4096 channel: 64 rows 90.8% of HBM peak, 48/96/160/192 rows
     // 88-90%, one wave of 586 rows 84%. Take 64 rows and halve it while
-    // the grid has fewer than 4 waves.
+    // the grid has fewer than 4 waves; then even the segments out (same
+    // count, heights differing by at most one row) so that no short last
+    // segment pays the pipeline start and halo rows for a few rows.
     const long long slots = 3LL * sm_count;
     int rows = 64;
     while (rows > 4 && (long long)ctas_x(nx) * ((ny + rows - 1) / rows) < 4 * slots) rows >>= 1;
-    return rows;
+    const int nseg = (ny + rows - 1) / rows;
+    const int even = (ny + nseg - 1) / nseg;
+    return even >= 4 ? even : rows;
 }
 
 // ---------------------------------------------------------------------------
