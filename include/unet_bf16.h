@@ -4,76 +4,108 @@
  * The paper has no learned component; this surrogate serves the batched
  * sweeps: from a channel's wall mask, electric-force level and fill fraction
  * it predicts the steady density and velocity, which initialise the lattice
- * Boltzmann run (lbm_set_field with LBM_RHO_U); the method then runs on to
- * convergence, so the surrogate's error never reaches the converged result.
+ * Boltzmann run (lbm_set_field with LBM_RHO_U_PHYS); the method then runs on
+ * to convergence, so the surrogate's error never reaches the converged result.
  *
- * Conventions: tensors are NCHW; BF16 tensors are passed as void* (bfloat16
- * values), FP32 as float*. "xbs" arguments are batch strides in elements, so
- * a tensor may be a channel range of a larger buffer (a concatenation).
- * 3x3 convolutions pad circularly in x and with zeros in y. All sums
- * accumulate in FP32. Every call enqueues on `stream` (a cudaStream_t) and
- * returns 0 on success, -1 for unsupported sizes (width and height must be
- * multiples of 32 and 4, output channels of the forward and weight-gradient
- * convolutions a multiple of 32), or a CUDA error code.
+ * Conventions: activations are BF16, channels-last (NHWC: element (b, y, x, c)
+ * at ((b * h + y) * w + x) * ct + c). A tensor argument is a "view": a pointer
+ * to its first channel and ct, the channels per pixel of the buffer it lives
+ * in, so a view may be a channel range of a larger buffer (a concatenation).
+ * BF16 tensors are passed as void*, FP32 as float*. 3x3 convolutions pad
+ * circularly in x and with zeros in y. All sums accumulate in FP32. Every call
+ * enqueues on `stream` (a cudaStream_t) and returns 0 on success, -1 for
+ * unsupported sizes or misaligned views (see each call), or a CUDA error code.
  */
 #ifndef UNET_BF16_H
 #define UNET_BF16_H
+
+#include <stddef.h>
 
 #ifdef __cplusplus
 extern "C" {
 #endif
 
-/* y[b, o] = relu?(bias[o] + sum_{i, taps} w[o][i][ky][kx] x[b, i, y+ky-1, x+kx-1]);
- * w: BF16 [co][ci][3][3]; bias: FP32 [co] (may be NULL); y: BF16. */
-int unet_conv3x3_fwd(const void *x, int ci, long xbs, const void *w, const float *bias, void *y, int co,
-                     long ybs, int n, int h, int wd, int relu, void *stream);
+/* Output-channel tile (128, 64 or 32) the convolution uses for `channels`
+ * output channels, and the number of BF16 elements of a packed weight
+ * operand (transpose = 0: forward, co output channels; transpose = 1: input
+ * gradient, ci output channels). */
+int unet_conv_ntile(int channels);
+size_t unet_conv_pack_elems(int co, int ci, int transpose);
 
-/* Gradient w.r.t. the input of unet_conv3x3_fwd (no activation):
- * dx[b, i] = sum_{o, taps} w[o][i][ky][kx] dy[b, o, y-ky+1, x-kx+1] (BF16 out). */
-int unet_conv3x3_bwd_data(const void *dy, int co, long dybs, const void *w, void *dx, int ci, long dxbs,
-                          int n, int h, int wd, void *stream);
+/* Pack FP32 master weights w [co][ci][3][3] into the tensor-core operand of
+ * unet_conv3x3: transpose = 0 for the forward convolution (output channels
+ * co), transpose = 1 for the gradient w.r.t. its input (the kernel
+ * transposed and flipped; output channels ci). The output count must be a
+ * multiple of 32; `out` holds unet_conv_pack_elems(co, ci, transpose)
+ * elements. */
+int unet_conv_pack(const float *w, int co, int ci, int transpose, void *out, void *stream);
 
-/* Gradients w.r.t. weights and bias, ACCUMULATED into FP32 dw [co][ci][3][3]
- * and db [co]: dw += sum_{b, pixels} dy x(shifted), db += sum dy. */
-int unet_conv3x3_bwd_weight(const void *x, int ci, long xbs, const void *dy, int co, long dybs, float *dw,
+/* 3x3 convolution on the tensor cores (tcgen05.mma, FP32 accumulation in
+ * tensor memory): y[b, p, o] = act(bias[o] + sum_{tap, i} W[o][i](tap)
+ * x[b, p + off(tap), i]) with W the packed operand `wt`; bias may be NULL,
+ * act = ReLU if relu != 0. With the transpose = 1 packing of a layer's
+ * weights, x = dy and y = dx, this is that layer's gradient w.r.t. its input.
+ * Requires wd % 32 == 0, h % 4 == 0, cout % 32 == 0, ct_in and ct_out
+ * multiples of 8, 16-byte aligned views, and cin a multiple of 16, or
+ * cin < 16 in a view of at least 16 readable channels whose channels >= cin
+ * are zero. */
+int unet_conv3x3(const void *x, int ct_in, int cin, const void *wt, const float *bias, void *y, int ct_out,
+                 int cout, int n, int h, int wd, int relu, void *stream);
+
+/* Gradients w.r.t. the weights and bias of unet_conv3x3 (forward packing),
+ * ACCUMULATED into FP32 dw [co][ci][3][3] and db [co]: dw += sum_{b, p}
+ * dy[b, p, o] x[b, p + off(tap), i] (tensor cores), db += sum dy. Requires
+ * wd % 16 == 0, co % 8 == 0, ct_x and ct_dy multiples of 8, 16-byte aligned
+ * views; x must have at least 8 readable channels when ci < 8. */
+int unet_conv3x3_bwd_weight(const void *x, int ct_x, int ci, const void *dy, int ct_dy, int co, float *dw,
                             float *db, int n, int h, int wd, void *stream);
 
-/* 1x1 output head (co <= 8, ci <= 64): y[b, o, p] = bias[o] + sum_i w[o][i] x[b, i, p]
- * with FP32 output y [n][co][hw]; backward gives BF16 dx and accumulates
- * FP32 dw [co][ci], db [co]. */
-int unet_head_fwd(const void *x, int ci, long xbs, const void *w, const float *bias, float *y, int co, int n,
+/* Sticky error flag of the tensor-core kernels (nonzero after an mbarrier
+ * wait timed out); reset != 0 clears it. Synchronises the stream. */
+int unet_tc_error(void *stream, int reset);
+
+/* 1x1 output head (co <= 8, ci <= 64): y[b, o, p] = bias[o] + sum_i w[o][i]
+ * x[b, p, i], with BF16 weights w [co][ci], NHWC input view and FP32 output y
+ * [n][co][hw] (NCHW); backward gives the NHWC BF16 dx and accumulates FP32
+ * dw [co][ci], db [co]. */
+int unet_head_fwd(const void *x, int ct, int ci, const void *w, const float *bias, float *y, int co, int n,
                   int hw, void *stream);
-int unet_head_bwd(const void *x, int ci, long xbs, const void *w, const float *dy, int co, int n, int hw,
-                  void *dx, long dxbs, float *dw, float *db, void *stream);
+int unet_head_bwd(const void *x, int ct, int ci, const void *w, const float *dy, int co, int n, int hw,
+                  void *dx, int ct_dx, float *dw, float *db, void *stream);
 
 /* 2x2 average pooling of an (h, wd) image and its adjoint (accumulate != 0
- * adds into dx instead of overwriting). */
-int unet_pool2_fwd(const void *x, long xbs, void *y, long ybs, int c, int n, int h, int wd, void *stream);
-int unet_pool2_bwd(const void *dy, long dybs, void *dx, long dxbs, int c, int n, int h, int wd, int accumulate,
+ * adds into dx instead of overwriting); c channels of NHWC views. */
+int unet_pool2_fwd(const void *x, int ctx, void *y, int cty, int c, int n, int h, int wd, void *stream);
+int unet_pool2_bwd(const void *dy, int cty, void *dx, int ctx, int c, int n, int h, int wd, int accumulate,
                    void *stream);
 
-/* nearest 2x upsampling of an (h, wd) image and its adjoint. */
-int unet_up2_fwd(const void *x, long xbs, void *y, long ybs, int c, int n, int h, int wd, void *stream);
-int unet_up2_bwd(const void *dy, long dybs, void *dx, long dxbs, int c, int n, int h, int wd, void *stream);
+/* Nearest 2x upsampling of an (h, wd) image and its adjoint. */
+int unet_up2_fwd(const void *x, int ctx, void *y, int cty, int c, int n, int h, int wd, void *stream);
+int unet_up2_bwd(const void *dy, int cty, void *dx, int ctx, int c, int n, int h, int wd, void *stream);
 
-/* dy *= (y > 0) for the ReLU output y, chw elements per image. */
-int unet_relu_bwd(const void *y, long ybs, void *dy, long dybs, int chw, int n, void *stream);
+/* dy *= (y > 0) for the ReLU output y, c channels of npix pixels. */
+int unet_relu_bwd(const void *y, int cty, void *dy, int ctd, int c, long npix, void *stream);
 
-/* loss += sum_i wc[c(i)] (pred - target)^2 / count; grad = 2 wc (pred - target) / count.
- * pred, target, grad FP32 [n][c][hw]; loss: one double in device memory. */
+/* FP32 NCHW planes x [n][c][hw] -> BF16 NHWC y with ct channels per pixel
+ * (channels c..ct-1 are zero). */
+int unet_input_nhwc(const float *x, int c, int hw, int n, void *y, int ct, void *stream);
+
+/* Weighted mean squared error over count = n*c*hw FP32 values (NCHW):
+ * *loss += sum wc[ch] (pred - target)^2 / count (FP64 accumulator),
+ * grad = 2 wc (pred - target) / count. */
 int unet_mse(const float *pred, const float *target, const float *wc, int c, int hw, long count, float *grad,
              double *loss, void *stream);
 
-/* Adam step `step` (>= 1) on FP32 master weights, refreshing the BF16 copy
- * (w_bf16 may be NULL). */
+/* One Adam step on FP32 master weights (bias-corrected with `step`);
+ * w_bf16 (may be NULL) receives the BF16 compute copy. */
 int unet_adam(float *w_master, void *w_bf16, const float *grad, float *m, float *v, long count, float lr,
               float beta1, float beta2, float eps, int step, float weight_decay, void *stream);
 
-/* Round FP32 to BF16 (nearest even). */
+/* y = BF16(x), count elements. */
 int unet_f32_to_bf16(const float *x, void *y, long count, void *stream);
 
 #ifdef __cplusplus
 }
 #endif
 
-#endif /* UNET_BF16_H */
+#endif

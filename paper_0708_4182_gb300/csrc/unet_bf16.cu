@@ -2,15 +2,27 @@
 //
 // The surrogate maps a channel's wall mask, electric-force level and fill
 // fraction to its steady density and velocity, which then initialise the
-// lattice Boltzmann run (the warm start). Storage is BF16 (activations and
-// the compute copy of the weights); every sum accumulates in FP32; the
-// optimizer keeps FP32 master weights and moments.
+// lattice Boltzmann run (the warm start). Activations are BF16, channels-last
+// (NHWC); every sum accumulates in FP32; the optimizer keeps FP32 master
+// weights and moments.
 //
-// Tensors are NCHW. A tensor "view" is (pointer, channels, batch stride in
-// elements), so a layer can read or write a channel range of a larger buffer
-// (the decoder's concatenations are such buffers; nothing is copied).
-// Padding of the 3x3 convolutions: circular in x (the channels are periodic
-// along the flow), zero in y (walls).
+// The 3x3 convolutions run on the 5th-generation tensor cores: tcgen05.mma
+// (kind::f16, BF16 operands from shared memory, FP32 accumulator in tensor
+// memory) issued by one thread per CTA, operands staged by cp.async into the
+// canonical no-swizzle layout (8-row x 16-byte core matrices), completion
+// tracked by tcgen05.commit on mbarriers, the accumulator read back with
+// tcgen05.ld for the epilogue. Forward and input-gradient convolutions are an
+// implicit GEMM with M = 128 output pixels (4 rows x 32 columns), N = a tile
+// of output channels, K = 16 input channels of one of the 9 taps per MMA
+// (both operands K-major: channels are contiguous per pixel). The weight
+// gradient is a GEMM per tap with M = 128 output channels, N = a tile of
+// input channels and K = 16 pixels per MMA (both operands MN-major).
+//
+// A tensor "view" is (pointer to its first channel, channels per pixel of
+// the underlying buffer), so a layer reads or writes a channel range of a
+// larger buffer (the decoder's concatenations); nothing is copied. Padding of
+// the 3x3 convolutions: circular in x (the channels are periodic along the
+// flow), zero in y (walls).
 #include "unet_bf16.h"
 
 #include <cuda_bf16.h>
@@ -23,222 +35,443 @@ namespace {
 
 using bf16 = __nv_bfloat16;
 
-constexpr int kT = 256;       // threads per CTA
-constexpr int kTco = 32;      // output channels per CTA
-constexpr int kRows = 4;      // pixel tile: 4 rows x 32 columns
-constexpr int kCols = 32;
-constexpr int kCk = 16;       // input channels per staged chunk
+constexpr int kT = 256;                      // threads of the SIMT kernels
+constexpr int kTcThreads = 128;              // threads of the tensor-core kernels (4 warps = 128 TMEM lanes)
+constexpr int kStages = 4;                   // operand ring depth of the tensor-core kernels
+constexpr uint32_t kWaitLimit = 1u << 22;    // try_wait rounds before giving up
+constexpr int kTileRows = 4, kTileCols = 32; // output pixels of one conv CTA (M = 128)
+constexpr int kSmemPerSm = 233472;           // shared memory of one SM (bytes)
 
 __device__ __forceinline__ float ld(const bf16* p) { return __bfloat162float(*p); }
 __device__ __forceinline__ int wrapx(int x, int w) { return x < 0 ? x + w : (x >= w ? x - w : x); }
 
-// y[b, co, :, :] = act(bias[co] + sum_ci sum_taps wt(co, ci, tap) x[b, ci, shifted])
-// TW = 0: wt(o, i, ky, kx) = w[o][i][ky][kx]     (forward)
-// TW = 1: wt(o, i, ky, kx) = w[i][o][2-ky][2-kx] (gradient w.r.t. the input)
-// w holds [wo][wi][3][3]. One CTA: 32 output channels x (4 x 32) pixels of one
-// image; each thread 4 channels x 4 consecutive pixels (16 FP32 sums).
-template <int TW>
-__global__ void __launch_bounds__(kT) conv3x3_kernel(const bf16* __restrict__ x, int Ci, long xbs,
-                                                     const bf16* __restrict__ w, int wo, int wi,
-                                                     const float* __restrict__ bias, bf16* __restrict__ y,
-                                                     int Co, long ybs, int H, int W, int relu)
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
-    __shared__ float sx[kCk][kRows + 2][kCols + 2];
-    __shared__ float sw[kTco][kCk][9];
-    const int tid = threadIdx.x;
-    const int tiles_x = W / kCols;
-    const int ty0 = (blockIdx.x / tiles_x) * kRows, tx0 = (blockIdx.x % tiles_x) * kCols;
-    const int co0 = blockIdx.y * kTco;
-    const int b = blockIdx.z;
-    const int cg = tid / 32;            // channel group: channels co0 + 4cg .. +3
-    const int pg = tid % 32;            // pixel group: 4 pixels
-    const int pr = pg / 8, pc = (pg % 8) * 4;
-    float acc[4][4];
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// Bounded wait on one phase of an mbarrier; on timeout raise *err and return
+// (the caller goes on without the data, so nothing hangs).
+__device__ __forceinline__ void mbar_wait(uint64_t* bar, uint32_t parity, int* err)
+{
+    for (uint32_t i = 0; i < kWaitLimit; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return;
+    }
+    atomicOr(err, 1);
+}
+
+// 16-byte global -> shared copy; src_bytes = 0 fills zeros (src is not read)
+__device__ __forceinline__ void cp_async16_ca(void* dst, const void* src, uint32_t src_bytes)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16_cg(void* dst, const void* src, uint32_t src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// shared-memory matrix descriptor, no swizzle: core matrix (8 rows x 16 B)
+// (i, j) at start + i * sbo + j * lbo, j along K, i along M (or N)
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return uint64_t((addr >> 4) & 0x3FFF) | (uint64_t((lbo >> 4) & 0x3FFF) << 16) |
+           (uint64_t((sbo >> 4) & 0x3FFF) << 32) | (uint64_t(1) << 46);
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B,
+// M = 128, N = n; a_mn / b_mn select MN-major operands
+__host__ __device__ constexpr uint32_t idesc_bf16(int n, bool a_mn, bool b_mn)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | (a_mn ? 1u << 15 : 0u) | (b_mn ? 1u << 16 : 0u) |
+           (uint32_t(n >> 3) << 17) | (uint32_t(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 32 lanes x 16 consecutive FP32 columns: thread t of the warp gets lane t
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// TMEM columns to allocate for an accumulator of n FP32 columns (a power of two >= 32)
+__host__ __device__ constexpr uint32_t tmem_cols(int n) { return n <= 32 ? 32u : (n <= 64 ? 64u : (n <= 128 ? 128u : 256u)); }
+
+// Dynamic shared memory that lets at most 512 / cols CTAs share an SM, so
+// their tensor-memory allocations (cols columns each) always fit in the 512.
+__host__ constexpr int smem_for_tmem(int cols, int needed)
+{
+    const int ctas = 512 / cols;
+    const int cap = kSmemPerSm / (ctas + 1) + 1024;
+    return needed > cap ? needed : cap;
+}
+
+// output-channel tile of a convolution with n output channels
+__host__ __device__ constexpr int conv_ntile(int n) { return n % 128 == 0 ? 128 : (n % 64 == 0 ? 64 : 32); }
+
+// ------------------------------------------------------------------ tensor-core 3x3 convolution
+// y[b, p, co] = act(bias[co] + sum_{tap, k} B[co][k](tap) x[b, p + off(tap), k])
+// x: NHWC view (channels per pixel ct_in, K = 16 kc channels used), y: NHWC
+// view (ct_out per pixel), wt: packed weights (conv_pack_kernel), one CTA =
+// 128 pixels x NT channels of one image.
+template <int NT>
+__global__ void __launch_bounds__(kTcThreads) conv3x3_tc_kernel(const bf16* __restrict__ x, int ct_in, int kc,
+                                                                const bf16* __restrict__ wt,
+                                                                const float* __restrict__ bias,
+                                                                bf16* __restrict__ y, int ct_out, int H, int W,
+                                                                int relu, int* __restrict__ err)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    constexpr int kABytes = 128 * 16 * 2;  // 128 pixels x 16 channels
+    constexpr int kBBytes = NT * 16 * 2;   // NT channels x 16 channels
+    unsigned char* sa = smem;
+    unsigned char* sb = smem + kStages * kABytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sb + kStages * kBBytes);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + kStages);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tiles_x = W / kTileCols;
+    const int ty0 = (blockIdx.x / tiles_x) * kTileRows, tx0 = (blockIdx.x % tiles_x) * kTileCols;
+    const int nb = blockIdx.y, b = blockIdx.z;
+    const int KT = kc * 9;
+    const bf16* wblk = wt + size_t(nb) * kc * 9 * NT * 16;
+
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(tmem_slot, tmem_cols(NT));
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    auto load = [&](int it) {
+        const int s = it % kStages;
+        const int c = it / 9, t = it % 9;
+        const int dy = t / 3 - 1, dx = t % 3 - 1;
+        unsigned char* da = sa + s * kABytes;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-    const bf16* xb = x + b * xbs;
-    for (int c0 = 0; c0 < Ci; c0 += kCk) {
-        __syncthreads();
-        for (int i = tid; i < kCk * (kRows + 2) * (kCols + 2); i += kT) {
-            const int ci = i / ((kRows + 2) * (kCols + 2));
-            const int rem = i % ((kRows + 2) * (kCols + 2));
-            const int r = rem / (kCols + 2), c = rem % (kCols + 2);
-            const int gy = ty0 + r - 1, gx = wrapx(tx0 + c - 1, W);
-            float v = 0.f;
-            if (c0 + ci < Ci && gy >= 0 && gy < H) v = ld(xb + (long)(c0 + ci) * H * W + (long)gy * W + gx);
-            sx[ci][r][c] = v;
+        for (int j = 0; j < 2; ++j) {
+            const int q = tid + j * kTcThreads;  // 256 chunks of 16 B: pixel q/2, channel half q%2
+            const int p = q >> 1, h = q & 1;
+            const int yy = ty0 + (p >> 5) + dy, xx = wrapx(tx0 + (p & 31) + dx, W);
+            const bool ok = yy >= 0 && yy < H;
+            const bf16* src = ok ? x + (size_t(b * H + yy) * W + xx) * ct_in + c * 16 + h * 8 : x;
+            cp_async16_ca(da + (p >> 3) * 256 + h * 128 + (p & 7) * 16, src, ok ? 16u : 0u);
         }
-        for (int i = tid; i < kTco * kCk * 9; i += kT) {
-            const int o = i / (kCk * 9), rem = i % (kCk * 9);
-            const int ci = rem / 9, tap = rem % 9;
-            const int co = co0 + o, cc = c0 + ci;
-            float v = 0.f;
-            if (co < Co && cc < Ci) {
-                if (TW == 0)
-                    v = ld(w + ((long)co * wi + cc) * 9 + tap);
-                else
-                    v = ld(w + ((long)cc * wi + co) * 9 + (8 - tap));
-            }
-            sw[o][ci][tap] = v;
-        }
-        __syncthreads();
+        const bf16* wsrc = wblk + size_t(c * 9 + t) * NT * 16;
+        unsigned char* db = sb + s * kBBytes;
+        for (int q = tid; q < NT * 2; q += kTcThreads) cp_async16_cg(db + q * 16, wsrc + q * 8, 16u);
+    };
+
+    constexpr uint32_t idesc = idesc_bf16(NT, false, false);
 #pragma unroll 1
-        for (int ci = 0; ci < kCk; ++ci) {
-#pragma unroll
-            for (int ky = 0; ky < 3; ++ky) {
-                float xv[6];
-#pragma unroll
-                for (int j = 0; j < 6; ++j) xv[j] = sx[ci][pr + ky][pc + j];
-#pragma unroll
-                for (int kx = 0; kx < 3; ++kx) {
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const float wv = sw[cg * 4 + i][ci][ky * 3 + kx];
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(wv, xv[j + kx], acc[i][j]);
-                    }
-                }
-            }
-        }
+    for (int it = 0; it < kStages - 1; ++it) {
+        if (it < KT) load(it);
+        cp_async_commit();
     }
-    const int gy = ty0 + pr;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int co = co0 + cg * 4 + i;
-        if (co >= Co) continue;
-        const float bv = bias ? bias[co] : 0.f;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            float v = acc[i][j] + bv;
-            if (relu) v = fmaxf(v, 0.f);
-            y[b * ybs + (long)co * H * W + (long)gy * W + tx0 + pc + j] = __float2bfloat16_rn(v);
+#pragma unroll 1
+    for (int it = 0; it < KT; ++it) {
+        const int s = it % kStages;
+        cp_async_wait<kStages - 2>();
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint64_t da = smem_desc(smem_u32(sa + s * kABytes), 128, 256);
+            const uint64_t db = smem_desc(smem_u32(sb + s * kBBytes), 128, 256);
+            mma_bf16(tmem, da, db, idesc, it > 0 ? 1u : 0u);
+            mma_commit(&bars[s]);
         }
+        const int nxt = it + kStages - 1;
+        if (nxt < KT) {
+            // the buffer of nxt was last read by the MMA of iteration nxt - kStages
+            if (nxt >= kStages) mbar_wait(&bars[nxt % kStages], uint32_t((nxt / kStages) - 1) & 1u, err);
+            load(nxt);
+        }
+        cp_async_commit();
     }
+    cp_async_wait<0>();
+    mbar_wait(&bars[(KT - 1) % kStages], uint32_t((KT - 1) / kStages) & 1u, err);
+    tc_fence_after();
+
+    // epilogue: lane = pixel, 16 columns at a time
+    const int p = warp * 32 + lane;
+    const int yy = ty0 + (p >> 5), xx = tx0 + (p & 31);
+    bf16* out = y + (size_t(b * H + yy) * W + xx) * ct_out + nb * NT;
+#pragma unroll 1
+    for (int n0 = 0; n0 < NT; n0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + n0, v);
+        __align__(16) bf16 o[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            float a = v[j] + (bias ? bias[nb * NT + n0 + j] : 0.f);
+            if (relu) a = fmaxf(a, 0.f);
+            o[j] = __float2bfloat16_rn(a);
+        }
+        uint4* dst = reinterpret_cast<uint4*>(out + n0);
+        dst[0] = reinterpret_cast<const uint4*>(o)[0];
+        dst[1] = reinterpret_cast<const uint4*>(o)[1];
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, tmem_cols(NT));
 }
 
-// dw[co][ci][tap] += sum_{b, pixels} dy[b, co, p] x[b, ci, p + tap];
-// one CTA: 32 output channels x 16 input channels over `rows_per_cta` rows
-// of one image; each thread 1 output channel x 2 input channels x 9 taps.
-__global__ void __launch_bounds__(kT) conv3x3_wgrad_kernel(const bf16* __restrict__ x, int Ci, long xbs,
-                                                           const bf16* __restrict__ dy, int Co, long dybs,
-                                                           float* __restrict__ dw, int H, int W,
-                                                           int rows_per_cta)
+// Packed B operand of the tensor-core convolution. Forward (transpose = 0):
+// row n = output channel, column k = input channel, B[n][k](tap) =
+// w[n][k][tap]. Input gradient (transpose = 1): row n = input channel of the
+// forward layer, column k = its output channel, B[n][k](tap) = w[k][n][8 - tap]
+// (the transposed, flipped kernel). w: FP32 master weights [co][ci][9]. Out:
+// blocks [n tile][k chunk of 16][tap] of NT x 16 BF16 in core-matrix order
+// (row group i at 256 B, k half j at 128 B, row r at 16 B); k beyond the real
+// channels is 0.
+__global__ void conv_pack_kernel(const float* __restrict__ w, int co, int ci, int transpose, int nt, int kc,
+                                 bf16* __restrict__ out)
 {
-    __shared__ float sx[kCk][3][kCols + 2];
-    __shared__ float sd[kTco][kCols];
-    const int tid = threadIdx.x;
-    const int co0 = blockIdx.x * kTco, c0 = blockIdx.y * kCk;
-    const int row_blocks = H / rows_per_cta;
-    const int b = blockIdx.z / row_blocks, r0 = (blockIdx.z % row_blocks) * rows_per_cta;
-    const int o = tid / 8, ip = (tid % 8) * 2;
-    float acc[2][9];
-#pragma unroll
-    for (int k = 0; k < 2; ++k)
-#pragma unroll
-        for (int t = 0; t < 9; ++t) acc[k][t] = 0.f;
-    const bf16* xb = x + b * xbs;
-    const bf16* db = dy + b * dybs;
-    for (int r = r0; r < r0 + rows_per_cta; ++r) {
-        for (int cx = 0; cx < W; cx += kCols) {
-            __syncthreads();
-            for (int i = tid; i < kCk * 3 * (kCols + 2); i += kT) {
-                const int ci = i / (3 * (kCols + 2)), rem = i % (3 * (kCols + 2));
-                const int ry = rem / (kCols + 2), c = rem % (kCols + 2);
-                const int gy = r + ry - 1, gx = wrapx(cx + c - 1, W);
-                float v = 0.f;
-                if (c0 + ci < Ci && gy >= 0 && gy < H) v = ld(xb + (long)(c0 + ci) * H * W + (long)gy * W + gx);
-                sx[ci][ry][c] = v;
-            }
-            for (int i = tid; i < kTco * kCols; i += kT) {
-                const int oo = i / kCols, c = i % kCols;
-                sd[oo][c] = (co0 + oo < Co) ? ld(db + (long)(co0 + oo) * H * W + (long)r * W + cx + c) : 0.f;
-            }
-            __syncthreads();
-#pragma unroll 4
-            for (int c = 0; c < kCols; ++c) {
-                const float d = sd[o][c];
-#pragma unroll
-                for (int k = 0; k < 2; ++k)
-#pragma unroll
-                    for (int ky = 0; ky < 3; ++ky)
-#pragma unroll
-                        for (int kx = 0; kx < 3; ++kx) acc[k][ky * 3 + kx] = fmaf(d, sx[ip + k][ky][c + kx], acc[k][ky * 3 + kx]);
-            }
-        }
-    }
-    const int co = co0 + o;
-    if (co >= Co) return;
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int ci = c0 + ip + k;
-        if (ci >= Ci) continue;
-#pragma unroll
-        for (int t = 0; t < 9; ++t) atomicAdd(&dw[((long)co * Ci + ci) * 9 + t], acc[k][t]);
+    const int nrows = transpose ? ci : co;
+    const int kreal = transpose ? co : ci;
+    const long long total = (long long)nrows * kc * 16 * 9;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int k = int(i % (kc * 16));
+        const long long r1 = i / (kc * 16);
+        const int t = int(r1 % 9);
+        const int n = int(r1 / 9);
+        float v = 0.f;
+        if (k < kreal) v = transpose ? w[(size_t(k) * ci + n) * 9 + (8 - t)] : w[(size_t(n) * ci + k) * 9 + t];
+        const int nbk = n / nt, nn = n % nt, c = k / 16, kk = k % 16;
+        const size_t blk = (size_t(nbk) * kc + c) * 9 + t;
+        const size_t off = blk * nt * 16 + ((nn >> 3) * 2 + (kk >> 3)) * 64 + (nn & 7) * 8 + (kk & 7);
+        out[off] = __float2bfloat16_rn(v);
     }
 }
 
-// db[c] += sum over images and pixels of dy[b, c, :, :] (one CTA per channel)
-__global__ void bias_grad_kernel(const bf16* __restrict__ dy, int C, long dybs, int B, int HW,
+// ------------------------------------------------------------------ tensor-core weight gradient
+// dw[co][ci][tap] += sum_{b, p} dy[b, p, co] x[b, p + off(tap), ci] over this
+// CTA's pixel range: M = 128 output channels (rows beyond co stay zero),
+// N = NT input channels, K = 16 pixels of one image row per MMA; both
+// operands MN-major (channels contiguous per pixel).
+template <int NT>
+__global__ void __launch_bounds__(kTcThreads) wgrad_tc_kernel(const bf16* __restrict__ x, int ct_x, int ci,
+                                                              const bf16* __restrict__ dy, int ct_dy, int co,
+                                                              float* __restrict__ dw, int H, int W, int npix,
+                                                              int* __restrict__ err)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    constexpr int kABytes = 128 * 16 * 2;  // 128 output channels x 16 pixels
+    constexpr int kBBytes = NT * 16 * 2;   // NT input channels x 16 pixels
+    unsigned char* sa = smem;
+    unsigned char* sb = smem + kStages * kABytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sb + kStages * kBBytes);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + kStages);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int co0 = blockIdx.x * 128, ci0 = blockIdx.y * NT;
+    const int tap = blockIdx.z % 9, split = blockIdx.z / 9;
+    const int dyo = tap / 3 - 1, dxo = tap % 3 - 1;
+    const int co_here = co - co0 < 128 ? co - co0 : 128;
+    const int ci_here = ci - ci0 < NT ? ci - ci0 : NT;
+    const long long p_begin = (long long)split * npix;
+    const int KT = npix / 16;
+
+    // rows of A beyond co_here are never loaded: zero them once
+    for (int i = tid; i < kStages * kABytes / 16; i += kTcThreads) reinterpret_cast<uint4*>(sa)[i] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(tmem_slot, tmem_cols(NT));
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const int ga = co_here / 8, gb = (ci_here + 7) / 8;  // 16-byte channel groups of A and B
+    auto load = [&](int it) {
+        const int s = it % kStages;
+        const long long p0 = p_begin + (long long)it * 16;  // 16 pixels of one image row
+        const int bimg = int(p0 / ((long long)H * W));
+        const int rem = int(p0 % ((long long)H * W));
+        const int yy = rem / W, x0 = rem % W;
+        unsigned char* da = sa + s * kABytes;
+        unsigned char* db = sb + s * kBBytes;
+        for (int q = tid; q < 16 * ga; q += kTcThreads) {
+            const int k = q % 16, g = q / 16;
+            const bf16* src = dy + (size_t(bimg * H + yy) * W + x0 + k) * ct_dy + co0 + g * 8;
+            cp_async16_cg(da + g * 256 + (k >> 3) * 128 + (k & 7) * 16, src, 16u);
+        }
+        const int ys = yy + dyo;
+        const bool ok = ys >= 0 && ys < H;
+        for (int q = tid; q < 16 * gb; q += kTcThreads) {
+            const int k = q % 16, g = q / 16;
+            const int xs = wrapx(x0 + k + dxo, W);
+            const bf16* src = ok ? x + (size_t(bimg * H + ys) * W + xs) * ct_x + ci0 + g * 8 : x;
+            cp_async16_ca(db + g * 256 + (k >> 3) * 128 + (k & 7) * 16, src, ok ? 16u : 0u);
+        }
+    };
+
+    constexpr uint32_t idesc = idesc_bf16(NT, true, true);
+#pragma unroll 1
+    for (int it = 0; it < kStages - 1; ++it) {
+        if (it < KT) load(it);
+        cp_async_commit();
+    }
+#pragma unroll 1
+    for (int it = 0; it < KT; ++it) {
+        const int s = it % kStages;
+        cp_async_wait<kStages - 2>();
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint64_t da = smem_desc(smem_u32(sa + s * kABytes), 128, 256);
+            const uint64_t db = smem_desc(smem_u32(sb + s * kBBytes), 128, 256);
+            mma_bf16(tmem, da, db, idesc, it > 0 ? 1u : 0u);
+            mma_commit(&bars[s]);
+        }
+        const int nxt = it + kStages - 1;
+        if (nxt < KT) {
+            if (nxt >= kStages) mbar_wait(&bars[nxt % kStages], uint32_t((nxt / kStages) - 1) & 1u, err);
+            load(nxt);
+        }
+        cp_async_commit();
+    }
+    cp_async_wait<0>();
+    mbar_wait(&bars[(KT - 1) % kStages], uint32_t((KT - 1) / kStages) & 1u, err);
+    tc_fence_after();
+
+    const int m = warp * 32 + lane;  // output channel co0 + m
+#pragma unroll 1
+    for (int n0 = 0; n0 < NT; n0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + n0, v);
+        if (m < co_here) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (n0 + j < ci_here) atomicAdd(&dw[(size_t(co0 + m) * ci + ci0 + n0 + j) * 9 + tap], v[j]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, tmem_cols(NT));
+}
+
+// ------------------------------------------------------------------ SIMT kernels (NHWC)
+// db[c] += sum over pixels of dy[p, c]; block = channels, grid over pixel ranges
+__global__ void bias_grad_kernel(const bf16* __restrict__ dy, int ct, int C, long long npix, int per_block,
                                  float* __restrict__ db)
 {
-    __shared__ float red[kT];
-    const int c = blockIdx.x;
+    const int c = threadIdx.x;
+    if (c >= C) return;
+    const long long p0 = (long long)blockIdx.x * per_block;
+    const long long p1 = p0 + per_block < npix ? p0 + per_block : npix;
     float s = 0.f;
-    for (int b = 0; b < B; ++b)
-        for (int i = threadIdx.x; i < HW; i += kT) s += ld(dy + b * dybs + (long)c * HW + i);
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int h = kT / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) db[c] += red[0];
+    for (long long p = p0; p < p1; ++p) s += ld(dy + p * ct + c);
+    atomicAdd(&db[c], s);
 }
 
-// 1x1 head: y[b, o, p] = bias[o] + sum_i w[o][i] x[b, i, p], FP32 output
-__global__ void head_fwd_kernel(const bf16* __restrict__ x, int Ci, long xbs, const bf16* __restrict__ w,
+// 1x1 head: y[b, o, p] = bias[o] + sum_i w[o][i] x[b, p, i] (x NHWC view, y FP32 NCHW)
+__global__ void head_fwd_kernel(const bf16* __restrict__ x, int ct, int Ci, const bf16* __restrict__ w,
                                 const float* __restrict__ bias, float* __restrict__ y, int Co, int HW, int B)
 {
-    const long n = (long)B * HW;
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const long long n = (long long)B * HW;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const int b = int(i / HW), p = int(i % HW);
+        const bf16* xp = x + i * ct;
         for (int o = 0; o < Co; ++o) {
             float s = bias[o];
-            for (int c = 0; c < Ci; ++c) s = fmaf(ld(w + o * Ci + c), ld(x + b * xbs + (long)c * HW + p), s);
-            y[((long)b * Co + o) * HW + p] = s;
+            for (int c = 0; c < Ci; ++c) s = fmaf(ld(w + o * Ci + c), ld(xp + c), s);
+            y[((long long)b * Co + o) * HW + p] = s;
         }
     }
 }
 
-// head backward: dx[b, i, p] = sum_o w[o][i] dy[b, o, p] (BF16 out);
-// dw[o][i] += sum dy x, db[o] += sum dy (FP32, atomics per CTA)
-__global__ void head_bwd_kernel(const bf16* __restrict__ x, int Ci, long xbs, const bf16* __restrict__ w,
+// head backward: dx[b, p, i] = sum_o w[o][i] dy[b, o, p] (NHWC BF16 out);
+// dw[o][i] += sum dy x, db[o] += sum dy (FP32)
+__global__ void head_bwd_kernel(const bf16* __restrict__ x, int ct, int Ci, const bf16* __restrict__ w,
                                 const float* __restrict__ dy, int Co, int HW, int B, bf16* __restrict__ dx,
-                                long dxbs, float* __restrict__ dw, float* __restrict__ db)
+                                int ct_dx, float* __restrict__ dw, float* __restrict__ db)
 {
     __shared__ float sdw[8 * 64];
     __shared__ float sdb[8];
     for (int i = threadIdx.x; i < Co * Ci; i += blockDim.x) sdw[i] = 0.f;
     if (threadIdx.x < Co) sdb[threadIdx.x] = 0.f;
     __syncthreads();
-    const long n = (long)B * HW;
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const long long n = (long long)B * HW;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const int b = int(i / HW), p = int(i % HW);
         float g[8];
         for (int o = 0; o < Co; ++o) {
-            g[o] = dy[((long)b * Co + o) * HW + p];
+            g[o] = dy[((long long)b * Co + o) * HW + p];
             atomicAdd(&sdb[o], g[o]);
         }
+        const bf16* xp = x + i * ct;
+        bf16* dxp = dx + i * ct_dx;
         for (int c = 0; c < Ci; ++c) {
-            const float xv = ld(x + b * xbs + (long)c * HW + p);
+            const float xv = ld(xp + c);
             float s = 0.f;
             for (int o = 0; o < Co; ++o) {
                 s = fmaf(ld(w + o * Ci + c), g[o], s);
                 atomicAdd(&sdw[o * Ci + c], g[o] * xv);
             }
-            dx[b * dxbs + (long)c * HW + p] = __float2bfloat16_rn(s);
+            dxp[c] = __float2bfloat16_rn(s);
         }
     }
     __syncthreads();
@@ -246,85 +479,98 @@ __global__ void head_bwd_kernel(const bf16* __restrict__ x, int Ci, long xbs, co
     if (threadIdx.x < Co) atomicAdd(&db[threadIdx.x], sdb[threadIdx.x]);
 }
 
-// 2x2 average pooling and its adjoint
-__global__ void pool2_fwd_kernel(const bf16* __restrict__ x, long xbs, bf16* __restrict__ y, long ybs, int C,
-                                 int H, int W, int B)
+// 2x2 average pooling of an (H, W) NHWC view and its adjoint
+__global__ void pool2_fwd_kernel(const bf16* __restrict__ x, int ctx, bf16* __restrict__ y, int cty, int C, int H,
+                                 int W, int B)
 {
     const int h = H / 2, w = W / 2;
-    const long n = (long)B * C * h * w;
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-        const int b = int(i / ((long)C * h * w));
-        const long r = i % ((long)C * h * w);
-        const int c = int(r / (h * w)), yy = int(r % (h * w)) / w, xx = int(r % (h * w)) % w;
-        const bf16* s = x + b * xbs + (long)c * H * W + (long)(2 * yy) * W + 2 * xx;
-        const float v = 0.25f * ((ld(s) + ld(s + 1)) + (ld(s + W) + ld(s + W + 1)));
-        y[b * ybs + (long)c * h * w + (long)yy * w + xx] = __float2bfloat16_rn(v);
+    const long long n = (long long)B * h * w * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = int(i % C);
+        const long long pix = i / C;
+        const int xx = int(pix % w), yy = int((pix / w) % h), b = int(pix / ((long long)w * h));
+        const bf16* s = x + (size_t(b * H + 2 * yy) * W + 2 * xx) * ctx + c;
+        const float v = 0.25f * ((ld(s) + ld(s + ctx)) + (ld(s + size_t(W) * ctx) + ld(s + size_t(W + 1) * ctx)));
+        y[(size_t(b * h + yy) * w + xx) * cty + c] = __float2bfloat16_rn(v);
     }
 }
 
-__global__ void pool2_bwd_kernel(const bf16* __restrict__ dy, long dybs, bf16* __restrict__ dx, long dxbs,
-                                 int C, int H, int W, int B, int accumulate)
+__global__ void pool2_bwd_kernel(const bf16* __restrict__ dy, int cty, bf16* __restrict__ dx, int ctx, int C, int H,
+                                 int W, int B, int accumulate)
 {
-    const long n = (long)B * C * H * W;
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-        const int b = int(i / ((long)C * H * W));
-        const long r = i % ((long)C * H * W);
-        const int c = int(r / (H * W)), yy = int(r % (H * W)) / W, xx = int(r % (H * W)) % W;
-        float v = 0.25f * ld(dy + b * dybs + (long)c * (H / 2) * (W / 2) + (long)(yy / 2) * (W / 2) + xx / 2);
-        bf16* o = dx + b * dxbs + (long)c * H * W + (long)yy * W + xx;
+    const long long n = (long long)B * H * W * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = int(i % C);
+        const long long pix = i / C;
+        const int xx = int(pix % W), yy = int((pix / W) % H), b = int(pix / ((long long)W * H));
+        float v = 0.25f * ld(dy + (size_t(b * (H / 2) + yy / 2) * (W / 2) + xx / 2) * cty + c);
+        bf16* o = dx + (size_t(b * H + yy) * W + xx) * ctx + c;
         if (accumulate) v += ld(o);
         *o = __float2bfloat16_rn(v);
     }
 }
 
-// nearest 2x upsampling and its adjoint (sum over the 4 copies)
-__global__ void up2_fwd_kernel(const bf16* __restrict__ x, long xbs, bf16* __restrict__ y, long ybs, int C,
-                               int h, int w, int B)
+// nearest 2x upsampling of an (h, w) NHWC view and its adjoint (sum over the 4 copies)
+__global__ void up2_fwd_kernel(const bf16* __restrict__ x, int ctx, bf16* __restrict__ y, int cty, int C, int h,
+                               int w, int B)
 {
     const int H = 2 * h, W = 2 * w;
-    const long n = (long)B * C * H * W;
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-        const int b = int(i / ((long)C * H * W));
-        const long r = i % ((long)C * H * W);
-        const int c = int(r / (H * W)), yy = int(r % (H * W)) / W, xx = int(r % (H * W)) % W;
-        y[b * ybs + (long)c * H * W + (long)yy * W + xx] = x[b * xbs + (long)c * h * w + (long)(yy / 2) * w + xx / 2];
+    const long long n = (long long)B * H * W * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = int(i % C);
+        const long long pix = i / C;
+        const int xx = int(pix % W), yy = int((pix / W) % H), b = int(pix / ((long long)W * H));
+        y[(size_t(b * H + yy) * W + xx) * cty + c] = x[(size_t(b * h + yy / 2) * w + xx / 2) * ctx + c];
     }
 }
 
-__global__ void up2_bwd_kernel(const bf16* __restrict__ dy, long dybs, bf16* __restrict__ dx, long dxbs, int C,
-                               int h, int w, int B)
+__global__ void up2_bwd_kernel(const bf16* __restrict__ dy, int cty, bf16* __restrict__ dx, int ctx, int C, int h,
+                               int w, int B)
 {
     const int W = 2 * w;
-    const long n = (long)B * C * h * w;
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-        const int b = int(i / ((long)C * h * w));
-        const long r = i % ((long)C * h * w);
-        const int c = int(r / (h * w)), yy = int(r % (h * w)) / w, xx = int(r % (h * w)) % w;
-        const bf16* s = dy + b * dybs + (long)c * 4 * h * w + (long)(2 * yy) * W + 2 * xx;
-        dx[b * dxbs + (long)c * h * w + (long)yy * w + xx] =
-            __float2bfloat16_rn((ld(s) + ld(s + 1)) + (ld(s + W) + ld(s + W + 1)));
+    const long long n = (long long)B * h * w * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = int(i % C);
+        const long long pix = i / C;
+        const int xx = int(pix % w), yy = int((pix / w) % h), b = int(pix / ((long long)w * h));
+        const bf16* s = dy + (size_t(b * 2 * h + 2 * yy) * W + 2 * xx) * cty + c;
+        const float v = (ld(s) + ld(s + cty)) + (ld(s + size_t(W) * cty) + ld(s + size_t(W + 1) * cty));
+        dx[(size_t(b * h + yy) * w + xx) * ctx + c] = __float2bfloat16_rn(v);
     }
 }
 
-// dy <- dy * (y > 0): gradient through a ReLU whose output is y
-__global__ void relu_bwd_kernel(const bf16* __restrict__ y, long ybs, bf16* __restrict__ dy, long dybs, int CHW,
-                                int B)
+// dy <- dy * (y > 0): gradient through a ReLU whose output is y (NHWC views)
+__global__ void relu_bwd_kernel(const bf16* __restrict__ y, int cty, bf16* __restrict__ dy, int ctd, int C,
+                                long long npix)
 {
-    const long n = (long)B * CHW;
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-        const int b = int(i / CHW), r = int(i % CHW);
-        if (!(ld(y + b * ybs + r) > 0.f)) dy[b * dybs + r] = __float2bfloat16_rn(0.f);
+    const long long n = npix * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = int(i % C);
+        const long long p = i / C;
+        if (!(ld(y + p * cty + c) > 0.f)) dy[p * ctd + c] = __float2bfloat16_rn(0.f);
+    }
+}
+
+// FP32 NCHW planes -> BF16 NHWC with ct channels per pixel (channels >= c are 0)
+__global__ void input_nhwc_kernel(const float* __restrict__ x, int C, int HW, int B, bf16* __restrict__ y, int ct)
+{
+    const long long n = (long long)B * HW * ct;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = int(i % ct);
+        const long long pix = i / ct;
+        const int b = int(pix / HW), p = int(pix % HW);
+        y[i] = __float2bfloat16_rn(c < C ? x[((long long)b * C + c) * HW + p] : 0.f);
     }
 }
 
 // weighted mean squared error over n = B*C*HW values, weight per channel:
-// loss = sum_i wc (p - t)^2 / n; grad = 2 wc (p - t) / n (FP32)
+// loss = sum_i wc (p - t)^2 / n; grad = 2 wc (p - t) / n (FP32, NCHW)
 __global__ void mse_kernel(const float* __restrict__ p, const float* __restrict__ t, const float* __restrict__ wc,
-                           int C, int HW, long n, float* __restrict__ grad, double* __restrict__ loss)
+                           int C, int HW, long long n, float* __restrict__ grad, double* __restrict__ loss)
 {
     __shared__ double red[kT];
     double s = 0.0;
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const int c = int((i / HW) % C);
         const float d = p[i] - t[i];
         s += double(wc[c]) * d * d;
@@ -339,12 +585,12 @@ __global__ void mse_kernel(const float* __restrict__ p, const float* __restrict_
     if (threadIdx.x == 0) atomicAdd(loss, red[0] / double(n));
 }
 
-// Adam on FP32 master weights; writes the BF16 compute copy
+// Adam on FP32 master weights; writes the BF16 compute copy if wb != NULL
 __global__ void adam_kernel(float* __restrict__ wm, bf16* __restrict__ wb, const float* __restrict__ g,
-                            float* __restrict__ m, float* __restrict__ v, long n, float lr, float b1, float b2,
+                            float* __restrict__ m, float* __restrict__ v, long long n, float lr, float b1, float b2,
                             float eps, float c1, float c2, float wd)
 {
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const float gi = g[i] + wd * wm[i];
         const float mi = b1 * m[i] + (1.f - b1) * gi;
         const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
@@ -356,15 +602,58 @@ __global__ void adam_kernel(float* __restrict__ wm, bf16* __restrict__ wb, const
     }
 }
 
-__global__ void f32_to_bf16_kernel(const float* __restrict__ x, bf16* __restrict__ y, long n)
+__global__ void f32_to_bf16_kernel(const float* __restrict__ x, bf16* __restrict__ y, long long n)
 {
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         y[i] = __float2bfloat16_rn(x[i]);
 }
 
-int blocks_for(long n) { return int(n / kT + 1 < 4096 ? n / kT + 1 : 4096); }
+int blocks_for(long long n) { return int(n / kT + 1 < 4096 ? n / kT + 1 : 4096); }
 
 int status(cudaError_t e) { return e == cudaSuccess ? 0 : int(e); }
+
+__device__ int g_err = 0;  // set by a tensor-core kernel whose mbarrier wait timed out
+
+int* err_ptr()
+{
+    static int* p = nullptr;
+    if (!p) cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_err);
+    return p;
+}
+
+template <int NT>
+int launch_conv(const void* x, int ct_in, int kc, const void* wt, const float* bias, void* y, int ct_out, int cout,
+                int n, int h, int wd, int relu, cudaStream_t st)
+{
+    constexpr int needed = kStages * (128 * 32 + NT * 32) + kStages * 8 + 16;
+    const int smem = smem_for_tmem(int(tmem_cols(NT)), needed);
+    auto k = conv3x3_tc_kernel<NT>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return int(e);
+    dim3 grid((h / kTileRows) * (wd / kTileCols), cout / NT, n);
+    k<<<grid, kTcThreads, smem, st>>>((const bf16*)x, ct_in, kc, (const bf16*)wt, bias, (bf16*)y, ct_out, h, wd, relu,
+                                      err_ptr());
+    return status(cudaGetLastError());
+}
+
+template <int NT>
+int launch_wgrad(const void* x, int ct_x, int ci, const void* dy, int ct_dy, int co, float* dw, int n, int h, int wd,
+                 cudaStream_t st)
+{
+    constexpr int needed = kStages * (128 * 32 + NT * 32) + kStages * 8 + 16;
+    const int smem = smem_for_tmem(int(tmem_cols(NT)), needed);
+    auto k = wgrad_tc_kernel<NT>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return int(e);
+    // pixels per CTA: whole 16-pixel row pieces, about 2048, dividing the total
+    const long long total = (long long)n * h * wd;
+    int npix = 2048;
+    while (npix > 16 && total % npix) npix >>= 1;
+    dim3 grid((co + 127) / 128, (ci + NT - 1) / NT, int(9 * (total / npix)));
+    k<<<grid, kTcThreads, smem, st>>>((const bf16*)x, ct_x, ci, (const bf16*)dy, ct_dy, co, dw, h, wd, npix,
+                                      err_ptr());
+    return status(cudaGetLastError());
+}
 
 }  // namespace
 }  // namespace unet
@@ -373,90 +662,138 @@ using namespace unet;
 
 extern "C" {
 
-int unet_conv3x3_fwd(const void* x, int ci, long xbs, const void* w, const float* bias, void* y, int co, long ybs,
-                     int n, int h, int wd, int relu, void* stream)
+int unet_conv_ntile(int channels) { return conv_ntile(channels); }
+
+size_t unet_conv_pack_elems(int co, int ci, int transpose)
 {
-    if (wd % kCols || h % kRows || co % kTco) return -1;
-    dim3 grid((h / kRows) * (wd / kCols), co / kTco, n);
-    conv3x3_kernel<0><<<grid, kT, 0, (cudaStream_t)stream>>>((const bf16*)x, ci, xbs, (const bf16*)w, co, ci, bias,
-                                                             (bf16*)y, co, ybs, h, wd, relu);
+    const int nrows = transpose ? ci : co, kreal = transpose ? co : ci;
+    const int kc = (kreal + 15) / 16;
+    return size_t(nrows) * kc * 16 * 9;
+}
+
+int unet_conv_pack(const float* w, int co, int ci, int transpose, void* out, void* stream)
+{
+    const int nrows = transpose ? ci : co, kreal = transpose ? co : ci;
+    if (nrows % 32) return -1;
+    const int kc = (kreal + 15) / 16;
+    const long long total = (long long)nrows * kc * 16 * 9;
+    conv_pack_kernel<<<blocks_for(total), kT, 0, (cudaStream_t)stream>>>(w, co, ci, transpose, conv_ntile(nrows), kc,
+                                                                        (bf16*)out);
     return status(cudaGetLastError());
 }
 
-int unet_conv3x3_bwd_data(const void* dy, int co, long dybs, const void* w, void* dx, int ci, long dxbs, int n,
-                          int h, int wd, void* stream)
+int unet_conv3x3(const void* x, int ct_in, int cin, const void* wt, const float* bias, void* y, int ct_out, int cout,
+                 int n, int h, int wd, int relu, void* stream)
 {
-    if (wd % kCols || h % kRows) return -1;
-    dim3 grid((h / kRows) * (wd / kCols), (ci + kTco - 1) / kTco, n);
-    conv3x3_kernel<1><<<grid, kT, 0, (cudaStream_t)stream>>>((const bf16*)dy, co, dybs, (const bf16*)w, co, ci,
-                                                             nullptr, (bf16*)dx, ci, dxbs, h, wd, 0);
+    // K runs over kc chunks of 16 channels: cin a multiple of 16, or cin < 16
+    // in a view whose first 16 channels are readable (channels >= cin zero)
+    const int kc = (cin + 15) / 16;
+    if (wd % kTileCols || h % kTileRows || cout % 32 || ct_in % 8 || ct_out % 8 || cin < 1 ||
+        (cin % 16 && cin > 16) || kc * 16 > ct_in ||
+        (reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y) | reinterpret_cast<uintptr_t>(wt)) & 15)
+        return -1;
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (conv_ntile(cout)) {
+    case 128: return launch_conv<128>(x, ct_in, kc, wt, bias, y, ct_out, cout, n, h, wd, relu, st);
+    case 64: return launch_conv<64>(x, ct_in, kc, wt, bias, y, ct_out, cout, n, h, wd, relu, st);
+    default: return launch_conv<32>(x, ct_in, kc, wt, bias, y, ct_out, cout, n, h, wd, relu, st);
+    }
+}
+
+int unet_conv3x3_bwd_weight(const void* x, int ct_x, int ci, const void* dy, int ct_dy, int co, float* dw, float* db,
+                            int n, int h, int wd, void* stream)
+{
+    if (wd % 16 || co % 8 || ct_x % 8 || ct_dy % 8 ||
+        (reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(dy)) & 15)
+        return -1;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc;
+    if (ci <= 16)
+        rc = launch_wgrad<16>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
+    else if (ci % 64 == 0)
+        rc = launch_wgrad<64>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
+    else
+        rc = launch_wgrad<32>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
+    if (rc) return rc;
+    const long long npix = (long long)n * h * wd;
+    const int per = 1024;
+    bias_grad_kernel<<<int((npix + per - 1) / per), co <= kT ? co : kT, 0, st>>>((const bf16*)dy, ct_dy, co, npix, per,
+                                                                                db);
     return status(cudaGetLastError());
 }
 
-int unet_conv3x3_bwd_weight(const void* x, int ci, long xbs, const void* dy, int co, long dybs, float* dw,
-                            float* db, int n, int h, int wd, void* stream)
+int unet_tc_error(void* stream, int reset)
 {
-    if (wd % kCols || co % kTco) return -1;
-    int rows = h >= 8 ? 8 : h;
-    while (h % rows) --rows;
-    dim3 grid(co / kTco, (ci + kCk - 1) / kCk, n * (h / rows));
-    conv3x3_wgrad_kernel<<<grid, kT, 0, (cudaStream_t)stream>>>((const bf16*)x, ci, xbs, (const bf16*)dy, co, dybs,
-                                                                dw, h, wd, rows);
-    bias_grad_kernel<<<co, kT, 0, (cudaStream_t)stream>>>((const bf16*)dy, co, dybs, n, h * wd, db);
-    return status(cudaGetLastError());
+    int h = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(&h, err_ptr(), sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return -int(e);
+    if (reset && h) {
+        const int z = 0;
+        cudaMemcpyAsync(err_ptr(), &z, sizeof(int), cudaMemcpyHostToDevice, st);
+        cudaStreamSynchronize(st);
+    }
+    return h;
 }
 
-int unet_head_fwd(const void* x, int ci, long xbs, const void* w, const float* bias, float* y, int co, int n, int hw,
+int unet_head_fwd(const void* x, int ct, int ci, const void* w, const float* bias, float* y, int co, int n, int hw,
                   void* stream)
 {
     if (co > 8 || ci > 64) return -1;
-    head_fwd_kernel<<<blocks_for((long)n * hw), kT, 0, (cudaStream_t)stream>>>((const bf16*)x, ci, xbs,
-                                                                               (const bf16*)w, bias, y, co, hw, n);
+    head_fwd_kernel<<<blocks_for((long long)n * hw), kT, 0, (cudaStream_t)stream>>>((const bf16*)x, ct, ci,
+                                                                                   (const bf16*)w, bias, y, co, hw, n);
     return status(cudaGetLastError());
 }
 
-int unet_head_bwd(const void* x, int ci, long xbs, const void* w, const float* dy, int co, int n, int hw, void* dx,
-                  long dxbs, float* dw, float* db, void* stream)
+int unet_head_bwd(const void* x, int ct, int ci, const void* w, const float* dy, int co, int n, int hw, void* dx,
+                  int ct_dx, float* dw, float* db, void* stream)
 {
     if (co > 8 || co * ci > 512) return -1;
-    head_bwd_kernel<<<blocks_for((long)n * hw) / 4 + 1, kT, 0, (cudaStream_t)stream>>>(
-        (const bf16*)x, ci, xbs, (const bf16*)w, dy, co, hw, n, (bf16*)dx, dxbs, dw, db);
+    head_bwd_kernel<<<blocks_for((long long)n * hw) / 4 + 1, kT, 0, (cudaStream_t)stream>>>(
+        (const bf16*)x, ct, ci, (const bf16*)w, dy, co, hw, n, (bf16*)dx, ct_dx, dw, db);
     return status(cudaGetLastError());
 }
 
-int unet_pool2_fwd(const void* x, long xbs, void* y, long ybs, int c, int n, int h, int wd, void* stream)
+int unet_pool2_fwd(const void* x, int ctx, void* y, int cty, int c, int n, int h, int wd, void* stream)
 {
-    pool2_fwd_kernel<<<blocks_for((long)n * c * h * wd / 4), kT, 0, (cudaStream_t)stream>>>(
-        (const bf16*)x, xbs, (bf16*)y, ybs, c, h, wd, n);
+    pool2_fwd_kernel<<<blocks_for((long long)n * c * h * wd / 4), kT, 0, (cudaStream_t)stream>>>(
+        (const bf16*)x, ctx, (bf16*)y, cty, c, h, wd, n);
     return status(cudaGetLastError());
 }
 
-int unet_pool2_bwd(const void* dy, long dybs, void* dx, long dxbs, int c, int n, int h, int wd, int accumulate,
+int unet_pool2_bwd(const void* dy, int cty, void* dx, int ctx, int c, int n, int h, int wd, int accumulate,
                    void* stream)
 {
-    pool2_bwd_kernel<<<blocks_for((long)n * c * h * wd), kT, 0, (cudaStream_t)stream>>>(
-        (const bf16*)dy, dybs, (bf16*)dx, dxbs, c, h, wd, n, accumulate);
+    pool2_bwd_kernel<<<blocks_for((long long)n * c * h * wd), kT, 0, (cudaStream_t)stream>>>(
+        (const bf16*)dy, cty, (bf16*)dx, ctx, c, h, wd, n, accumulate);
     return status(cudaGetLastError());
 }
 
-int unet_up2_fwd(const void* x, long xbs, void* y, long ybs, int c, int n, int h, int wd, void* stream)
+int unet_up2_fwd(const void* x, int ctx, void* y, int cty, int c, int n, int h, int wd, void* stream)
 {
-    up2_fwd_kernel<<<blocks_for((long)n * c * h * wd * 4), kT, 0, (cudaStream_t)stream>>>(
-        (const bf16*)x, xbs, (bf16*)y, ybs, c, h, wd, n);
+    up2_fwd_kernel<<<blocks_for((long long)n * c * h * wd * 4), kT, 0, (cudaStream_t)stream>>>(
+        (const bf16*)x, ctx, (bf16*)y, cty, c, h, wd, n);
     return status(cudaGetLastError());
 }
 
-int unet_up2_bwd(const void* dy, long dybs, void* dx, long dxbs, int c, int n, int h, int wd, void* stream)
+int unet_up2_bwd(const void* dy, int cty, void* dx, int ctx, int c, int n, int h, int wd, void* stream)
 {
-    up2_bwd_kernel<<<blocks_for((long)n * c * h * wd), kT, 0, (cudaStream_t)stream>>>(
-        (const bf16*)dy, dybs, (bf16*)dx, dxbs, c, h, wd, n);
+    up2_bwd_kernel<<<blocks_for((long long)n * c * h * wd), kT, 0, (cudaStream_t)stream>>>(
+        (const bf16*)dy, cty, (bf16*)dx, ctx, c, h, wd, n);
     return status(cudaGetLastError());
 }
 
-int unet_relu_bwd(const void* y, long ybs, void* dy, long dybs, int chw, int n, void* stream)
+int unet_relu_bwd(const void* y, int cty, void* dy, int ctd, int c, long npix, void* stream)
 {
-    relu_bwd_kernel<<<blocks_for((long)n * chw), kT, 0, (cudaStream_t)stream>>>((const bf16*)y, ybs, (bf16*)dy,
-                                                                                dybs, chw, n);
+    relu_bwd_kernel<<<blocks_for((long long)npix * c), kT, 0, (cudaStream_t)stream>>>((const bf16*)y, cty, (bf16*)dy,
+                                                                                     ctd, c, npix);
+    return status(cudaGetLastError());
+}
+
+int unet_input_nhwc(const float* x, int c, int hw, int n, void* y, int ct, void* stream)
+{
+    input_nhwc_kernel<<<blocks_for((long long)n * hw * ct), kT, 0, (cudaStream_t)stream>>>(x, c, hw, n, (bf16*)y, ct);
     return status(cudaGetLastError());
 }
 

@@ -2,11 +2,14 @@
 
 Input planes: wall mask, electric-force level / 15, fill fraction. Output:
 steady density and velocity (normalised), used through lbm_set_field
-(LBM_RHO_U) as the initial state of a lattice Boltzmann run that then runs
-on to convergence. Training data are steady states the LBM itself produces.
+(LBM_RHO_U_PHYS) as the initial state of a lattice Boltzmann run that then
+runs on to convergence. Training data are steady states the LBM itself
+produces.
 
-All arithmetic runs in the hand-written kernels of libunet_bf16 (BF16
-storage, FP32 accumulation, FP32 master weights with Adam); this module only
+All arithmetic runs in the hand-written kernels of libunet_bf16: 3x3
+convolutions and their gradients on the tensor cores (tcgen05, BF16 operands,
+FP32 accumulation), the rest as CUDA-core kernels; activations are BF16
+channels-last, master weights and Adam moments FP32. This module only
 sequences layers and owns the buffers (torch CUDA tensors used as memory).
 Architecture and padding are those of the CPU reference network used by the
 tests: encoder levels with (32, 64, 128, 256) channels, two 3x3
@@ -25,6 +28,7 @@ from . import build as _build
 
 C = (32, 64, 128, 256)
 IN_CH, OUT_CH = 3, 3
+IN_PAD = 16  # input channels as stored (the convolutions read 16 channels per step)
 
 _lib = None
 
@@ -37,25 +41,29 @@ def load_unet():
         from .lbm import LbmUnavailable
         raise LbmUnavailable(f"{_build.UNET_LIB} is not built; run __graft_entry__.build()")
     lib = ctypes.CDLL(_build.UNET_LIB)
-    vp, L, I, F, D = ctypes.c_void_p, ctypes.c_long, ctypes.c_int, ctypes.c_float, ctypes.c_double
+    vp, L, I, F = ctypes.c_void_p, ctypes.c_long, ctypes.c_int, ctypes.c_float
     sig = {
-        "unet_conv3x3_fwd": [vp, I, L, vp, vp, vp, I, L, I, I, I, I, vp],
-        "unet_conv3x3_bwd_data": [vp, I, L, vp, vp, I, L, I, I, I, vp],
-        "unet_conv3x3_bwd_weight": [vp, I, L, vp, I, L, vp, vp, I, I, I, vp],
-        "unet_head_fwd": [vp, I, L, vp, vp, vp, I, I, I, vp],
-        "unet_head_bwd": [vp, I, L, vp, vp, I, I, I, vp, L, vp, vp, vp],
-        "unet_pool2_fwd": [vp, L, vp, L, I, I, I, I, vp],
-        "unet_pool2_bwd": [vp, L, vp, L, I, I, I, I, I, vp],
-        "unet_up2_fwd": [vp, L, vp, L, I, I, I, I, vp],
-        "unet_up2_bwd": [vp, L, vp, L, I, I, I, I, vp],
-        "unet_relu_bwd": [vp, L, vp, L, I, I, vp],
-        "unet_mse": [vp, vp, vp, I, I, L, vp, vp, vp],
-        "unet_adam": [vp, vp, vp, vp, vp, L, F, F, F, F, I, F, vp],
-        "unet_f32_to_bf16": [vp, vp, L, vp],
+        "unet_conv_ntile": ([I], I),
+        "unet_conv_pack_elems": ([I, I, I], ctypes.c_size_t),
+        "unet_conv_pack": ([vp, I, I, I, vp, vp], I),
+        "unet_conv3x3": ([vp, I, I, vp, vp, vp, I, I, I, I, I, I, vp], I),
+        "unet_conv3x3_bwd_weight": ([vp, I, I, vp, I, I, vp, vp, I, I, I, vp], I),
+        "unet_tc_error": ([vp, I], I),
+        "unet_head_fwd": ([vp, I, I, vp, vp, vp, I, I, I, vp], I),
+        "unet_head_bwd": ([vp, I, I, vp, vp, I, I, I, vp, I, vp, vp, vp], I),
+        "unet_pool2_fwd": ([vp, I, vp, I, I, I, I, I, vp], I),
+        "unet_pool2_bwd": ([vp, I, vp, I, I, I, I, I, I, vp], I),
+        "unet_up2_fwd": ([vp, I, vp, I, I, I, I, I, vp], I),
+        "unet_up2_bwd": ([vp, I, vp, I, I, I, I, I, vp], I),
+        "unet_relu_bwd": ([vp, I, vp, I, I, L, vp], I),
+        "unet_input_nhwc": ([vp, I, I, I, vp, I, vp], I),
+        "unet_mse": ([vp, vp, vp, I, I, L, vp, vp, vp], I),
+        "unet_adam": ([vp, vp, vp, vp, vp, L, F, F, F, F, I, F, vp], I),
+        "unet_f32_to_bf16": ([vp, vp, L, vp], I),
     }
-    for name, args in sig.items():
+    for name, (args, res) in sig.items():
         fn = getattr(lib, name)
-        fn.argtypes, fn.restype = args, ctypes.c_int
+        fn.argtypes, fn.restype = args, res
     _lib = lib
     return lib
 
@@ -81,20 +89,18 @@ def layer_shapes(in_ch: int = IN_CH) -> dict:
 
 
 class View:
-    """A channel range of an NCHW buffer: (tensor, channel offset, channels)."""
+    """A channel range of an NHWC buffer: (tensor, channel offset, channels)."""
 
     def __init__(self, t, c0, c):
         self.t, self.c0, self.c = t, c0, c
 
     @property
     def ptr(self):
-        n, ct, h, w = self.t.shape
-        return self.t.data_ptr() + self.c0 * h * w * self.t.element_size()
+        return ctypes.c_void_p(self.t.data_ptr() + self.c0 * self.t.element_size())
 
     @property
-    def bs(self):
-        n, ct, h, w = self.t.shape
-        return ct * h * w
+    def ct(self):
+        return self.t.shape[-1]
 
 
 class UNet:
@@ -105,10 +111,12 @@ class UNet:
         self.torch = torch
         self.lib = load_unet()
         self.B, self.H, self.W = batch, height, width
-        self.in_ch = in_ch
-        self.shapes = layer_shapes(in_ch)
         if height % 32 or width % 256:
             raise ValueError("height must be a multiple of 32 and width of 256")
+        if in_ch > IN_PAD:
+            raise ValueError(f"at most {IN_PAD} input planes")
+        self.in_ch = in_ch
+        self.shapes = layer_shapes(in_ch)
         self.dev = "cuda"
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.s = ctypes.c_void_p(self.stream.cuda_stream)
@@ -117,19 +125,35 @@ class UNet:
         for name, (co, ci, k) in self.shapes.items():
             std = (2.0 / (ci * k * k)) ** 0.5
             wm = (torch.randn((co, ci, k, k), generator=g, dtype=torch.float64) * std).float().to(self.dev)
-            self.params[name] = self._param(wm, torch.zeros(co, device=self.dev))
+            self.params[name] = self._param(name, wm, torch.zeros(co, device=self.dev))
         self.step_count = 0
         self.norm = dict(rho_mean=1.5, rho_std=1.0, u_scale=1e-3)
         self._alloc(batch)
 
-    def _param(self, wm, bm):
+    def _param(self, name, wm, bm):
         t = self.torch
-        bf = t.empty_like(wm, dtype=t.bfloat16)
-        p = dict(w=wm.contiguous(), b=bm.contiguous(), wb=bf, gw=t.zeros_like(wm), gb=t.zeros_like(bm),
-                 mw=t.zeros_like(wm), vw=t.zeros_like(wm), mb=t.zeros_like(bm), vb=t.zeros_like(bm))
-        _call(self.lib.unet_f32_to_bf16, ctypes.c_void_p(p["w"].data_ptr()), ctypes.c_void_p(bf.data_ptr()),
-              p["w"].numel(), self.s)
+        p = dict(w=wm.contiguous(), b=bm.contiguous(), wb=t.empty_like(wm, dtype=t.bfloat16), gw=t.zeros_like(wm),
+                 gb=t.zeros_like(bm), mw=t.zeros_like(wm), vw=t.zeros_like(wm), mb=t.zeros_like(bm),
+                 vb=t.zeros_like(bm))
+        co, ci, k = self.shapes[name]
+        if k == 3:
+            p["wt"] = t.empty(int(self.lib.unet_conv_pack_elems(co, ci, 0)), dtype=t.bfloat16, device=self.dev)
+            if ci % 32 == 0:  # the input gradient of the first layer is not needed
+                p["wtT"] = t.empty(int(self.lib.unet_conv_pack_elems(co, ci, 1)), dtype=t.bfloat16, device=self.dev)
+        self._refresh(name, p)
         return p
+
+    def _refresh(self, name, p):
+        """BF16 compute copy and packed tensor-core operands from the FP32 master weights."""
+        co, ci, k = self.shapes[name]
+        _call(self.lib.unet_f32_to_bf16, ctypes.c_void_p(p["w"].data_ptr()), ctypes.c_void_p(p["wb"].data_ptr()),
+              p["w"].numel(), self.s)
+        if k == 3:
+            _call(self.lib.unet_conv_pack, ctypes.c_void_p(p["w"].data_ptr()), co, ci, 0,
+                  ctypes.c_void_p(p["wt"].data_ptr()), self.s)
+            if "wtT" in p:
+                _call(self.lib.unet_conv_pack, ctypes.c_void_p(p["w"].data_ptr()), co, ci, 1,
+                      ctypes.c_void_p(p["wtT"].data_ptr()), self.s)
 
     def set_weights(self, weights: dict):
         """Load FP32 weights/biases {name: (w, b)} (e.g. to match a reference)."""
@@ -137,8 +161,7 @@ class UNet:
             p = self.params[name]
             p["w"].copy_(self.torch.as_tensor(w, dtype=self.torch.float32))
             p["b"].copy_(self.torch.as_tensor(b, dtype=self.torch.float32))
-            _call(self.lib.unet_f32_to_bf16, ctypes.c_void_p(p["w"].data_ptr()),
-                  ctypes.c_void_p(p["wb"].data_ptr()), p["w"].numel(), self.s)
+            self._refresh(name, p)
 
     def weights(self) -> dict:
         return {k: (p["w"].detach().cpu().numpy(), p["b"].detach().cpu().numpy()) for k, p in self.params.items()}
@@ -148,13 +171,13 @@ class UNet:
         H, W = self.H, self.W
         bf = dict(dtype=t.bfloat16, device=self.dev)
         hw = [(H >> l, W >> l) for l in range(4)]
-        self.x0 = t.zeros((B, self.in_ch, H, W), **bf)
-        self.A = [t.zeros((B, C[l], *hw[l]), **bf) for l in range(4)]
-        self.B3 = t.zeros((B, C[3], *hw[3]), **bf)
-        self.cat = [t.zeros((B, C[l + 1] + C[l], *hw[l]), **bf) for l in range(3)]
-        self.P = [t.zeros((B, C[l], *hw[l + 1]), **bf) for l in range(3)]
-        self.DA = [t.zeros((B, C[l], *hw[l]), **bf) for l in range(3)]
-        self.DB = [t.zeros((B, C[l], *hw[l]), **bf) for l in range(3)]
+        self.x0 = t.zeros((B, H, W, IN_PAD), **bf)
+        self.A = [t.zeros((B, *hw[l], C[l]), **bf) for l in range(4)]
+        self.B3 = t.zeros((B, *hw[3], C[3]), **bf)
+        self.cat = [t.zeros((B, *hw[l], C[l + 1] + C[l]), **bf) for l in range(3)]
+        self.P = [t.zeros((B, *hw[l + 1], C[l]), **bf) for l in range(3)]
+        self.DA = [t.zeros((B, *hw[l], C[l]), **bf) for l in range(3)]
+        self.DB = [t.zeros((B, *hw[l], C[l]), **bf) for l in range(3)]
         self.out = t.zeros((B, OUT_CH, H, W), dtype=t.float32, device=self.dev)
         # gradients of the activations
         self.gA = [t.zeros_like(a) for a in self.A]
@@ -171,9 +194,8 @@ class UNet:
     def _conv(self, name, x: View, y: View, h, w, relu=True):
         p = self.params[name]
         co, ci, _ = self.shapes[name]
-        _call(self.lib.unet_conv3x3_fwd, ctypes.c_void_p(x.ptr), ci, x.bs, ctypes.c_void_p(p["wb"].data_ptr()),
-              ctypes.c_void_p(p["b"].data_ptr()), ctypes.c_void_p(y.ptr), co, y.bs, self.batch, h, w,
-              1 if relu else 0, self.s)
+        _call(self.lib.unet_conv3x3, x.ptr, x.ct, ci, ctypes.c_void_p(p["wt"].data_ptr()),
+              ctypes.c_void_p(p["b"].data_ptr()), y.ptr, y.ct, co, self.batch, h, w, 1 if relu else 0, self.s)
 
     def _conv_bwd(self, name, x: View, y: View, gy: View, gx: View | None, h, w):
         """Through relu(conv(x)): gy *= (y > 0); accumulate weight/bias grads;
@@ -181,20 +203,20 @@ class UNet:
         p = self.params[name]
         co, ci, _ = self.shapes[name]
         lib, n = self.lib, self.batch
-        _call(lib.unet_relu_bwd, ctypes.c_void_p(y.ptr), y.bs, ctypes.c_void_p(gy.ptr), gy.bs, co * h * w, n, self.s)
-        _call(lib.unet_conv3x3_bwd_weight, ctypes.c_void_p(x.ptr), ci, x.bs, ctypes.c_void_p(gy.ptr), co, gy.bs,
+        _call(lib.unet_relu_bwd, y.ptr, y.ct, gy.ptr, gy.ct, co, n * h * w, self.s)
+        _call(lib.unet_conv3x3_bwd_weight, x.ptr, x.ct, ci, gy.ptr, gy.ct, co,
               ctypes.c_void_p(p["gw"].data_ptr()), ctypes.c_void_p(p["gb"].data_ptr()), n, h, w, self.s)
         if gx is not None:
-            _call(lib.unet_conv3x3_bwd_data, ctypes.c_void_p(gy.ptr), co, gy.bs, ctypes.c_void_p(p["wb"].data_ptr()),
-                  ctypes.c_void_p(gx.ptr), ci, gx.bs, n, h, w, self.s)
+            _call(lib.unet_conv3x3, gy.ptr, gy.ct, co, ctypes.c_void_p(p["wtT"].data_ptr()), None, gx.ptr, gx.ct,
+                  ci, n, h, w, 0, self.s)
 
     def forward(self, x_planes):
-        """x_planes: float tensor [B, 3, H, W] on the device -> self.out (FP32)."""
+        """x_planes: float tensor [B, in_ch, H, W] on the device -> self.out (FP32, [B, 3, H, W])."""
         lib, n, s = self.lib, self.batch, self.s
         H, W = self.H, self.W
         xs = x_planes.contiguous().float()
-        _call(lib.unet_f32_to_bf16, ctypes.c_void_p(xs.data_ptr()), ctypes.c_void_p(self.x0.data_ptr()),
-              xs.numel(), s)
+        _call(lib.unet_input_nhwc, ctypes.c_void_p(xs.data_ptr()), xs.shape[1], H * W, n,
+              ctypes.c_void_p(self.x0.data_ptr()), IN_PAD, s)
         h = View(self.x0, 0, self.in_ch)
         for l in range(4):
             hh, ww = H >> l, W >> l
@@ -203,8 +225,8 @@ class UNet:
             if l < 3:
                 skip = View(self.cat[l], C[l + 1], C[l])
                 self._conv(f"e{l}b", a, skip, hh, ww)
-                _call(lib.unet_pool2_fwd, ctypes.c_void_p(skip.ptr), skip.bs, ctypes.c_void_p(self.P[l].data_ptr()),
-                      C[l] * (hh // 2) * (ww // 2), C[l], n, hh, ww, s)
+                _call(lib.unet_pool2_fwd, skip.ptr, skip.ct, ctypes.c_void_p(self.P[l].data_ptr()), C[l], C[l], n,
+                      hh, ww, s)
                 h = View(self.P[l], 0, C[l])
             else:
                 self._conv("e3b", a, View(self.B3, 0, C[3]), hh, ww)
@@ -212,13 +234,12 @@ class UNet:
         for l in (2, 1, 0):
             hh, ww = H >> l, W >> l
             up = View(self.cat[l], 0, C[l + 1])
-            _call(lib.unet_up2_fwd, ctypes.c_void_p(lower.ptr), lower.bs, ctypes.c_void_p(up.ptr), up.bs,
-                  C[l + 1], n, hh // 2, ww // 2, s)
+            _call(lib.unet_up2_fwd, lower.ptr, lower.ct, up.ptr, up.ct, C[l + 1], n, hh // 2, ww // 2, s)
             self._conv(f"d{l}a", View(self.cat[l], 0, C[l + 1] + C[l]), View(self.DA[l], 0, C[l]), hh, ww)
             self._conv(f"d{l}b", View(self.DA[l], 0, C[l]), View(self.DB[l], 0, C[l]), hh, ww)
             lower = View(self.DB[l], 0, C[l])
         hp = self.params["head"]
-        _call(lib.unet_head_fwd, ctypes.c_void_p(lower.ptr), C[0], lower.bs, ctypes.c_void_p(hp["wb"].data_ptr()),
+        _call(lib.unet_head_fwd, lower.ptr, lower.ct, C[0], ctypes.c_void_p(hp["wb"].data_ptr()),
               ctypes.c_void_p(hp["b"].data_ptr()), ctypes.c_void_p(self.out.data_ptr()), OUT_CH, n, H * W, s)
         return self.out
 
@@ -238,18 +259,17 @@ class UNet:
               ctypes.c_void_p(wct.data_ptr()), OUT_CH, H * W, self.out.numel(),
               ctypes.c_void_p(self.gout.data_ptr()), ctypes.c_void_p(self.loss_acc.data_ptr()), s)
         hp = self.params["head"]
-        gdb0 = View(self.gDB[0], 0, C[0])
-        _call(lib.unet_head_bwd, ctypes.c_void_p(self.DB[0].data_ptr()), C[0], C[0] * H * W,
-              ctypes.c_void_p(hp["wb"].data_ptr()), ctypes.c_void_p(self.gout.data_ptr()), OUT_CH, n, H * W,
-              ctypes.c_void_p(gdb0.ptr), gdb0.bs, ctypes.c_void_p(hp["gw"].data_ptr()),
-              ctypes.c_void_p(hp["gb"].data_ptr()), s)
+        db0, gdb0 = View(self.DB[0], 0, C[0]), View(self.gDB[0], 0, C[0])
+        _call(lib.unet_head_bwd, db0.ptr, db0.ct, C[0], ctypes.c_void_p(hp["wb"].data_ptr()),
+              ctypes.c_void_p(self.gout.data_ptr()), OUT_CH, n, H * W, gdb0.ptr, gdb0.ct,
+              ctypes.c_void_p(hp["gw"].data_ptr()), ctypes.c_void_p(hp["gb"].data_ptr()), s)
         gup = None
         for l in (0, 1, 2):
             hh, ww = H >> l, W >> l
             if gup is not None:
                 # gradient of level l's decoder output arrives through the upsampling
-                _call(lib.unet_up2_bwd, ctypes.c_void_p(gup.ptr), gup.bs, ctypes.c_void_p(self.gDB[l].data_ptr()),
-                      C[l] * hh * ww, C[l], n, hh, ww, s)
+                g = View(self.gDB[l], 0, C[l])
+                _call(lib.unet_up2_bwd, gup.ptr, gup.ct, g.ptr, g.ct, C[l], n, hh, ww, s)
             self._conv_bwd(f"d{l}b", View(self.DA[l], 0, C[l]), View(self.DB[l], 0, C[l]),
                            View(self.gDB[l], 0, C[l]), View(self.gDA[l], 0, C[l]), hh, ww)
             self._conv_bwd(f"d{l}a", View(self.cat[l], 0, C[l + 1] + C[l]), View(self.DA[l], 0, C[l]),
@@ -257,17 +277,16 @@ class UNet:
             gup = View(self.gcat[l], 0, C[l + 1])  # towards the level below (coarser)
         # bottleneck: gradient of B3 through the level-2 upsampling
         hh, ww = H >> 3, W >> 3
-        _call(lib.unet_up2_bwd, ctypes.c_void_p(gup.ptr), gup.bs, ctypes.c_void_p(self.gB3.data_ptr()),
-              C[3] * hh * ww, C[3], n, hh, ww, s)
-        self._conv_bwd("e3b", View(self.A[3], 0, C[3]), View(self.B3, 0, C[3]), View(self.gB3, 0, C[3]),
-                       View(self.gA[3], 0, C[3]), hh, ww)
+        g3 = View(self.gB3, 0, C[3])
+        _call(lib.unet_up2_bwd, gup.ptr, gup.ct, g3.ptr, g3.ct, C[3], n, hh, ww, s)
+        self._conv_bwd("e3b", View(self.A[3], 0, C[3]), View(self.B3, 0, C[3]), g3, View(self.gA[3], 0, C[3]), hh, ww)
         self._conv_bwd("e3a", View(self.P[2], 0, C[2]), View(self.A[3], 0, C[3]), View(self.gA[3], 0, C[3]),
                        View(self.gP[2], 0, C[2]), hh, ww)
         for l in (2, 1, 0):
             hh, ww = H >> l, W >> l
             gskip = View(self.gcat[l], C[l + 1], C[l])
-            _call(lib.unet_pool2_bwd, ctypes.c_void_p(self.gP[l].data_ptr()), C[l] * (hh // 2) * (ww // 2),
-                  ctypes.c_void_p(gskip.ptr), gskip.bs, C[l], n, hh, ww, 1, s)
+            gp = View(self.gP[l], 0, C[l])
+            _call(lib.unet_pool2_bwd, gp.ptr, gp.ct, gskip.ptr, gskip.ct, C[l], n, hh, ww, 1, s)
             self._conv_bwd(f"e{l}b", View(self.A[l], 0, C[l]), View(self.cat[l], C[l + 1], C[l]), gskip,
                            View(self.gA[l], 0, C[l]), hh, ww)
             below = View(self.x0, 0, self.in_ch) if l == 0 else View(self.P[l - 1], 0, C[l - 1])
@@ -277,7 +296,7 @@ class UNet:
 
     def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0):
         self.step_count += 1
-        for p in self.params.values():
+        for name, p in self.params.items():
             _call(self.lib.unet_adam, ctypes.c_void_p(p["w"].data_ptr()), ctypes.c_void_p(p["wb"].data_ptr()),
                   ctypes.c_void_p(p["gw"].data_ptr()), ctypes.c_void_p(p["mw"].data_ptr()),
                   ctypes.c_void_p(p["vw"].data_ptr()), p["w"].numel(), lr, beta1, beta2, eps, self.step_count,
@@ -285,6 +304,13 @@ class UNet:
             _call(self.lib.unet_adam, ctypes.c_void_p(p["b"].data_ptr()), None, ctypes.c_void_p(p["gb"].data_ptr()),
                   ctypes.c_void_p(p["mb"].data_ptr()), ctypes.c_void_p(p["vb"].data_ptr()), p["b"].numel(), lr,
                   beta1, beta2, eps, self.step_count, 0.0, self.s)
+            if "wt" in p:
+                self._refresh(name, p)
+
+    def check_tensor_cores(self):
+        """Raise if a tensor-core kernel's bounded wait timed out (flag cleared)."""
+        if self.lib.unet_tc_error(self.s, 1) != 0:
+            raise RuntimeError("a tensor-core kernel timed out waiting for its MMAs")
 
     # -------------------------------------------------------- data mapping
     def planes(self, masks, levels, fills):

@@ -44,7 +44,7 @@ def test_every_unet_symbol_is_exported(lib):
     from paper_0708_4182_gb300 import build
     unet = ctypes.CDLL(build.UNET_LIB)
     names = declared_functions(UNET_HEADER, "unet_")
-    assert "unet_conv3x3_fwd" in names and "unet_adam" in names
+    assert "unet_conv3x3" in names and "unet_conv_pack" in names and "unet_adam" in names
     for name in names:
         assert hasattr(unet, name), name
 

@@ -1,11 +1,13 @@
 """U-Net kernels and network against the CPU reference (oracle/unet_oracle).
 
-BF16 storage with FP32 sums: the reference gets the same BF16-rounded
+Activations are BF16 channels-last; the 3x3 convolutions and their
+gradients run on the tensor cores. The reference gets the same BF16-rounded
 weights and inputs in FP64, so the remaining differences are accumulation
-order and the BF16 rounding of intermediate activations and gradients.
-Bounds: single kernels 1e-2 relative (L2) of the output; the whole network's
-output 3e-2 and every layer's weight gradient 8e-2 relative (L2) after the
-16 layers of BF16 round trips.
+order and the BF16 rounding of outputs and of intermediate activations and
+gradients. Bounds: single kernels 1e-2 relative (L2) of the output; the whole
+network's output 3e-2 and every layer's weight gradient 8e-2 relative (L2)
+after the 16 layers of BF16 round trips. Views are exercised as channel
+ranges of wider buffers.
 """
 import ctypes
 
@@ -22,7 +24,8 @@ def env():
         pytest.skip("no CUDA device")
     from paper_0708_4182_gb300 import surrogate
     lib = surrogate.load_unet()
-    return torch, surrogate, lib
+    yield torch, surrogate, lib
+    assert lib.unet_tc_error(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), 1) == 0
 
 
 def rel(a, b):
@@ -30,90 +33,111 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
-def bf(t, x):
-    return x.to(t.bfloat16)
-
-
-def ref_conv(t, x, w, b=None):
+def ref_conv(x, w, b=None):
     import torch.nn.functional as F
     xp = F.pad(F.pad(x, (1, 1, 0, 0), mode="circular"), (0, 0, 1, 1))
     return F.conv2d(xp, w, b)
 
 
-@pytest.mark.parametrize("ci,co,h,w", [(3, 32, 64, 256), (96, 32, 32, 64), (256, 128, 8, 32)])
+def vp(t, c0=0):
+    return ctypes.c_void_p(t.data_ptr() + c0 * t.element_size())
+
+
+def nhwc_buffer(t, x_nchw, extra, off):
+    """BF16 NHWC buffer with `extra` more channels than x, x stored at channel `off`."""
+    n, c, h, w = x_nchw.shape
+    buf = t.zeros((n, h, w, c + extra), dtype=t.bfloat16, device="cuda")
+    buf[..., off:off + c] = x_nchw.permute(0, 2, 3, 1).to(t.bfloat16).cuda()
+    return buf
+
+
+@pytest.mark.parametrize("ci,co,h,w", [(3, 32, 64, 256), (96, 32, 32, 64), (32, 64, 32, 32), (256, 128, 8, 32),
+                                       (384, 128, 8, 32), (64, 96, 8, 64)])
 def test_conv3x3_forward_backward(env, ci, co, h, w):
     t, surrogate, lib = env
     g = t.Generator().manual_seed(ci + co)
     n = 2
-    x = t.randn((n, ci, h, w), generator=g)
-    wt = t.randn((co, ci, 3, 3), generator=g) * (2.0 / (9 * ci)) ** 0.5
-    b = t.randn(co, generator=g) * 0.1
-    dy = t.randn((n, co, h, w), generator=g)
-    xb, wb, dyb = bf(t, x).cuda(), bf(t, wt).cuda(), bf(t, dy).cuda()
     s = ctypes.c_void_p(t.cuda.current_stream().cuda_stream)
-    y = t.empty((n, co, h, w), dtype=t.bfloat16, device="cuda")
+    x = t.randn((n, ci, h, w), generator=g).to(t.bfloat16).double()
+    wt = (t.randn((co, ci, 3, 3), generator=g) * (2.0 / (9 * ci)) ** 0.5).to(t.bfloat16)
+    b = t.randn(co, generator=g) * 0.1
+    dy = t.randn((n, co, h, w), generator=g).to(t.bfloat16).double()
+    # input view: channels [8, 8 + ci) of a wider buffer (ci = 3: 16 readable zero-padded channels)
+    pad_in = 16 - ci if ci < 16 else 0
+    xoff = 0 if ci < 16 else 8
+    xb = nhwc_buffer(t, x, pad_in + (0 if ci < 16 else 16), xoff)
+    wm = wt.float().cuda().contiguous()
+    packed = t.empty(int(lib.unet_conv_pack_elems(co, ci, 0)), dtype=t.bfloat16, device="cuda")
+    assert lib.unet_conv_pack(vp(wm), co, ci, 0, vp(packed), s) == 0
+    yb = t.zeros((n, h, w, co + 32), dtype=t.bfloat16, device="cuda")  # output at channel 16
     bias = b.float().cuda()
-    assert lib.unet_conv3x3_fwd(ctypes.c_void_p(xb.data_ptr()), ci, ci * h * w, ctypes.c_void_p(wb.data_ptr()),
-                                ctypes.c_void_p(bias.data_ptr()), ctypes.c_void_p(y.data_ptr()), co, co * h * w,
-                                n, h, w, 1, s) == 0
-    ref = t.relu(ref_conv(t, xb.double().cpu(), wb.double().cpu(), b.double()))
-    assert rel(y.float().cpu(), ref) < 1e-2
-    # gradient w.r.t. input (no activation) and w.r.t. weights/bias
-    dx = t.empty((n, ci, h, w), dtype=t.bfloat16, device="cuda")
-    assert lib.unet_conv3x3_bwd_data(ctypes.c_void_p(dyb.data_ptr()), co, co * h * w,
-                                     ctypes.c_void_p(wb.data_ptr()), ctypes.c_void_p(dx.data_ptr()), ci,
-                                     ci * h * w, n, h, w, s) == 0
-    dw = t.zeros((co, ci, 3, 3), device="cuda")
-    db = t.zeros(co, device="cuda")
-    assert lib.unet_conv3x3_bwd_weight(ctypes.c_void_p(xb.data_ptr()), ci, ci * h * w,
-                                       ctypes.c_void_p(dyb.data_ptr()), co, co * h * w,
-                                       ctypes.c_void_p(dw.data_ptr()), ctypes.c_void_p(db.data_ptr()), n, h, w,
-                                       s) == 0
-    xr = xb.double().cpu().requires_grad_(True)
-    wr = wb.double().cpu().requires_grad_(True)
+    assert lib.unet_conv3x3(vp(xb, xoff), xb.shape[-1], ci, vp(packed), vp(bias), vp(yb, 16), yb.shape[-1], co,
+                            n, h, w, 1, s) == 0
+    ref = t.relu(ref_conv(x, wt.double(), b.double()))
+    got = yb[..., 16:16 + co].permute(0, 3, 1, 2).float().cpu()
+    assert rel(got, ref) < 1e-2
+    assert t.all(yb[..., :16] == 0) and t.all(yb[..., 16 + co:] == 0)  # nothing outside the view
+    # gradient w.r.t. the input (no activation): transposed packing, needs ci % 32 == 0
+    xr = x.clone().requires_grad_(True)
+    wr = wt.double().requires_grad_(True)
     br = t.zeros(co, dtype=t.float64, requires_grad=True)
-    (ref_conv(t, xr, wr, br) * dyb.double().cpu()).sum().backward()
-    assert rel(dx.float().cpu(), xr.grad) < 1e-2
-    assert rel(dw.cpu(), wr.grad) < 1e-2
-    assert rel(db.cpu(), br.grad) < 1e-2
+    (ref_conv(xr, wr, br) * dy).sum().backward()
+    dyb = nhwc_buffer(t, dy, 8, 8)
+    if ci % 32 == 0:
+        packT = t.empty(int(lib.unet_conv_pack_elems(co, ci, 1)), dtype=t.bfloat16, device="cuda")
+        assert lib.unet_conv_pack(vp(wm), co, ci, 1, vp(packT), s) == 0
+        dxb = t.zeros((n, h, w, ci), dtype=t.bfloat16, device="cuda")
+        assert lib.unet_conv3x3(vp(dyb, 8), dyb.shape[-1], co, vp(packT), None, vp(dxb), ci, ci, n, h, w, 0, s) == 0
+        assert rel(dxb.permute(0, 3, 1, 2).float().cpu(), xr.grad) < 1e-2
+    # gradients w.r.t. weights and bias (accumulated: start from a known value)
+    dw = t.full((co, ci, 3, 3), 0.5, device="cuda")
+    db = t.full((co,), 0.25, device="cuda")
+    assert lib.unet_conv3x3_bwd_weight(vp(xb, xoff), xb.shape[-1], ci, vp(dyb, 8), dyb.shape[-1], co, vp(dw), vp(db),
+                                       n, h, w, s) == 0
+    assert rel(dw.cpu() - 0.5, wr.grad) < 1e-2
+    assert rel(db.cpu() - 0.25, br.grad) < 1e-2
 
 
-def test_pool_upsample_head(env):
+def test_pool_upsample_head_relu(env):
     t, surrogate, lib = env
     import torch.nn.functional as F
     g = t.Generator().manual_seed(7)
     n, c, h, w = 2, 32, 16, 64
-    x = bf(t, t.randn((n, c, h, w), generator=g)).cuda()
     s = ctypes.c_void_p(t.cuda.current_stream().cuda_stream)
-    p = t.empty((n, c, h // 2, w // 2), dtype=t.bfloat16, device="cuda")
-    lib.unet_pool2_fwd(ctypes.c_void_p(x.data_ptr()), c * h * w, ctypes.c_void_p(p.data_ptr()), c * h * w // 4,
-                       c, n, h, w, s)
-    assert rel(p.float().cpu(), F.avg_pool2d(x.double().cpu(), 2)) < 1e-2
-    u = t.empty((n, c, h, w), dtype=t.bfloat16, device="cuda")
-    lib.unet_up2_fwd(ctypes.c_void_p(p.data_ptr()), c * h * w // 4, ctypes.c_void_p(u.data_ptr()), c * h * w, c, n,
-                     h // 2, w // 2, s)
-    assert t.equal(u.cpu(), F.interpolate(p.cpu().float(), scale_factor=2, mode="nearest").to(t.bfloat16))
+    x = t.randn((n, c, h, w), generator=g).to(t.bfloat16).double()
+    xb = nhwc_buffer(t, x, 16, 8)
+    p = t.zeros((n, h // 2, w // 2, c), dtype=t.bfloat16, device="cuda")
+    assert lib.unet_pool2_fwd(vp(xb, 8), xb.shape[-1], vp(p), c, c, n, h, w, s) == 0
+    assert rel(p.permute(0, 3, 1, 2).float().cpu(), F.avg_pool2d(x, 2)) < 1e-2
+    u = t.zeros((n, h, w, c + 8), dtype=t.bfloat16, device="cuda")
+    assert lib.unet_up2_fwd(vp(p), c, vp(u, 8), u.shape[-1], c, n, h // 2, w // 2, s) == 0
+    want = F.interpolate(p.permute(0, 3, 1, 2).float().cpu(), scale_factor=2, mode="nearest")
+    assert t.equal(u[..., 8:].permute(0, 3, 1, 2).float().cpu(), want)
     # adjoints: <pool(x), y> = <x, pool^T(y)>, <up(a), b> = <a, up^T(b)>
-    yb = bf(t, t.randn((n, c, h // 2, w // 2), generator=g)).cuda()
-    dx = t.zeros((n, c, h, w), dtype=t.bfloat16, device="cuda")
-    lib.unet_pool2_bwd(ctypes.c_void_p(yb.data_ptr()), c * h * w // 4, ctypes.c_void_p(dx.data_ptr()), c * h * w,
-                       c, n, h, w, 0, s)
-    lhs = (F.avg_pool2d(x.double().cpu(), 2) * yb.double().cpu()).sum().item()
-    assert abs(lhs - (x.double().cpu() * dx.double().cpu()).sum().item()) < 2e-2 * abs(lhs) + 1e-3
-    bb = bf(t, t.randn((n, c, h, w), generator=g)).cuda()
-    da = t.empty((n, c, h // 2, w // 2), dtype=t.bfloat16, device="cuda")
-    lib.unet_up2_bwd(ctypes.c_void_p(bb.data_ptr()), c * h * w, ctypes.c_void_p(da.data_ptr()), c * h * w // 4,
-                     c, n, h // 2, w // 2, s)
-    lhs = (F.interpolate(yb.double().cpu(), scale_factor=2, mode="nearest") * bb.double().cpu()).sum().item()
-    assert abs(lhs - (yb.double().cpu() * da.double().cpu()).sum().item()) < 2e-2 * abs(lhs) + 1e-3
-    # 1x1 head
-    wh = bf(t, t.randn((3, c, 1, 1), generator=g)).cuda()
+    yb = t.randn((n, c, h // 2, w // 2), generator=g).to(t.bfloat16).double()
+    ybn = nhwc_buffer(t, yb, 0, 0)
+    dx = t.zeros((n, h, w, c), dtype=t.bfloat16, device="cuda")
+    assert lib.unet_pool2_bwd(vp(ybn), c, vp(dx), c, c, n, h, w, 0, s) == 0
+    lhs = (F.avg_pool2d(x, 2) * yb).sum().item()
+    assert abs(lhs - (x * dx.permute(0, 3, 1, 2).double().cpu()).sum().item()) < 2e-2 * abs(lhs) + 1e-3
+    bb = t.randn((n, c, h, w), generator=g).to(t.bfloat16).double()
+    bbn = nhwc_buffer(t, bb, 0, 0)
+    da = t.zeros((n, h // 2, w // 2, c), dtype=t.bfloat16, device="cuda")
+    assert lib.unet_up2_bwd(vp(bbn), c, vp(da), c, c, n, h // 2, w // 2, s) == 0
+    lhs = (F.interpolate(yb, scale_factor=2, mode="nearest") * bb).sum().item()
+    assert abs(lhs - (yb * da.permute(0, 3, 1, 2).double().cpu()).sum().item()) < 2e-2 * abs(lhs) + 1e-3
+    # 1x1 head (NHWC in, FP32 NCHW out)
+    wh = t.randn((3, c, 1, 1), generator=g).to(t.bfloat16)
     bh = t.randn(3, generator=g).float().cuda()
     yh = t.empty((n, 3, h, w), device="cuda")
-    lib.unet_head_fwd(ctypes.c_void_p(x.data_ptr()), c, c * h * w, ctypes.c_void_p(wh.data_ptr()),
-                      ctypes.c_void_p(bh.data_ptr()), ctypes.c_void_p(yh.data_ptr()), 3, n, h * w, s)
-    ref = F.conv2d(x.double().cpu(), wh.double().cpu(), bh.double().cpu())
-    assert rel(yh.cpu(), ref) < 1e-3
+    whc = wh.reshape(3, c).contiguous().cuda()
+    assert lib.unet_head_fwd(vp(xb, 8), xb.shape[-1], c, vp(whc), vp(bh), vp(yh), 3, n, h * w, s) == 0
+    assert rel(yh.cpu(), F.conv2d(x, wh.double(), bh.double().cpu())) < 1e-3
+    # ReLU backward on views
+    gyb = nhwc_buffer(t, bb, 8, 0)
+    assert lib.unet_relu_bwd(vp(xb, 8), xb.shape[-1], vp(gyb), gyb.shape[-1], c, n * h * w, s) == 0
+    want = t.where(x > 0, bb, t.zeros_like(bb))
+    assert t.equal(gyb[..., :c].permute(0, 3, 1, 2).double().cpu(), want)
 
 
 def test_network_matches_reference(env):
@@ -133,6 +157,7 @@ def test_network_matches_reference(env):
     wc = [1.0, 0.5, 0.25]
     out = net.forward(x.cuda())
     loss = net.loss_backward(target.cuda(), wc)
+    net.check_tensor_cores()
     ref_params = {k: (t.as_tensor(w, dtype=t.float64), t.as_tensor(b, dtype=t.float64)) for k, (w, b) in wts.items()}
     ref_out = U.forward(ref_params, x.double())
     assert rel(out.cpu(), ref_out) < 3e-2
@@ -162,4 +187,5 @@ def test_training_reduces_loss(env):
         net.forward(planes)
         losses.append(net.loss_backward(target, [1.0, 1.0, 1.0]))
         net.adam(lr=2e-3)
+    net.check_tensor_cores()
     assert losses[-1] < 0.2 * losses[0], (losses[0], losses[-1])
