@@ -53,7 +53,8 @@ int unet_conv3x3(const void *x, int ct_in, int cin, const void *wt, const float 
                  int cout, int n, int h, int wd, int relu, void *stream);
 
 /* Gradients w.r.t. the weights and bias of unet_conv3x3 (forward packing),
- * ACCUMULATED into FP32 dw [co][ci][3][3] and db [co]: dw += sum_{b, p}
+ * ACCUMULATED into FP32 dw [co][ci][3][3] and db [co] (db may be NULL, e.g.
+ * when unet_relu_bwd already accumulated it): dw += sum_{b, p}
  * dy[b, p, o] x[b, p + off(tap), i] (tensor cores), db += sum dy. Requires
  * wd % 16 == 0, co % 8 == 0, ct_x and ct_dy multiples of 8, 16-byte aligned
  * views; x must have at least 8 readable channels when ci < 8. */
@@ -64,7 +65,8 @@ int unet_conv3x3_bwd_weight(const void *x, int ct_x, int ci, const void *dy, int
  * wait timed out); reset != 0 clears it. Synchronises the stream. */
 int unet_tc_error(void *stream, int reset);
 
-/* 1x1 output head (co <= 8, ci <= 64): y[b, o, p] = bias[o] + sum_i w[o][i]
+/* 1x1 output head (forward: co <= 8, ci <= 64; backward: co = 3, ci <= 256):
+ * y[b, o, p] = bias[o] + sum_i w[o][i]
  * x[b, p, i], with BF16 weights w [co][ci], NHWC input view and FP32 output y
  * [n][co][hw] (NCHW); backward gives the NHWC BF16 dx and accumulates FP32
  * dw [co][ci], db [co]. */
@@ -79,12 +81,16 @@ int unet_pool2_fwd(const void *x, int ctx, void *y, int cty, int c, int n, int h
 int unet_pool2_bwd(const void *dy, int cty, void *dx, int ctx, int c, int n, int h, int wd, int accumulate,
                    void *stream);
 
-/* Nearest 2x upsampling of an (h, wd) image and its adjoint. */
+/* Nearest 2x upsampling of an (h, wd) image and its adjoint (forward: c,
+ * ctx, cty multiples of 8 and 16-byte aligned views). */
 int unet_up2_fwd(const void *x, int ctx, void *y, int cty, int c, int n, int h, int wd, void *stream);
 int unet_up2_bwd(const void *dy, int cty, void *dx, int ctx, int c, int n, int h, int wd, void *stream);
 
-/* dy *= (y > 0) for the ReLU output y, c channels of npix pixels. */
-int unet_relu_bwd(const void *y, int cty, void *dy, int ctd, int c, long npix, void *stream);
+/* dy *= (y > 0) for the ReLU output y, c <= 256 channels (c, cty, ctd
+ * multiples of 8, 16-byte aligned views) of npix pixels;
+ * with db != NULL also db[ch] += sum over pixels of the masked dy (FP32),
+ * the bias gradient of the layer that produced y. */
+int unet_relu_bwd(const void *y, int cty, void *dy, int ctd, int c, long npix, float *db, void *stream);
 
 /* FP32 NCHW planes x [n][c][hw] -> BF16 NHWC y with ct channels per pixel
  * (channels c..ct-1 are zero). */

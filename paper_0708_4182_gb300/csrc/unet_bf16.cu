@@ -444,39 +444,59 @@ __global__ void head_fwd_kernel(const bf16* __restrict__ x, int ct, int Ci, cons
 }
 
 // head backward: dx[b, p, i] = sum_o w[o][i] dy[b, o, p] (NHWC BF16 out);
-// dw[o][i] += sum dy x, db[o] += sum dy (FP32)
+// dw[o][i] += sum dy x, db[o] += sum dy (FP32). Block: Ci channels x
+// (256 / Ci) pixel lanes; each thread keeps its CO partial sums of dw and db
+// in registers, reduced per block in shared memory.
+template <int CO>
 __global__ void head_bwd_kernel(const bf16* __restrict__ x, int ct, int Ci, const bf16* __restrict__ w,
-                                const float* __restrict__ dy, int Co, int HW, int B, bf16* __restrict__ dx,
-                                int ct_dx, float* __restrict__ dw, float* __restrict__ db)
+                                const float* __restrict__ dy, int HW, int B, bf16* __restrict__ dx, int ct_dx,
+                                float* __restrict__ dw, float* __restrict__ db)
 {
-    __shared__ float sdw[8 * 64];
-    __shared__ float sdb[8];
-    for (int i = threadIdx.x; i < Co * Ci; i += blockDim.x) sdw[i] = 0.f;
-    if (threadIdx.x < Co) sdb[threadIdx.x] = 0.f;
-    __syncthreads();
+    __shared__ float red[kT][CO];
+    const int lanes = kT / Ci;
+    const int c = threadIdx.x % Ci, lane = threadIdx.x / Ci;
+    float wc[CO], sw[CO], sb[CO];
+#pragma unroll
+    for (int o = 0; o < CO; ++o) {
+        wc[o] = ld(w + o * Ci + c);
+        sw[o] = sb[o] = 0.f;
+    }
     const long long n = (long long)B * HW;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int b = int(i / HW), p = int(i % HW);
-        float g[8];
-        for (int o = 0; o < Co; ++o) {
-            g[o] = dy[((long long)b * Co + o) * HW + p];
-            atomicAdd(&sdb[o], g[o]);
-        }
-        const bf16* xp = x + i * ct;
-        bf16* dxp = dx + i * ct_dx;
-        for (int c = 0; c < Ci; ++c) {
-            const float xv = ld(xp + c);
+    if (lane < lanes) {
+        for (long long i = (long long)blockIdx.x * lanes + lane; i < n; i += (long long)gridDim.x * lanes) {
+            const int b = int(i / HW), p = int(i % HW);
+            const float xv = ld(x + i * ct + c);
             float s = 0.f;
-            for (int o = 0; o < Co; ++o) {
-                s = fmaf(ld(w + o * Ci + c), g[o], s);
-                atomicAdd(&sdw[o * Ci + c], g[o] * xv);
+#pragma unroll
+            for (int o = 0; o < CO; ++o) {
+                const float g = dy[((long long)b * CO + o) * HW + p];
+                s = fmaf(wc[o], g, s);
+                sw[o] = fmaf(g, xv, sw[o]);
+                sb[o] += g;
             }
-            dxp[c] = __float2bfloat16_rn(s);
+            dx[i * ct_dx + c] = __float2bfloat16_rn(s);
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < CO; ++o) red[threadIdx.x][o] = lane < lanes ? sw[o] : 0.f;
+    __syncthreads();
+    if (lane == 0) {
+        for (int o = 0; o < CO; ++o) {
+            float t = red[c][o];
+            for (int k = 1; k < lanes; ++k) t += red[k * Ci + c][o];
+            atomicAdd(&dw[o * Ci + c], t);
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < Co * Ci; i += blockDim.x) atomicAdd(&dw[i], sdw[i]);
-    if (threadIdx.x < Co) atomicAdd(&db[threadIdx.x], sdb[threadIdx.x]);
+    // db: every channel's thread saw the same dy values, so channel 0's lanes suffice
+#pragma unroll
+    for (int o = 0; o < CO; ++o) red[threadIdx.x][o] = (c == 0 && lane < lanes) ? sb[o] : 0.f;
+    __syncthreads();
+    if (threadIdx.x < CO) {
+        float t = 0.f;
+        for (int k = 0; k < lanes; ++k) t += red[k * Ci][threadIdx.x];
+        atomicAdd(&db[threadIdx.x], t);
+    }
 }
 
 // 2x2 average pooling of an (H, W) NHWC view and its adjoint
@@ -510,17 +530,20 @@ __global__ void pool2_bwd_kernel(const bf16* __restrict__ dy, int cty, bf16* __r
     }
 }
 
-// nearest 2x upsampling of an (h, w) NHWC view and its adjoint (sum over the 4 copies)
+// nearest 2x upsampling of an (h, w) NHWC view and its adjoint (sum over the
+// 4 copies); the forward copies 8 channels (16 bytes) per thread, so C, ctx,
+// cty must be multiples of 8 and the views 16-byte aligned
 __global__ void up2_fwd_kernel(const bf16* __restrict__ x, int ctx, bf16* __restrict__ y, int cty, int C, int h,
                                int w, int B)
 {
-    const int H = 2 * h, W = 2 * w;
-    const long long n = (long long)B * H * W * C;
+    const int H = 2 * h, W = 2 * w, C8 = C / 8;
+    const long long n = (long long)B * H * W * C8;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int c = int(i % C);
-        const long long pix = i / C;
+        const int c = int(i % C8) * 8;
+        const long long pix = i / C8;
         const int xx = int(pix % W), yy = int((pix / W) % H), b = int(pix / ((long long)W * H));
-        y[(size_t(b * H + yy) * W + xx) * cty + c] = x[(size_t(b * h + yy / 2) * w + xx / 2) * ctx + c];
+        *reinterpret_cast<uint4*>(y + (size_t(b * H + yy) * W + xx) * cty + c) =
+            *reinterpret_cast<const uint4*>(x + (size_t(b * h + yy / 2) * w + xx / 2) * ctx + c);
     }
 }
 
@@ -539,15 +562,46 @@ __global__ void up2_bwd_kernel(const bf16* __restrict__ dy, int cty, bf16* __res
     }
 }
 
-// dy <- dy * (y > 0): gradient through a ReLU whose output is y (NHWC views)
+// dy <- dy * (y > 0): gradient through a ReLU whose output is y (NHWC views,
+// C <= 256 channels, C, cty, ctd multiples of 8, 16-byte aligned); with db !=
+// NULL also db[c] += sum over pixels of the masked dy (the bias gradient of the
+// layer that produced y). A thread handles 8 channels of a pixel with 16-byte
+// loads and keeps 8 partial sums; the block sums them per channel in shared
+// memory, one atomic per channel.
 __global__ void relu_bwd_kernel(const bf16* __restrict__ y, int cty, bf16* __restrict__ dy, int ctd, int C,
-                                long long npix)
+                                long long npix, float* __restrict__ db)
 {
-    const long long n = npix * C;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int c = int(i % C);
-        const long long p = i / C;
-        if (!(ld(y + p * cty + c) > 0.f)) dy[p * ctd + c] = __float2bfloat16_rn(0.f);
+    __shared__ float red[kT][8];
+    const int G = C / 8, lanes = kT / G;
+    const int grp = threadIdx.x % G, lane = threadIdx.x / G;
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (lane < lanes) {
+        for (long long p = (long long)blockIdx.x * lanes + lane; p < npix; p += (long long)gridDim.x * lanes) {
+            const uint4 yv = *reinterpret_cast<const uint4*>(y + p * cty + grp * 8);
+            uint4* gp = reinterpret_cast<uint4*>(dy + p * ctd + grp * 8);
+            uint4 gv = *gp;
+            const bf16* ye = reinterpret_cast<const bf16*>(&yv);
+            bf16* ge = reinterpret_cast<bf16*>(&gv);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (__bfloat162float(ye[j]) > 0.f)
+                    s[j] += __bfloat162float(ge[j]);
+                else
+                    ge[j] = __float2bfloat16_rn(0.f);
+            }
+            *gp = gv;
+        }
+    }
+    if (!db) return;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) red[threadIdx.x][j] = lane < lanes ? s[j] : 0.f;
+    __syncthreads();
+    if (lane == 0) {
+        for (int k = 1; k < lanes; ++k)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) s[j] += red[k * G + grp][j];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) atomicAdd(&db[grp * 8 + j], s[j]);
     }
 }
 
@@ -645,10 +699,16 @@ int launch_wgrad(const void* x, int ct_x, int ci, const void* dy, int ct_dy, int
     auto k = wgrad_tc_kernel<NT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return int(e);
-    // pixels per CTA: whole 16-pixel row pieces, about 2048, dividing the total
+    // pixels per CTA: a power of two (whole 16-pixel row pieces) dividing the
+    // total, at most 2048, and small enough that the grid fills every SM about
+    // four times over (at least 64 pixels, four MMAs, per CTA)
     const long long total = (long long)n * h * wd;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+    const long long tiles = 9LL * ((co + 127) / 128) * ((ci + NT - 1) / NT);
     int npix = 2048;
     while (npix > 16 && total % npix) npix >>= 1;
+    while (npix > 64 && tiles * (total / npix) < 4LL * (sms > 0 ? sms : 148) && total % (npix / 2) == 0) npix >>= 1;
     dim3 grid((co + 127) / 128, (ci + NT - 1) / NT, int(9 * (total / npix)));
     k<<<grid, kTcThreads, smem, st>>>((const bf16*)x, ct_x, ci, (const bf16*)dy, ct_dy, co, dw, h, wd, npix,
                                       err_ptr());
@@ -714,7 +774,7 @@ int unet_conv3x3_bwd_weight(const void* x, int ct_x, int ci, const void* dy, int
         rc = launch_wgrad<64>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
     else
         rc = launch_wgrad<32>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
-    if (rc) return rc;
+    if (rc || !db) return rc;
     const long long npix = (long long)n * h * wd;
     const int per = 1024;
     bias_grad_kernel<<<int((npix + per - 1) / per), co <= kT ? co : kT, 0, st>>>((const bf16*)dy, ct_dy, co, npix, per,
@@ -749,9 +809,9 @@ int unet_head_fwd(const void* x, int ct, int ci, const void* w, const float* bia
 int unet_head_bwd(const void* x, int ct, int ci, const void* w, const float* dy, int co, int n, int hw, void* dx,
                   int ct_dx, float* dw, float* db, void* stream)
 {
-    if (co > 8 || co * ci > 512) return -1;
-    head_bwd_kernel<<<blocks_for((long long)n * hw) / 4 + 1, kT, 0, (cudaStream_t)stream>>>(
-        (const bf16*)x, ct, ci, (const bf16*)w, dy, co, hw, n, (bf16*)dx, ct_dx, dw, db);
+    if (co != 3 || ci < 1 || ci > kT) return -1;
+    head_bwd_kernel<3><<<blocks_for((long long)n * hw * ci) / 4 + 1, kT, 0, (cudaStream_t)stream>>>(
+        (const bf16*)x, ct, ci, (const bf16*)w, dy, hw, n, (bf16*)dx, ct_dx, dw, db);
     return status(cudaGetLastError());
 }
 
@@ -772,7 +832,9 @@ int unet_pool2_bwd(const void* dy, int cty, void* dx, int ctx, int c, int n, int
 
 int unet_up2_fwd(const void* x, int ctx, void* y, int cty, int c, int n, int h, int wd, void* stream)
 {
-    up2_fwd_kernel<<<blocks_for((long long)n * c * h * wd * 4), kT, 0, (cudaStream_t)stream>>>(
+    if (c % 8 || ctx % 8 || cty % 8 || (reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15)
+        return -1;
+    up2_fwd_kernel<<<blocks_for((long long)n * c / 8 * h * wd * 4), kT, 0, (cudaStream_t)stream>>>(
         (const bf16*)x, ctx, (bf16*)y, cty, c, h, wd, n);
     return status(cudaGetLastError());
 }
@@ -784,10 +846,14 @@ int unet_up2_bwd(const void* dy, int cty, void* dx, int ctx, int c, int n, int h
     return status(cudaGetLastError());
 }
 
-int unet_relu_bwd(const void* y, int cty, void* dy, int ctd, int c, long npix, void* stream)
+int unet_relu_bwd(const void* y, int cty, void* dy, int ctd, int c, long npix, float* db, void* stream)
 {
-    relu_bwd_kernel<<<blocks_for((long long)npix * c), kT, 0, (cudaStream_t)stream>>>((const bf16*)y, cty, (bf16*)dy,
-                                                                                     ctd, c, npix);
+    if (c < 8 || c > kT || c % 8 || cty % 8 || ctd % 8 ||
+        (reinterpret_cast<uintptr_t>(y) | reinterpret_cast<uintptr_t>(dy)) & 15)
+        return -1;
+    long long blocks = (long long)npix * (c / 8) / (kT * 4) + 1;  // about 4 pixels per thread
+    if (blocks > 1024) blocks = 1024;
+    relu_bwd_kernel<<<int(blocks), kT, 0, (cudaStream_t)stream>>>((const bf16*)y, cty, (bf16*)dy, ctd, c, npix, db);
     return status(cudaGetLastError());
 }
 

@@ -55,7 +55,7 @@ def load_unet():
         "unet_pool2_bwd": ([vp, I, vp, I, I, I, I, I, I, vp], I),
         "unet_up2_fwd": ([vp, I, vp, I, I, I, I, I, vp], I),
         "unet_up2_bwd": ([vp, I, vp, I, I, I, I, I, vp], I),
-        "unet_relu_bwd": ([vp, I, vp, I, I, L, vp], I),
+        "unet_relu_bwd": ([vp, I, vp, I, I, L, vp, vp], I),
         "unet_input_nhwc": ([vp, I, I, I, vp, I, vp], I),
         "unet_mse": ([vp, vp, vp, I, I, L, vp, vp, vp], I),
         "unet_adam": ([vp, vp, vp, vp, vp, L, F, F, F, F, I, F, vp], I),
@@ -203,9 +203,10 @@ class UNet:
         p = self.params[name]
         co, ci, _ = self.shapes[name]
         lib, n = self.lib, self.batch
-        _call(lib.unet_relu_bwd, y.ptr, y.ct, gy.ptr, gy.ct, co, n * h * w, self.s)
+        _call(lib.unet_relu_bwd, y.ptr, y.ct, gy.ptr, gy.ct, co, n * h * w, ctypes.c_void_p(p["gb"].data_ptr()),
+              self.s)
         _call(lib.unet_conv3x3_bwd_weight, x.ptr, x.ct, ci, gy.ptr, gy.ct, co,
-              ctypes.c_void_p(p["gw"].data_ptr()), ctypes.c_void_p(p["gb"].data_ptr()), n, h, w, self.s)
+              ctypes.c_void_p(p["gw"].data_ptr()), None, n, h, w, self.s)
         if gx is not None:
             _call(lib.unet_conv3x3, gy.ptr, gy.ct, co, ctypes.c_void_p(p["wtT"].data_ptr()), None, gx.ptr, gx.ct,
                   ci, n, h, w, 0, self.s)

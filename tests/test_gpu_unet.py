@@ -135,9 +135,25 @@ def test_pool_upsample_head_relu(env):
     assert rel(yh.cpu(), F.conv2d(x, wh.double(), bh.double().cpu())) < 1e-3
     # ReLU backward on views
     gyb = nhwc_buffer(t, bb, 8, 0)
-    assert lib.unet_relu_bwd(vp(xb, 8), xb.shape[-1], vp(gyb), gyb.shape[-1], c, n * h * w, s) == 0
+    dbr = t.full((c,), 0.5, device="cuda")
+    assert lib.unet_relu_bwd(vp(xb, 8), xb.shape[-1], vp(gyb), gyb.shape[-1], c, n * h * w, vp(dbr), s) == 0
     want = t.where(x > 0, bb, t.zeros_like(bb))
     assert t.equal(gyb[..., :c].permute(0, 3, 1, 2).double().cpu(), want)
+    assert rel(dbr.cpu() - 0.5, want.sum(dim=(0, 2, 3))) < 1e-5
+    # head backward (NHWC dx, accumulated FP32 dw and db)
+    gh = t.randn((n, 3, h, w), generator=g)
+    dxh = t.zeros((n, h, w, c), dtype=t.bfloat16, device="cuda")
+    dwh = t.full((3, c), 0.5, device="cuda")
+    dbh = t.full((3,), 0.25, device="cuda")
+    assert lib.unet_head_bwd(vp(xb, 8), xb.shape[-1], c, vp(whc), vp(gh.cuda()), 3, n, h * w, vp(dxh), c, vp(dwh),
+                             vp(dbh), s) == 0
+    xr = x.clone().requires_grad_(True)
+    wr = wh.double().requires_grad_(True)
+    brh = t.zeros(3, dtype=t.float64, requires_grad=True)
+    (F.conv2d(xr, wr, brh) * gh.double()).sum().backward()
+    assert rel(dxh.permute(0, 3, 1, 2).float().cpu(), xr.grad) < 1e-2
+    assert rel(dwh.cpu() - 0.5, wr.grad.reshape(3, c)) < 1e-4
+    assert rel(dbh.cpu() - 0.25, brh.grad) < 1e-4
 
 
 def test_network_matches_reference(env):
