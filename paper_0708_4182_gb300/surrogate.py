@@ -525,3 +525,43 @@ def batch_run_to_steady(ws, net=None, stream=None, rel_tol=1e-7, check_every=100
     finally:
         b.close()
     return steps, obs, info
+
+
+def _time_training_step(argv=None):
+    """Time forward + backward + Adam of one network on random planes (CUDA
+    events around `steps` steps after `warmup` steps); prints ms per step."""
+    import argparse
+    import torch
+    ap = argparse.ArgumentParser(description=_time_training_step.__doc__)
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--height", type=int, default=64)
+    ap.add_argument("--width", type=int, default=256)
+    ap.add_argument("--warmup", type=int, default=4)
+    ap.add_argument("--steps", type=int, default=10)
+    a = ap.parse_args(argv)
+    net = UNet(batch=a.batch, height=a.height, width=a.width, seed=0)
+    g = torch.Generator().manual_seed(0)
+    planes = torch.rand((a.batch, IN_CH, a.height, a.width), generator=g).cuda()
+    target = torch.randn((a.batch, OUT_CH, a.height, a.width), generator=g).cuda()
+
+    def step():
+        net.forward(planes)
+        net.loss_backward(target, [1.0, 1.0, 1.0], sync=False)
+        net.adam(1e-3)
+
+    for _ in range(a.warmup):
+        step()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(a.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    net.check_tensor_cores()
+    print(f"U-Net training step, batch {a.batch} of {a.height}x{a.width}: "
+          f"{e0.elapsed_time(e1) / max(1, a.steps):.3f} ms")
+
+
+if __name__ == "__main__":
+    _time_training_step()
