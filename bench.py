@@ -292,6 +292,9 @@ def run_ours(args, rank, world, local_rank):
         del lat
         torch.cuda.empty_cache()
         extra = run_batch_measurements(lbm, stream, rank, world)
+        if world == 1:
+            extra["storage_forms"] = storage_forms(lbm, stream, w, params)
+            extra["small_configs"] = small_configs(lbm, stream)
 
     line = {"metric": "MLUPS", "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 5),
@@ -346,6 +349,74 @@ def run_e2e(args, w, params, lbm, stream, world):
             "h2d_bytes_per_step": int((rho_u.nbytes + mask.nbytes) / steps),
             "d2h_bytes_per_step": 64,
             "what": "host mask + FP64 (rho,u) upload, then per step lbm_step + fused observables read-back"}
+
+
+# ----------------------------------------------------------------- other configurations
+
+def storage_forms(lbm, stream, w, params, steps=50):
+    """MLUPS of the step kernel per population storage form on the benchmark
+    workload (CUDA events on the kernel's stream, after 5 warm-up steps)."""
+    import torch
+    out = {}
+    for name, (code, nbytes) in STORAGE.items():
+        lat = lbm.Lattice(w.nx, w.ny, stream=stream, **dict(params, storage=code, obs_every=0))
+        lat.set_geometry(w.mask)
+        lat.set_rho_u(w.rho)
+        lat.step(5)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        lat.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        n_fluid = int((w.mask == 0).sum())
+        out[name] = {"mlups": round(w.nx * w.ny / ms / 1e3, 1), "bytes_per_node": nbytes,
+                     "gb_s": round(nbytes * n_fluid / ms / 1e6, 1)}
+        lat.close()
+        torch.cuda.empty_cache()
+    return out
+
+
+def small_configs(lbm, stream):
+    """The 128x64 sessile droplet and the 1024x128 rough channel as single
+    domains (launch-bound, L2-resident: one kernel launch per step), and the
+    rough channel's steady flux Q(f)/Q(0) at four force levels, run to steady
+    as one batch (FP32 deviation storage)."""
+    import torch
+    from paper_0708_4182_gb300 import workloads as wl
+    out = {}
+    for name, w, steps in (("droplet_128x64_f0.25", wl.droplet_128x64(0.25), 2000),
+                           ("rough_channel_1024x128_level15", wl.rough_channel(level=15), 2000)):
+        lat = lbm.Lattice(w.nx, w.ny, stream=stream, **w.params)
+        lat.set_geometry(w.mask)
+        lat.set_rho_u(w.rho)
+        lat.step(20)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        lat.step(steps)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        out[name] = {"mlups": round(w.nx * w.ny * steps / dt / 1e6, 1), "steps": steps}
+        lat.close()
+    levels = (0, 5, 10, 15)
+    ws = [wl.rough_channel(level=lv) for lv in levels]
+    b = lbm.Batch([dict(nx=w.nx, ny=w.ny, storage=lbm.LBM_FP32_DEV, **w.params) for w in ws], stream=stream)
+    for w, d in zip(ws, b.domains):
+        d.set_geometry(w.mask)
+        d.set_rho_u(w.rho)
+    t = time.perf_counter()
+    steps, obs, ok = b.run_to_steady(1e-7, 1000, 300000)
+    dt = time.perf_counter() - t
+    b.close()
+    q = [o["flux_Q"] for o in obs]
+    out["rough_channel_1024x128_flux_vs_force"] = {
+        "workload": "1024x128 rough channel (roughness 8, seed 0), body force 1e-6, liquid up to the crests; "
+                    "steady when |dQ|/|Q| < 1e-7 per 1000 steps",
+        "levels": list(levels), "f": [wl.f_level(lv) for lv in levels],
+        "Q_over_Q0": [round(x / q[0], 5) for x in q], "steps_to_steady": steps, "all_steady": ok,
+        "seconds": round(dt, 2)}
+    return out
 
 
 # ----------------------------------------------------------------- batched sweep
@@ -501,6 +572,7 @@ def warm_start_sweep(lbm, stream, n_train=1024, epochs=40, n_eval=64):
         "surrogate": f"U-Net 4 levels, 32 base channels, BF16 storage / FP32 sums, trained {epochs} epochs "
                      f"on {info['samples']} steady states (seed 100)",
         "surrogate_generate_s": round(info["generate_s"], 2), "surrogate_train_s": round(info["train_s"], 2),
+        "surrogate_train_rel_l2": {k: round(v, 4) for k, v in info["train_rel_l2"].items()},
         "plain_one_domain_at_a_time_s": round(t_plain, 3), "batched_cold_s": round(t_cold, 3),
         "batched_warm_s": round(t_warm, 3), "speedup_vs_plain": round(t_plain / t_warm, 2),
         "speedup_warm_vs_batched_cold": round(t_cold / t_warm, 2),

@@ -107,6 +107,15 @@ int unet_mse(const float *pred, const float *target, const float *wc, int c, int
 int unet_adam(float *w_master, void *w_bf16, const float *grad, float *m, float *v, long count, float lr,
               float beta1, float beta2, float eps, int step, float weight_decay, void *stream);
 
+/* Warm-start fields of n domains (n <= 65535) from the network output y
+ * [n][3][hw] (FP32, normalised): on fluid nodes (mask [n][hw] == 0)
+ * rho = clamp(y0 * rho_std + rho_mean, lo, hi) and u = (y1, y2) * u_scale;
+ * 0 on solid nodes; then each domain's rho is scaled so that it sums to
+ * mass[b]. out [n][3][hw] FP64 (the LBM_RHO_U_PHYS layout of each domain);
+ * sums [n] FP64 scratch. */
+int unet_warm_fields(const float *y, int n, int hw, const unsigned char *mask, const double *mass, float rho_mean,
+                     float rho_std, float u_scale, double lo, double hi, double *out, double *sums, void *stream);
+
 /* y = BF16(x), count elements. */
 int unet_f32_to_bf16(const float *x, void *y, long count, void *stream);
 

@@ -662,6 +662,46 @@ __global__ void f32_to_bf16_kernel(const float* __restrict__ x, bf16* __restrict
         y[i] = __float2bfloat16_rn(x[i]);
 }
 
+// Warm-start fields from the network output y [n][3][hw] (normalised): on
+// fluid nodes (mask 0) rho = clamp(y0 rho_std + rho_mean, lo, hi), u = y1,2
+// u_scale; 0 on solids. out [n][3][hw] FP64; sums[b] += sum of rho over image b.
+__global__ void warm_decode_kernel(const float* __restrict__ y, int hw, int n, const uint8_t* __restrict__ mask,
+                                   float rho_mean, float rho_std, float u_scale, double lo, double hi,
+                                   double* __restrict__ out, double* __restrict__ sums)
+{
+    __shared__ double red[kT];
+    const int b = blockIdx.y;
+    double s = 0.0;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < hw; p += gridDim.x * blockDim.x) {
+        const bool fluid = mask[(size_t)b * hw + p] == 0;
+        const float* yb = y + (size_t)b * 3 * hw;
+        double r = double(yb[p]) * rho_std + rho_mean;
+        r = fluid ? fmin(fmax(r, lo), hi) : 0.0;
+        double* ob = out + (size_t)b * 3 * hw;
+        ob[p] = r;
+        ob[hw + p] = fluid ? double(yb[hw + p]) * u_scale : 0.0;
+        ob[2 * hw + p] = fluid ? double(yb[2 * hw + p]) * u_scale : 0.0;
+        s += r;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = kT / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(&sums[b], red[0]);
+}
+
+// rho of image b scaled by mass[b] / sums[b]
+__global__ void warm_scale_kernel(int hw, const double* __restrict__ mass, const double* __restrict__ sums,
+                                  double* __restrict__ out)
+{
+    const int b = blockIdx.y;
+    const double k = sums[b] > 0.0 ? mass[b] / sums[b] : 1.0;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < hw; p += gridDim.x * blockDim.x)
+        out[(size_t)b * 3 * hw + p] *= k;
+}
+
 int blocks_for(long long n) { return int(n / kT + 1 < 4096 ? n / kT + 1 : 4096); }
 
 int status(cudaError_t e) { return e == cudaSuccess ? 0 : int(e); }
@@ -882,6 +922,19 @@ int unet_adam(float* w_master, void* w_bf16, const float* grad, float* m, float*
     adam_kernel<<<blocks_for(count), kT, 0, (cudaStream_t)stream>>>(w_master, (bf16*)w_bf16, grad, m, v, count, lr,
                                                                     beta1, beta2, eps, 1.f - c1, 1.f - c2,
                                                                     weight_decay);
+    return status(cudaGetLastError());
+}
+
+int unet_warm_fields(const float* y, int n, int hw, const uint8_t* mask, const double* mass, float rho_mean,
+                     float rho_std, float u_scale, double lo, double hi, double* out, double* sums, void* stream)
+{
+    if (n < 1 || n > 65535 || hw < 1) return -1;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(sums, 0, size_t(n) * sizeof(double), st);
+    if (e != cudaSuccess) return int(e);
+    const int bx = (hw + kT - 1) / kT < 64 ? (hw + kT - 1) / kT : 64;
+    warm_decode_kernel<<<dim3(bx, n), kT, 0, st>>>(y, hw, n, mask, rho_mean, rho_std, u_scale, lo, hi, out, sums);
+    warm_scale_kernel<<<dim3(bx, n), kT, 0, st>>>(hw, mass, sums, out);
     return status(cudaGetLastError());
 }
 

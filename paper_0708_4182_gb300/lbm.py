@@ -264,6 +264,10 @@ class Lattice:
                              for v in (rho, ux, uy)])
         self._set(LBM_RHO_U_PHYS if physical else LBM_RHO_U, data, 3)
 
+    def set_rho_u_field(self, data, physical=False):
+        """(rho, u_x, u_y) as one [3, ny, nx] array or device tensor (FP64)."""
+        self._set(LBM_RHO_U_PHYS if physical else LBM_RHO_U, data, 3)
+
     def set_populations(self, f):
         self._set(LBM_POPS, f, 9)
 

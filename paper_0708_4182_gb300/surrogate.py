@@ -60,6 +60,7 @@ def load_unet():
         "unet_mse": ([vp, vp, vp, I, I, L, vp, vp, vp], I),
         "unet_adam": ([vp, vp, vp, vp, vp, L, F, F, F, F, I, F, vp], I),
         "unet_f32_to_bf16": ([vp, vp, L, vp], I),
+        "unet_warm_fields": ([vp, I, I, vp, vp, F, F, F, ctypes.c_double, ctypes.c_double, vp, vp, vp], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -333,20 +334,44 @@ class UNet:
         rho = out[:, 0] * nm["rho_std"] + nm["rho_mean"]
         return rho, out[:, 1] * nm["u_scale"], out[:, 2] * nm["u_scale"]
 
-    def predict(self, planes):
-        """Decoded (rho, u_x, u_y) device tensors [N, H, W] for input planes
-        [N, 3, H, W], N any size (run in batches of the network's batch)."""
+    def predict_raw(self, planes):
+        """Normalised network output [N, 3, H, W] (FP32, device) for input
+        planes [N, 3, H, W], N any size (run in batches of the network's batch)."""
         t = self.torch
         n = planes.shape[0]
-        outs = []
+        out = t.empty((n, OUT_CH, self.H, self.W), dtype=t.float32, device=self.dev)
         for i in range(0, n, self.batch):
             chunk = planes[i:i + self.batch]
             k = chunk.shape[0]
             if k < self.batch:
                 chunk = t.cat([chunk, chunk[-1:].expand(self.batch - k, -1, -1, -1)])
-            outs.append(self.forward(chunk)[:k].clone())
-        out = t.cat(outs)
-        return self.decode(out)
+            out[i:i + k] = self.forward(chunk)[:k]
+        return out
+
+    def predict(self, planes):
+        """Decoded (rho, u_x, u_y) device tensors [N, H, W] for input planes."""
+        return self.decode(self.predict_raw(planes))
+
+    def warm_fields(self, planes, masks, mass, rho_range):
+        """Initial (rho, u_x, u_y) of N domains as one FP64 device tensor
+        [N, 3, H, W] (each [3, H, W] slice in the LBM_RHO_U_PHYS layout): the
+        decoded prediction with rho clamped to rho_range on fluid nodes, 0 on
+        solids, and each domain's rho scaled to sum to mass[i] (the method
+        conserves mass, and its steady state depends on it). masks: [N, H, W]
+        (1 = solid); mass: N values."""
+        t = self.torch
+        raw = self.predict_raw(planes)
+        n = raw.shape[0]
+        m = t.as_tensor(np.asarray(masks), dtype=t.uint8, device=self.dev).contiguous()
+        ms = t.as_tensor(np.asarray(mass, dtype=np.float64), device=self.dev)
+        out = t.empty((n, OUT_CH, self.H, self.W), dtype=t.float64, device=self.dev)
+        sums = t.empty(n, dtype=t.float64, device=self.dev)
+        nm = self.norm
+        _call(self.lib.unet_warm_fields, ctypes.c_void_p(raw.data_ptr()), n, self.H * self.W,
+              ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(ms.data_ptr()), nm["rho_mean"], nm["rho_std"],
+              nm["u_scale"], float(rho_range[0]), float(rho_range[1]), ctypes.c_void_p(out.data_ptr()),
+              ctypes.c_void_p(sums.data_ptr()), self.s)
+        return out
 
 
 # ---------------------------------------------------------------- warm start
@@ -453,23 +478,19 @@ def fit(ws, epochs=40, lr=2e-3, batch=16, seed=0, stream=None, wc=(1.0, 1.0, 0.2
     info["loss"] = train(net, planes, targets, epochs=epochs, lr=lr, wc=wc, seed=seed)
     torch.cuda.synchronize()
     info["train_s"] = time.perf_counter() - t0
+    # fit on (up to 64 of) the training states, relative L2 over fluid nodes
+    k = min(64, planes.shape[0])
+    rho, ux, _ = net.predict(planes[:k])
+    fl = masks[:k] == 0
+    info["train_rel_l2"] = {
+        "rho": float(torch.linalg.norm((rho - fields[:k, 0])[fl]) / torch.linalg.norm(fields[:k, 0][fl])),
+        "u_x": float(torch.linalg.norm((ux - fields[:k, 1])[fl]) / torch.linalg.norm(fields[:k, 1][fl]))}
     return net, info
 
 
-def warm_fields(pred, w):
-    """Prediction -> (rho, u_x, u_y) FP64 device tensors for lbm_set_field
-    (LBM_RHO_U_PHYS): densities clipped to the coexistence range, zero on
-    solid nodes, and scaled so that the mass equals that of the cold start
-    (the steady state the method reaches depends on the mass it conserves)."""
-    import torch
-    from . import workloads as wl
-    rho, ux, uy = pred
-    fluid = torch.as_tensor(w.mask == 0, device=rho.device)
-    rho = torch.where(fluid, rho.double().clamp(0.5 * wl.RHO_V, 1.1 * wl.RHO_L), 0.0)
-    m0 = float(np.sum(np.where(w.mask == 0, w.rho, 0.0)))
-    rho = rho * (m0 / float(rho.sum()))
-    z = torch.zeros((), dtype=torch.float64, device=rho.device)
-    return rho, torch.where(fluid, ux.double(), z), torch.where(fluid, uy.double(), z)
+def cold_mass(w) -> float:
+    """Mass of a workload's cold start (sum of rho over fluid nodes)."""
+    return float(np.sum(np.where(w.mask == 0, w.rho, 0.0)))
 
 
 def batch_run_to_steady(ws, net=None, stream=None, rel_tol=1e-7, check_every=1000, max_steps=60000,
@@ -490,11 +511,13 @@ def batch_run_to_steady(ws, net=None, stream=None, rel_tol=1e-7, check_every=100
     [N] lists}."""
     from . import lbm as L
     storage = L.LBM_FP32_DEV if storage is None else storage
+    from . import workloads as wl
     warm = [net is not None and bool(policy(w.mask)) for w in ws]
-    pred = None
+    fields = None
     if any(warm):
         sel = [w for w, f in zip(ws, warm) if f]
-        pred = net.predict(channel_planes(net, sel))
+        fields = net.warm_fields(channel_planes(net, sel), np.stack([w.mask for w in sel]),
+                                 [cold_mass(w) for w in sel], (0.5 * wl.RHO_V, 1.1 * wl.RHO_L))
     b = L.Batch([dict(nx=w.nx, ny=w.ny, storage=storage, **w.params) for w in ws], stream=stream)
     info = dict(warm=warm, restarted=[False] * len(ws), probe_residuals=[[] for _ in ws])
     try:
@@ -502,7 +525,7 @@ def batch_run_to_steady(ws, net=None, stream=None, rel_tol=1e-7, check_every=100
         for w, d, f in zip(ws, b.domains, warm):
             d.set_geometry(w.mask)
             if f:
-                d.set_rho_u(*warm_fields((pred[0][k], pred[1][k], pred[2][k]), w), physical=True)
+                d.set_rho_u_field(fields[k], physical=True)
                 k += 1
             else:
                 d.set_rho_u(w.rho)

@@ -205,3 +205,26 @@ def test_training_reduces_loss(env):
         net.adam(lr=2e-3)
     net.check_tensor_cores()
     assert losses[-1] < 0.2 * losses[0], (losses[0], losses[-1])
+
+
+def test_warm_fields_kernel(env):
+    """Decode, clamp, mask and per-domain mass rescale of the warm-start
+    fields against the same steps in FP64 on the host."""
+    t, surrogate, lib = env
+    net = surrogate.UNet(batch=2, height=32, width=256, seed=2)
+    net.norm = dict(rho_mean=1.5, rho_std=0.7, u_scale=0.05)
+    g = t.Generator().manual_seed(11)
+    n = 3
+    planes = t.rand((n, 3, 32, 256), generator=g).cuda()
+    masks = (t.rand((n, 32, 256), generator=g) < 0.2).numpy().astype(np.uint8)
+    mass = [1000.0, 2000.0, 3000.0]
+    lo, hi = 0.03, 3.0
+    out = net.warm_fields(planes, masks, mass, (lo, hi)).cpu().double()
+    raw = net.predict_raw(planes).cpu().double()
+    fluid = t.as_tensor(masks == 0)
+    rho = t.where(fluid, (raw[:, 0] * 0.7 + 1.5).clamp(lo, hi), t.zeros(()).double())
+    rho = rho * (t.tensor(mass, dtype=t.float64) / rho.sum(dim=(1, 2)))[:, None, None]
+    assert t.allclose(out[:, 0], rho, rtol=1e-6, atol=1e-9)
+    assert t.allclose(out[:, 1], t.where(fluid, raw[:, 1] * 0.05, t.zeros(()).double()), rtol=1e-6, atol=1e-9)
+    assert t.allclose(out[:, 2], t.where(fluid, raw[:, 2] * 0.05, t.zeros(()).double()), rtol=1e-6, atol=1e-9)
+    assert out[:, 0].sum(dim=(1, 2)).tolist() == pytest.approx(mass, rel=1e-12)
