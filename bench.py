@@ -474,15 +474,16 @@ def run_batch_measurements(lbm, stream, rank=0, world=1):
     torch.cuda.synchronize()
     ms_step = replicas.max_over_ranks(e0.elapsed_time(e1) / 100, device="cuda")
     nodes = int(replicas.sum_over_ranks(nodes, device="cuda"))
-    # the same domains one at a time (first 32, 20 steps each)
+    # the same domains one at a time (first 32, 64 steps each: two CUDA
+    # graphs of 32 steps per domain)
     seq_t, seq_nodes = 0.0, 0
     for w, d in zip(ws[:32], b.domains[:32]):
         torch.cuda.synchronize()
         t = time.perf_counter()
-        d.step(20)
+        d.step(64)
         torch.cuda.synchronize()
         seq_t += time.perf_counter() - t
-        seq_nodes += 20 * w.nx * w.ny
+        seq_nodes += 64 * w.nx * w.ny
     b.close()
     out["batched"] = {
         "workload": f"{len(all_ws)} rough channels (width 32-256, length 512-2048, roughness 0-8, level 0-15, "

@@ -164,8 +164,10 @@ lbm_status lbm_set_field(lbm_ctx *ctx, int which, const double *data, int on_dev
  * Synchronises the context's stream when out is host memory. */
 lbm_status lbm_get_field(lbm_ctx *ctx, int which, double *out, int on_device);
 
-/* Advance nsteps >= 0 time steps (asynchronous). LBM_ESTATE before geometry
- * and field are set. */
+/* Advance nsteps >= 0 time steps (asynchronous). Runs of 32 plain steps
+ * with no fused-observables step among them are replayed as one CUDA graph
+ * (built on first use, per context). LBM_ESTATE before geometry and field
+ * are set. */
 lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps);
 
 /* Observables of the current state (Eq. 11 and mass/momentum bookkeeping),

@@ -27,6 +27,7 @@ namespace lbm {
 namespace {
 
 constexpr int kRing = 64;
+constexpr int kGraphSteps = 32;  // plain steps per CUDA graph of lbm_step (even)
 constexpr size_t kStagingMax = size_t(16) << 20;
 constexpr int kAuxThreads = 256;
 
@@ -581,6 +582,14 @@ struct lbm_ctx {
     int ring_count = 0;
     bool has_geometry = false, has_field = false;
     char err[512] = {0};
+    // kGraphSteps plain steps as one CUDA graph, one per buffer holding the
+    // current state (buffer A, buffer B); built on first use
+    cudaGraphExec_t step_graph[2] = {nullptr, nullptr};
+    ~lbm_ctx()
+    {
+        for (cudaGraphExec_t e : step_graph)
+            if (e) cudaGraphExecDestroy(e);
+    }
 };
 
 namespace {
@@ -643,6 +652,66 @@ lbm_status launch_step(lbm_ctx* c, const float* fin, float* fout, double* fields
     default: return launch_step_st<MODE, kF32>(c, fin, fout, fields);
     }
 }
+
+// Step kernel (plain step, no observables) of a storage form.
+template <int ST> const void* plain_step_ptr() { return reinterpret_cast<const void*>(&step_kernel<kStep, ST>); }
+
+const void* plain_step_kernel(int storage)
+{
+    switch (storage) {
+    case LBM_FP32_DEV: return plain_step_ptr<kF32Dev>();
+    case LBM_FP16_DEV: return plain_step_ptr<kF16Dev>();
+    case LBM_BF16_DEV: return plain_step_ptr<kBF16Dev>();
+    default: return plain_step_ptr<kF32>();
+    }
+}
+
+size_t step_smem(int storage)
+{
+    switch (storage) {
+    case LBM_FP32_DEV: return smem_bytes<kF32Dev>();
+    case LBM_FP16_DEV: return smem_bytes<kF16Dev>();
+    case LBM_BF16_DEV: return smem_bytes<kBF16Dev>();
+    default: return smem_bytes<kF32>();
+    }
+}
+
+// kGraphSteps (even) plain steps starting from the current buffer, as one
+// explicitly built graph of kernel nodes; an even count returns the state
+// to the same buffer, so the graph replays for as long as the context lives.
+lbm_status step_graph(lbm_ctx* c, cudaGraphExec_t* out)
+{
+    const int slot = c->cur == reinterpret_cast<float*>(c->ws + c->L.off_a) ? 0 : 1;
+    if (c->step_graph[slot]) {
+        *out = c->step_graph[slot];
+        return LBM_OK;
+    }
+    cudaGraph_t graph = nullptr;
+    lbm_status s = check_cuda(c, cudaGraphCreate(&graph, 0), "graph create");
+    if (s) return s;
+    cudaGraphNode_t prev = nullptr;
+    double* no_fields = nullptr;
+    for (int k = 0; k < kGraphSteps && !s; ++k) {
+        const float* fin = (k & 1) ? c->nxt : c->cur;
+        float* fout = (k & 1) ? c->cur : c->nxt;
+        void* args[] = {&fin, &fout, &c->g, &c->ph, &c->partials, &no_fields, &c->status};
+        cudaKernelNodeParams kp{};
+        kp.func = const_cast<void*>(plain_step_kernel(c->prm.storage));
+        kp.gridDim = c->grid;
+        kp.blockDim = dim3(kThreads);
+        kp.sharedMemBytes = static_cast<unsigned>(step_smem(c->prm.storage));
+        kp.kernelParams = args;
+        cudaGraphNode_t node;
+        s = check_cuda(c, cudaGraphAddKernelNode(&node, graph, prev ? &prev : nullptr, prev ? 1 : 0, &kp),
+                       "graph node");
+        prev = node;
+    }
+    if (!s) s = check_cuda(c, cudaGraphInstantiate(&c->step_graph[slot], graph, 0), "graph instantiate");
+    cudaGraphDestroy(graph);
+    if (!s) *out = c->step_graph[slot];
+    return s;
+}
+
 
 template <int MODE, int ST>
 cudaError_t allow_smem_st()
@@ -946,6 +1015,15 @@ lbm_status lbm_step(lbm_ctx* c, int64_t nsteps)
     if (nsteps < 0) return fail(c, LBM_EINVAL, "nsteps must be >= 0");
     const int K = c->prm.obs_every;
     for (int64_t k = 0; k < nsteps; ++k) {
+        // whole graphs of plain steps while no fused-observables step falls inside
+        if (nsteps - k >= kGraphSteps && (K == 0 || (c->t % K != 0 && c->t / K == (c->t + kGraphSteps - 1) / K))) {
+            cudaGraphExec_t exec;
+            if ((s = step_graph(c, &exec))) return s;
+            if ((s = check_cuda(c, cudaGraphLaunch(exec, c->stream), "graph launch"))) return s;
+            c->t += kGraphSteps;
+            k += kGraphSteps - 1;
+            continue;
+        }
         if (K > 0 && c->t % K == 0) {
             if ((s = launch_step<kStepObs>(c, c->cur, c->nxt, nullptr))) return s;
             if ((s = finalize(c, c->t, c->ring + (c->ring_count % kRing)))) return s;
