@@ -462,8 +462,8 @@ def run_batch_measurements(lbm, stream, rank=0, world=1):
     for w, d in zip(ws, b.domains):
         d.set_geometry(w.mask)
         d.set_rho_u(w.rho)
-    cands = (8, 16, 32, 64, 128)
-    chosen, ms = b.autotune(cands, steps=10)
+    cands = (16, 32, 64, 128)
+    chosen, chosen_ctas, table = b.autotune_grid(cands, (2, 3), steps=10)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if world > 1:
         dist.barrier()
@@ -490,7 +490,8 @@ def run_batch_measurements(lbm, stream, rank=0, world=1):
                     f"seed 0), FP32 populations, one persistent launch per step"
                     + (f", split over {world} ranks by node count" if world > 1 else ""),
         "nodes": nodes, "mlups": round(nodes / ms_step / 1e3, 1), "ms_per_step": round(ms_step, 4),
-        "tile_rows": chosen, "autotune_ms_per_step": {str(c): round(m, 4) for c, m in zip(cands, ms)},
+        "tile_rows": chosen, "ctas_per_sm": chosen_ctas,
+        "autotune_ms_per_step": {f"{r}rows_{c}ctas": round(m, 4) for (r, c), m in table.items()},
         "one_domain_at_a_time_mlups": round(seq_nodes / seq_t / 1e6, 1)}
     if world > 1:
         return out

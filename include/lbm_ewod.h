@@ -249,6 +249,19 @@ int32_t lbm_batch_tile_rows(const lbm_batch *b);
 lbm_status lbm_batch_autotune(lbm_batch *b, const int32_t *candidates, int32_t n, int32_t steps,
                               int32_t *chosen, double *ms_per_step);
 
+/* Resident CTAs per SM of the persistent grid (1, 2 or 3; default 3, the
+ * most the step kernel's shared memory allows). */
+lbm_status lbm_batch_set_ctas_per_sm(lbm_batch *b, int32_t ctas);
+int32_t lbm_batch_ctas_per_sm(const lbm_batch *b);
+
+/* Autotune over tile height x CTAs per SM: every pair (rows[i], ctas[j]) is
+ * timed as in lbm_batch_autotune, ms_per_step[j * nrows + i] (may be NULL)
+ * gets its time, and the fastest pair is kept (*chosen_rows, *chosen_ctas).
+ * Advances every active domain by nrows * nctas * (steps + 2) steps. */
+lbm_status lbm_batch_autotune_grid(lbm_batch *b, const int32_t *rows, int32_t nrows, const int32_t *ctas,
+                                   int32_t nctas, int32_t steps, int32_t *chosen_rows, int32_t *chosen_ctas,
+                                   double *ms_per_step);
+
 /* Step the active domains until each one's flux is steady (criterion as in
  * lbm_run_to_steady, checked every check_every steps); a domain stops being
  * stepped once it is steady. steps_to_steady[count] gets each domain's time

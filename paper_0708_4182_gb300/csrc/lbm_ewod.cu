@@ -1209,6 +1209,7 @@ struct lbm_batch {
     cudaStream_t stream = nullptr;
     int sm_count = 0;
     int tile_rows = 0;                   // 0 = each domain's own choice
+    int ctas_per_sm = 3;                 // resident CTAs per SM of the persistent grid (1..3)
     // device tables (in the batch's own workspace region)
     DomainDev* d_dom = nullptr;
     int4* d_tiles = nullptr;
@@ -1375,7 +1376,11 @@ size_t batch_smem(int storage)
     }
 }
 
-int batch_grid(const lbm_batch* b) { return b->ntiles < 3 * b->sm_count ? b->ntiles : 3 * b->sm_count; }
+int batch_grid(const lbm_batch* b)
+{
+    const int slots = b->ctas_per_sm * b->sm_count;
+    return b->ntiles < slots ? b->ntiles : slots;
+}
 
 lbm_status launch_batch(lbm_batch* b, int mode, int parity)
 {
@@ -1696,6 +1701,48 @@ lbm_status lbm_batch_autotune(lbm_batch* b, const int32_t* candidates, int32_t n
     *chosen = pick;
     if ((s = lbm_batch_set_tile_rows(b, pick))) return s;
     return batch_check_status(b);
+}
+
+lbm_status lbm_batch_set_ctas_per_sm(lbm_batch* b, int32_t ctas)
+{
+    if (!b) return LBM_EINVAL;
+    if (ctas < 1 || ctas > 3) return bfail(b, LBM_EINVAL, "ctas_per_sm must be 1, 2 or 3");
+    b->ctas_per_sm = ctas;  // the graph is rebuilt when the grid changes
+    return LBM_OK;
+}
+
+int32_t lbm_batch_ctas_per_sm(const lbm_batch* b) { return b ? b->ctas_per_sm : -1; }
+
+lbm_status lbm_batch_autotune_grid(lbm_batch* b, const int32_t* rows, int32_t nrows, const int32_t* ctas,
+                                   int32_t nctas, int32_t steps, int32_t* chosen_rows, int32_t* chosen_ctas,
+                                   double* ms_per_step)
+{
+    lbm_status s = batch_ready(b);
+    if (s) return s;
+    if (!rows || nrows < 1 || !ctas || nctas < 1 || steps < 1 || !chosen_rows || !chosen_ctas)
+        return bfail(b, LBM_EINVAL, "bad arguments");
+    for (int j = 0; j < nctas; ++j)
+        if (ctas[j] < 1 || ctas[j] > 3) return bfail(b, LBM_EINVAL, "ctas_per_sm must be 1, 2 or 3");
+    double best = 1e300;
+    int32_t best_rows = b->tile_rows, best_ctas = b->ctas_per_sm;
+    std::vector<double> ms(nrows);
+    for (int j = 0; j < nctas; ++j) {
+        b->ctas_per_sm = ctas[j];
+        int32_t r = 0;
+        if ((s = lbm_batch_autotune(b, rows, nrows, steps, &r, ms.data()))) return s;
+        for (int i = 0; i < nrows; ++i) {
+            if (ms_per_step) ms_per_step[j * nrows + i] = ms[i];
+            if (ms[i] < best) {
+                best = ms[i];
+                best_rows = rows[i];
+                best_ctas = ctas[j];
+            }
+        }
+    }
+    b->ctas_per_sm = best_ctas;
+    *chosen_rows = best_rows;
+    *chosen_ctas = best_ctas;
+    return lbm_batch_set_tile_rows(b, best_rows);
 }
 
 const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err : "null batch"; }

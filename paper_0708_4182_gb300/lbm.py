@@ -377,6 +377,13 @@ def _batch_lib():
                                                   ctypes.POINTER(ctypes.c_double)]),
             "lbm_batch_run_to_steady": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int64, ctypes.c_int64,
                                                        ctypes.POINTER(ctypes.c_int64), O]),
+            "lbm_batch_set_ctas_per_sm": (ctypes.c_int, [vp, ctypes.c_int32]),
+            "lbm_batch_ctas_per_sm": (ctypes.c_int32, [vp]),
+            "lbm_batch_autotune_grid": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                                                       ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                                                       ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                                       ctypes.POINTER(ctypes.c_int32),
+                                                       ctypes.POINTER(ctypes.c_double)]),
             "lbm_batch_last_error": (ctypes.c_char_p, [vp]),
             "lbm_batch_destroy": (None, [vp]),
         }
@@ -453,6 +460,24 @@ class Batch:
         self._check(_batch_lib().lbm_batch_autotune(self.handle, c, len(candidates), int(steps),
                                                     ctypes.byref(chosen), ms))
         return int(chosen.value), list(ms)
+
+    def set_ctas_per_sm(self, ctas: int):
+        self._check(_batch_lib().lbm_batch_set_ctas_per_sm(self.handle, int(ctas)))
+
+    @property
+    def ctas_per_sm(self) -> int:
+        return int(_batch_lib().lbm_batch_ctas_per_sm(self.handle))
+
+    def autotune_grid(self, rows=(16, 32, 64, 128), ctas=(2, 3), steps: int = 10):
+        """Tile height x CTAs per SM; returns (rows, ctas, {(rows, ctas): ms per step})."""
+        r = (ctypes.c_int32 * len(rows))(*rows)
+        c = (ctypes.c_int32 * len(ctas))(*ctas)
+        ms = (ctypes.c_double * (len(rows) * len(ctas)))()
+        cr, cc = ctypes.c_int32(), ctypes.c_int32()
+        self._check(_batch_lib().lbm_batch_autotune_grid(self.handle, r, len(rows), c, len(ctas), int(steps),
+                                                         ctypes.byref(cr), ctypes.byref(cc), ms))
+        table = {(rows[i], ctas[j]): ms[j * len(rows) + i] for j in range(len(ctas)) for i in range(len(rows))}
+        return int(cr.value), int(cc.value), table
 
     def run_to_steady(self, rel_tol=1e-7, check_every=1000, max_steps=10 ** 6):
         steps = (ctypes.c_int64 * self.count)()

@@ -98,6 +98,32 @@ def test_batch_active_set_and_autotune(lbm):
     b.close()
 
 
+def test_batch_autotune_grid_and_ctas_per_sm(lbm):
+    """Tile height x CTAs per SM: every pair is timed, the fastest kept, and
+    the result does not depend on the grid (bitwise equal populations)."""
+    ws = sweep_workloads(4, seed=5)
+    outs = []
+    for ctas in (1, 3):
+        b = lbm.Batch(specs_of(ws))
+        for w, d in zip(ws, b.domains):
+            d.set_geometry(w.mask)
+            d.set_rho_u(w.rho)
+        b.set_ctas_per_sm(ctas)
+        assert b.ctas_per_sm == ctas
+        b.step(9)
+        outs.append([d.populations() for d in b.domains])
+        if ctas == 3:
+            rows, cts, table = b.autotune_grid((8, 32), (2, 3), steps=4)
+            assert set(table) == {(8, 2), (32, 2), (8, 3), (32, 3)} and all(v > 0 for v in table.values())
+            assert table[(rows, cts)] == min(table.values())
+            assert b.tile_rows == rows and b.ctas_per_sm == cts
+            with pytest.raises(lbm.LbmError):
+                b.set_ctas_per_sm(4)
+        b.close()
+    for a, c in zip(*outs):
+        assert np.array_equal(a, c)
+
+
 def test_batch_run_to_steady_matches_oracle(lbm):
     """Three smooth channels at levels 0, 10, 15 in one batch (FP32
     deviation storage), each run to steady flux; the steady Q match the
