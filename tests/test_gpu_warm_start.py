@@ -84,3 +84,39 @@ def test_rough_domains_keep_the_cold_start(trained):
         if cold_steps[i] > 0:
             assert steps[i] == cold_steps[i]
             assert obs[i]["flux_Q"] == cold_obs[i]["flux_Q"]
+
+
+def test_rough_walls_steady_flux_depends_on_the_path():
+    """Why rough walls keep their cold start, and why warm starts go through
+    LBM_RHO_U_PHYS: four rough channels run to steady flux and restart from
+    their own converged (rho, u). Restarted as f_eq(rho, u) (a momentum kick
+    of F/2 per node at every interface) at least one settles on another
+    steady flux; restarted with the force correction every one returns to
+    its flux within 1e-3 after a few thousand steps."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0708_4182_gb300 import lbm as L
+    L.load()
+    ws = [wl.warm_start_channels(32, seed=7)[i] for i in (11, 17, 18, 22)]
+    specs = [dict(nx=w.nx, ny=w.ny, storage=L.LBM_FP32_DEV, **w.params) for w in ws]
+
+    def run(setter):
+        b = L.Batch(specs)
+        for i, (w, d) in enumerate(zip(ws, b.domains)):
+            d.set_geometry(w.mask)
+            setter(i, w, d)
+        steps, obs, _ = b.run_to_steady(1e-7, 1000, 80000)
+        fields = [d.fields_device() for d in b.domains]
+        b.close()
+        return np.array(steps), np.array([o["flux_Q"] for o in obs]), fields
+
+    cold_steps, q_cold, f_cold = run(lambda i, w, d: d.set_rho_u(w.rho))
+    assert np.all(cold_steps > 0)
+    _, q_kick, _ = run(lambda i, w, d: d.set_rho_u_field(f_cold[i]))
+    phys_steps, q_phys, _ = run(lambda i, w, d: d.set_rho_u_field(f_cold[i], physical=True))
+    rel_kick = np.abs(q_kick / q_cold - 1)
+    rel_phys = np.abs(q_phys / q_cold - 1)
+    assert np.all(rel_phys <= 1e-3), rel_phys
+    assert np.all((phys_steps > 0) & (phys_steps <= 10000)), phys_steps
+    assert rel_kick.max() > 3e-3, rel_kick
