@@ -274,6 +274,120 @@ __global__ void __launch_bounds__(kTcThreads) conv3x3_tc_kernel(const bf16* __re
     if (warp == 0) tmem_dealloc(tmem, tmem_cols(NT));
 }
 
+// The same convolution for images at least 128 pixels wide: one CTA = 128
+// consecutive pixels of one image row. Per 16-channel chunk the CTA stages a
+// halo of 3 rows x 130 pixels once, pixels at a uniform 16-byte pitch (two
+// planes of 8 channels, LBO = the plane distance, SBO = 8 pixels), and the 9
+// taps are 9 MMAs whose A descriptors start at that halo shifted by dx pixels
+// (16 bytes each) and dy rows: the input crosses shared memory once per chunk
+// instead of once per tap. Two stages: the next chunk loads while the MMAs of
+// this one run.
+constexpr int kRowPix = 128, kHaloPix = kRowPix + 2;
+constexpr int kHaloPlane = kHaloPix * 16;      // bytes of one 8-channel plane of one halo row
+constexpr int kHaloBytes = 3 * 2 * kHaloPlane; // 3 rows x 2 planes
+
+template <int NT>
+__global__ void __launch_bounds__(kTcThreads) conv3x3_tc_row_kernel(const bf16* __restrict__ x, int ct_in, int kc,
+                                                                    const bf16* __restrict__ wt,
+                                                                    const float* __restrict__ bias,
+                                                                    bf16* __restrict__ y, int ct_out, int H, int W,
+                                                                    int relu, int* __restrict__ err)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    constexpr int kRowStages = 2;
+    constexpr int kBBytes = 9 * NT * 16 * 2;  // the 9 taps' weights of one chunk
+    unsigned char* sa = smem;
+    unsigned char* sb = smem + kRowStages * kHaloBytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sb + kRowStages * kBBytes);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + kRowStages);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tiles_x = W / kRowPix;
+    const int y0 = blockIdx.x / tiles_x, x0 = (blockIdx.x % tiles_x) * kRowPix;
+    const int nb = blockIdx.y, b = blockIdx.z;
+    const bf16* wblk = wt + size_t(nb) * kc * 9 * NT * 16;
+
+    if (tid == 0) {
+        for (int s = 0; s < kRowStages; ++s) mbar_init(&bars[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(tmem_slot, tmem_cols(NT));
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    auto load = [&](int c) {
+        const int s = c % kRowStages;
+        unsigned char* da = sa + s * kHaloBytes;
+        // 3 rows x 130 pixels x 2 planes of 16 bytes
+        for (int q = tid; q < 3 * kHaloPix * 2; q += kTcThreads) {
+            const int h = q & 1, pix = (q >> 1) % kHaloPix, r = (q >> 1) / kHaloPix;
+            const int yy = y0 + r - 1, xx = wrapx(x0 + pix - 1, W);
+            const bool ok = yy >= 0 && yy < H;
+            const bf16* src = ok ? x + (size_t(b * H + yy) * W + xx) * ct_in + c * 16 + h * 8 : x;
+            cp_async16_ca(da + (r * 2 + h) * kHaloPlane + pix * 16, src, ok ? 16u : 0u);
+        }
+        const bf16* wsrc = wblk + size_t(c) * 9 * NT * 16;
+        unsigned char* db = sb + s * kBBytes;
+        for (int q = tid; q < 9 * NT * 2; q += kTcThreads) cp_async16_cg(db + q * 16, wsrc + q * 8, 16u);
+    };
+
+    constexpr uint32_t idesc = idesc_bf16(NT, false, false);
+    load(0);
+    cp_async_commit();
+#pragma unroll 1
+    for (int c = 0; c < kc; ++c) {
+        const int s = c % kRowStages;
+        cp_async_wait<0>();
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(sa + s * kHaloBytes);
+            const uint32_t b0 = smem_u32(sb + s * kBBytes);
+#pragma unroll 1
+            for (int t = 0; t < 9; ++t) {
+                const int dy = t / 3, dx = t % 3;  // halo row and pixel shift of this tap
+                const uint64_t da = smem_desc(a0 + dy * 2 * kHaloPlane + dx * 16, kHaloPlane, 128);
+                const uint64_t db = smem_desc(b0 + t * NT * 32, 128, 256);
+                mma_bf16(tmem, da, db, idesc, (c > 0 || t > 0) ? 1u : 0u);
+            }
+            mma_commit(&bars[s]);
+        }
+        if (c + 1 < kc) {
+            // the buffer of chunk c + 1 was last read by the MMAs of chunk c - 1
+            if (c >= 1) mbar_wait(&bars[(c + 1) % kRowStages], uint32_t(((c + 1) / kRowStages) - 1) & 1u, err);
+            load(c + 1);
+        }
+        cp_async_commit();
+    }
+    cp_async_wait<0>();
+    mbar_wait(&bars[(kc - 1) % kRowStages], uint32_t((kc - 1) / kRowStages) & 1u, err);
+    tc_fence_after();
+
+    const int p = warp * 32 + lane;
+    bf16* out = y + (size_t(b * H + y0) * W + x0 + p) * ct_out + nb * NT;
+#pragma unroll 1
+    for (int n0 = 0; n0 < NT; n0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + n0, v);
+        __align__(16) bf16 o[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            float a = v[j] + (bias ? bias[nb * NT + n0 + j] : 0.f);
+            if (relu) a = fmaxf(a, 0.f);
+            o[j] = __float2bfloat16_rn(a);
+        }
+        uint4* dst = reinterpret_cast<uint4*>(out + n0);
+        dst[0] = reinterpret_cast<const uint4*>(o)[0];
+        dst[1] = reinterpret_cast<const uint4*>(o)[1];
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, tmem_cols(NT));
+}
+
 // Packed B operand of the tensor-core convolution. Forward (transpose = 0):
 // row n = output channel, column k = input channel, B[n][k](tap) =
 // w[n][k][tap]. Input gradient (transpose = 1): row n = input channel of the
@@ -716,9 +830,25 @@ int* err_ptr()
 }
 
 template <int NT>
+int launch_conv_row(const void* x, int ct_in, int kc, const void* wt, const float* bias, void* y, int ct_out,
+                    int cout, int n, int h, int wd, int relu, cudaStream_t st)
+{
+    constexpr int needed = 2 * (kHaloBytes + 9 * NT * 32) + 2 * 8 + 16;
+    const int smem = smem_for_tmem(int(tmem_cols(NT)), needed);
+    auto k = conv3x3_tc_row_kernel<NT>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return int(e);
+    dim3 grid(h * (wd / kRowPix), cout / NT, n);
+    k<<<grid, kTcThreads, smem, st>>>((const bf16*)x, ct_in, kc, (const bf16*)wt, bias, (bf16*)y, ct_out, h, wd, relu,
+                                      err_ptr());
+    return status(cudaGetLastError());
+}
+
+template <int NT>
 int launch_conv(const void* x, int ct_in, int kc, const void* wt, const float* bias, void* y, int ct_out, int cout,
                 int n, int h, int wd, int relu, cudaStream_t st)
 {
+    if (wd % kRowPix == 0) return launch_conv_row<NT>(x, ct_in, kc, wt, bias, y, ct_out, cout, n, h, wd, relu, st);
     constexpr int needed = kStages * (128 * 32 + NT * 32) + kStages * 8 + 16;
     const int smem = smem_for_tmem(int(tmem_cols(NT)), needed);
     auto k = conv3x3_tc_kernel<NT>;
