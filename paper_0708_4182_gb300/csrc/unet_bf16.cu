@@ -12,11 +12,12 @@
 // canonical no-swizzle layout (8-row x 16-byte core matrices), completion
 // tracked by tcgen05.commit on mbarriers, the accumulator read back with
 // tcgen05.ld for the epilogue. Forward and input-gradient convolutions are an
-// implicit GEMM with M = 128 output pixels (4 rows x 32 columns), N = a tile
-// of output channels, K = 16 input channels of one of the 9 taps per MMA
-// (both operands K-major: channels are contiguous per pixel). The weight
-// gradient is a GEMM per tap with M = 128 output channels, N = a tile of
-// input channels and K = 16 pixels per MMA (both operands MN-major).
+// implicit GEMM with M = 128 output pixels (one row of 128, or 4 rows x 32
+// columns for narrower images), N = a tile of output channels, K = 16 input
+// channels of one of the 9 taps per MMA (both operands K-major: channels are
+// contiguous per pixel). The weight gradient is a GEMM per tap with M = 128
+// output channels, N = a tile of input channels and K = 16 pixels per MMA
+// (both operands MN-major), the 3 taps of a row sharing a CTA's staged operands.
 //
 // A tensor "view" is (pointer to its first channel, channels per pixel of
 // the underlying buffer), so a layer reads or writes a channel range of a
@@ -148,8 +149,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// TMEM columns to allocate for an accumulator of n FP32 columns (a power of two >= 32)
-__host__ __device__ constexpr uint32_t tmem_cols(int n) { return n <= 32 ? 32u : (n <= 64 ? 64u : (n <= 128 ? 128u : 256u)); }
+// TMEM columns to allocate for accumulators spanning n FP32 columns (a power
+// of two >= 32, at most the 512 of an SM; n > 512 cannot be allocated)
+__host__ __device__ constexpr uint32_t tmem_cols(int n)
+{
+    return n <= 32 ? 32u : (n <= 64 ? 64u : (n <= 128 ? 128u : (n <= 256 ? 256u : 512u)));
+}
 
 // Dynamic shared memory that lets at most 512 / cols CTAs share an SM, so
 // their tensor-memory allocations (cols columns each) always fit in the 512.
@@ -176,6 +181,7 @@ __global__ void __launch_bounds__(kTcThreads) conv3x3_tc_kernel(const bf16* __re
                                                                 int relu, int* __restrict__ err)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
+    static_assert(NT <= int(tmem_cols(NT)), "the accumulator must fit the allocation");
     constexpr int kABytes = 128 * 16 * 2;  // 128 pixels x 16 channels
     constexpr int kBBytes = NT * 16 * 2;   // NT channels x 16 channels
     unsigned char* sa = smem;
@@ -294,6 +300,7 @@ __global__ void __launch_bounds__(kTcThreads) conv3x3_tc_row_kernel(const bf16* 
                                                                     int relu, int* __restrict__ err)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
+    static_assert(NT <= int(tmem_cols(NT)), "the accumulator must fit the allocation");
     constexpr int kRowStages = 2;
     constexpr int kBBytes = 9 * NT * 16 * 2;  // the 9 taps' weights of one chunk
     unsigned char* sa = smem;
@@ -418,19 +425,27 @@ __global__ void conv_pack_kernel(const float* __restrict__ w, int co, int ci, in
 }
 
 // ------------------------------------------------------------------ tensor-core weight gradient
-// dw[co][ci][tap] += sum_{b, p} dy[b, p, co] x[b, p + off(tap), ci] over this
-// CTA's pixel range: M = 128 output channels (rows beyond co stay zero),
-// N = NT input channels, K = 16 pixels of one image row per MMA; both
-// operands MN-major (channels contiguous per pixel).
+// Weight gradient, one CTA per tap row: per K-step of 16 pixels of one image
+// row, dy (A, 128 output channels x 16 pixels) is staged once and x as a halo
+// row of 18 pixels x NT channels (B, MN-major, pixels at a uniform 16-byte
+// pitch within a channel group: SBO = 18 pixels, LBO = 8 pixels); the three
+// taps (dy, dx = -1, 0, 1) of the row are three MMAs whose B descriptors start
+// dx pixels in, into three accumulators of NT columns (3 NT <= 128 tensor-memory
+// columns, so four CTAs share an SM).
+constexpr int kWHaloPix = 18;
+
 template <int NT>
-__global__ void __launch_bounds__(kTcThreads) wgrad_tc_kernel(const bf16* __restrict__ x, int ct_x, int ci,
-                                                              const bf16* __restrict__ dy, int ct_dy, int co,
-                                                              float* __restrict__ dw, int H, int W, int npix,
-                                                              int* __restrict__ err)
+__global__ void __launch_bounds__(kTcThreads) wgrad_tc_taps_kernel(const bf16* __restrict__ x, int ct_x, int ci,
+                                                                   const bf16* __restrict__ dy, int ct_dy, int co,
+                                                                   float* __restrict__ dw, int H, int W, int npix,
+                                                                   int* __restrict__ err)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    constexpr int kABytes = 128 * 16 * 2;  // 128 output channels x 16 pixels
-    constexpr int kBBytes = NT * 16 * 2;   // NT input channels x 16 pixels
+    static_assert(3 * NT <= int(tmem_cols(3 * NT)), "three accumulators must fit the allocation");
+    constexpr int G = NT / 8;                              // 8-channel groups of B
+    constexpr int kABytes = 128 * 16 * 2;                  // 128 output channels x 16 pixels
+    constexpr int kBBytes = G * kWHaloPix * 16;            // one halo row of B
+    constexpr uint32_t kCols = tmem_cols(3 * NT);
     unsigned char* sa = smem;
     unsigned char* sb = smem + kStages * kABytes;
     uint64_t* bars = reinterpret_cast<uint64_t*>(sb + kStages * kBBytes);
@@ -438,29 +453,29 @@ __global__ void __launch_bounds__(kTcThreads) wgrad_tc_kernel(const bf16* __rest
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int co0 = blockIdx.x * 128, ci0 = blockIdx.y * NT;
-    const int tap = blockIdx.z % 9, split = blockIdx.z / 9;
-    const int dyo = tap / 3 - 1, dxo = tap % 3 - 1;
+    const int trow = blockIdx.z % 3;                       // taps 3 trow .. 3 trow + 2 (row offset trow - 1)
     const int co_here = co - co0 < 128 ? co - co0 : 128;
     const int ci_here = ci - ci0 < NT ? ci - ci0 : NT;
-    const long long p_begin = (long long)split * npix;
+    const long long p_begin = (long long)(blockIdx.z / 3) * npix;
     const int KT = npix / 16;
 
-    // rows of A beyond co_here are never loaded: zero them once
-    for (int i = tid; i < kStages * kABytes / 16; i += kTcThreads) reinterpret_cast<uint4*>(sa)[i] = make_uint4(0, 0, 0, 0);
+    // rows of A beyond co_here and channel groups of B beyond ci_here are never loaded: zero them once
+    for (int i = tid; i < kStages * (kABytes + kBBytes) / 16; i += kTcThreads)
+        reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) tmem_alloc(tmem_slot, tmem_cols(NT));
+    if (warp == 0) tmem_alloc(tmem_slot, kCols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const int ga = co_here / 8, gb = (ci_here + 7) / 8;  // 16-byte channel groups of A and B
+    const int ga = co_here / 8, gb = (ci_here + 7) / 8;
     auto load = [&](int it) {
         const int s = it % kStages;
-        const long long p0 = p_begin + (long long)it * 16;  // 16 pixels of one image row
+        const long long p0 = p_begin + (long long)it * 16;
         const int bimg = int(p0 / ((long long)H * W));
         const int rem = int(p0 % ((long long)H * W));
         const int yy = rem / W, x0 = rem % W;
@@ -471,13 +486,13 @@ __global__ void __launch_bounds__(kTcThreads) wgrad_tc_kernel(const bf16* __rest
             const bf16* src = dy + (size_t(bimg * H + yy) * W + x0 + k) * ct_dy + co0 + g * 8;
             cp_async16_cg(da + g * 256 + (k >> 3) * 128 + (k & 7) * 16, src, 16u);
         }
-        const int ys = yy + dyo;
+        const int ys = yy + trow - 1;
         const bool ok = ys >= 0 && ys < H;
-        for (int q = tid; q < 16 * gb; q += kTcThreads) {
-            const int k = q % 16, g = q / 16;
-            const int xs = wrapx(x0 + k + dxo, W);
+        for (int q = tid; q < kWHaloPix * gb; q += kTcThreads) {
+            const int pix = q % kWHaloPix, g = q / kWHaloPix;
+            const int xs = wrapx(x0 + pix - 1, W);
             const bf16* src = ok ? x + (size_t(bimg * H + ys) * W + xs) * ct_x + ci0 + g * 8 : x;
-            cp_async16_ca(db + g * 256 + (k >> 3) * 128 + (k & 7) * 16, src, ok ? 16u : 0u);
+            cp_async16_ca(db + g * (kWHaloPix * 16) + pix * 16, src, ok ? 16u : 0u);
         }
     };
 
@@ -496,8 +511,12 @@ __global__ void __launch_bounds__(kTcThreads) wgrad_tc_kernel(const bf16* __rest
         if (tid == 0) {
             tc_fence_after();
             const uint64_t da = smem_desc(smem_u32(sa + s * kABytes), 128, 256);
-            const uint64_t db = smem_desc(smem_u32(sb + s * kBBytes), 128, 256);
-            mma_bf16(tmem, da, db, idesc, it > 0 ? 1u : 0u);
+            const uint32_t b0 = smem_u32(sb + s * kBBytes);
+#pragma unroll 1
+            for (int dx = 0; dx < 3; ++dx) {
+                const uint64_t db = smem_desc(b0 + dx * 16, 128, kWHaloPix * 16);
+                mma_bf16(tmem + dx * NT, da, db, idesc, it > 0 ? 1u : 0u);
+            }
             mma_commit(&bars[s]);
         }
         const int nxt = it + kStages - 1;
@@ -513,18 +532,22 @@ __global__ void __launch_bounds__(kTcThreads) wgrad_tc_kernel(const bf16* __rest
 
     const int m = warp * 32 + lane;  // output channel co0 + m
 #pragma unroll 1
-    for (int n0 = 0; n0 < NT; n0 += 16) {
-        float v[16];
-        tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + n0, v);
-        if (m < co_here) {
+    for (int dx = 0; dx < 3; ++dx) {
+        const int tap = trow * 3 + dx;
+#pragma unroll 1
+        for (int n0 = 0; n0 < NT; n0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + dx * NT + n0, v);
+            if (m < co_here) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-                if (n0 + j < ci_here) atomicAdd(&dw[(size_t(co0 + m) * ci + ci0 + n0 + j) * 9 + tap], v[j]);
+                for (int j = 0; j < 16; ++j)
+                    if (n0 + j < ci_here) atomicAdd(&dw[(size_t(co0 + m) * ci + ci0 + n0 + j) * 9 + tap], v[j]);
+            }
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, tmem_cols(NT));
+    if (warp == 0) tmem_dealloc(tmem, kCols);
 }
 
 // ------------------------------------------------------------------ SIMT kernels (NHWC)
@@ -861,25 +884,25 @@ int launch_conv(const void* x, int ct_in, int kc, const void* wt, const float* b
 }
 
 template <int NT>
-int launch_wgrad(const void* x, int ct_x, int ci, const void* dy, int ct_dy, int co, float* dw, int n, int h, int wd,
-                 cudaStream_t st)
+int launch_wgrad_taps(const void* x, int ct_x, int ci, const void* dy, int ct_dy, int co, float* dw, int n, int h,
+                      int wd, cudaStream_t st)
 {
-    constexpr int needed = kStages * (128 * 32 + NT * 32) + kStages * 8 + 16;
-    const int smem = smem_for_tmem(int(tmem_cols(NT)), needed);
-    auto k = wgrad_tc_kernel<NT>;
+    constexpr int needed = kStages * (128 * 32 + (NT / 8) * kWHaloPix * 16) + kStages * 8 + 16;
+    const int smem = smem_for_tmem(int(tmem_cols(3 * NT)), needed);
+    auto k = wgrad_tc_taps_kernel<NT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return int(e);
     // pixels per CTA: a power of two (whole 16-pixel row pieces) dividing the
-    // total, at most 2048, and small enough that the grid fills every SM about
-    // four times over (at least 64 pixels, four MMAs, per CTA)
+    // total, at most 2048, halved while the grid has fewer than four CTAs per
+    // SM (at least 64 pixels per CTA)
     const long long total = (long long)n * h * wd;
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
-    const long long tiles = 9LL * ((co + 127) / 128) * ((ci + NT - 1) / NT);
+    const long long tiles = 3LL * ((co + 127) / 128) * ((ci + NT - 1) / NT);
     int npix = 2048;
     while (npix > 16 && total % npix) npix >>= 1;
     while (npix > 64 && tiles * (total / npix) < 4LL * (sms > 0 ? sms : 148) && total % (npix / 2) == 0) npix >>= 1;
-    dim3 grid((co + 127) / 128, (ci + NT - 1) / NT, int(9 * (total / npix)));
+    dim3 grid((co + 127) / 128, (ci + NT - 1) / NT, int(3 * (total / npix)));
     k<<<grid, kTcThreads, smem, st>>>((const bf16*)x, ct_x, ci, (const bf16*)dy, ct_dy, co, dw, h, wd, npix,
                                       err_ptr());
     return status(cudaGetLastError());
@@ -939,11 +962,9 @@ int unet_conv3x3_bwd_weight(const void* x, int ct_x, int ci, const void* dy, int
     cudaStream_t st = (cudaStream_t)stream;
     int rc;
     if (ci <= 16)
-        rc = launch_wgrad<16>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
-    else if (ci % 64 == 0)
-        rc = launch_wgrad<64>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
+        rc = launch_wgrad_taps<16>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
     else
-        rc = launch_wgrad<32>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
+        rc = launch_wgrad_taps<32>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
     if (rc || !db) return rc;
     const long long npix = (long long)n * h * wd;
     const int per = 1024;
