@@ -186,12 +186,20 @@ class OracleSample:
 
 
 def cpu_baseline(w, target_s, cores):
-    """Time the FP64 oracle on a crop of the workload (bounded CPU time)."""
+    """Time the FP64 oracle on a crop of the workload (bounded CPU time), on
+    all host cores and, for a fifth of that time, on one core."""
     s = OracleSample(w, cores)
+    used = s.oracle.set_threads(cores)
     steps = s.steps_for(target_s)
     t = s.run(steps)
-    return {"value": s.cx * s.cy * steps / t / 1e6, "unit": "MLUPS", "cores": cores,
-            "kind": "oracle", "sample": s.describe(steps, t)}
+    s.oracle.set_threads(1)
+    steps1 = s.steps_for(0.2 * target_s)
+    t1 = s.run(steps1)
+    s.oracle.set_threads(cores)
+    return {"value": s.cx * s.cy * steps / t / 1e6, "unit": "MLUPS", "cores": used,
+            "kind": "oracle", "sample": s.describe(steps, t),
+            "one_core": {"value": round(s.cx * s.cy * steps1 / t1 / 1e6, 3), "unit": "MLUPS", "cores": 1,
+                         "sample": s.describe(steps1, t1)}}
 
 
 # ----------------------------------------------------------------- arms

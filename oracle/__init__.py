@@ -92,8 +92,9 @@ def _load():
             lib.orc_fields.argtypes = [P, u8, d, d, d, d]
             lib.orc_forces.argtypes = [P, u8, d, d, d, d, d]
             lib.orc_observables.argtypes = [P, u8, d, d]
+            lib.orc_set_threads.argtypes = [ctypes.c_int]
             for fn in (lib.orc_equilibrium, lib.orc_step, lib.orc_fields, lib.orc_forces,
-                       lib.orc_observables):
+                       lib.orc_observables, lib.orc_set_threads):
                 fn.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -123,6 +124,11 @@ def _u8ptr(a: np.ndarray):
 def _check(rc: int, what: str):
     if rc != 0:
         raise RuntimeError(f"oracle {what} failed with code {rc}")
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's OpenMP loops (timing only); returns the count in effect."""
+    return int(_load().orc_set_threads(int(n)))
 
 
 def equilibrium(p: Params, solid, rho, ux, uy) -> np.ndarray:

@@ -44,6 +44,9 @@
  * (-1,0),(0,-1), e5..e8 = (1,1),(-1,1),(-1,-1),(1,-1).
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -351,4 +354,17 @@ int orc_observables(const orc_params *p, const uint8_t *solid, const double *f, 
     }
     free(rho); free(ux); free(uy);
     return rc;
+}
+
+/* Threads of the OpenMP loops (n >= 1); returns the count in effect (1
+ * without OpenMP). Only timing uses it: results do not depend on it. */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
