@@ -170,6 +170,14 @@ lbm_status lbm_get_field(lbm_ctx *ctx, int which, double *out, int on_device);
  * are set. */
 lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps);
 
+/* Self-test of the device-side timeout path (no counterpart in the paper):
+ * one kernel waits, with the step kernel's bounded mbarrier wait (2^18
+ * polls), on an mbarrier phase that nothing completes. The wait gives up and
+ * raises the context's error flag, and the call returns LBM_ETIMEOUT once the
+ * stream has drained (about a second). The flag is cleared when read, so the
+ * context stays usable. Any other status means the timeout path is broken. */
+lbm_status lbm_selftest_timeout(lbm_ctx *ctx);
+
 /* Observables of the current state (Eq. 11 and mass/momentum bookkeeping),
  * computed by an extra read-only pass; synchronises the stream. Returns
  * LBM_ENAN (with *out filled) if any fluid node is non-finite. */

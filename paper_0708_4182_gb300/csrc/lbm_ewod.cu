@@ -337,6 +337,19 @@ __global__ void dev_to_plain_kernel(const float* __restrict__ in, const uint8_t*
     }
 }
 
+// Self-test of the timeout path: thread 0 waits, with the step kernel's
+// bounded mbarrier wait, on a phase of an mbarrier that nothing arrives at;
+// the wait gives up and raises *err.
+__global__ void wait_selftest_kernel(int* err)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        mbar_wait(&bar, 0, err);
+    }
+}
+
 // Mean velocity profile across the channel: out[y] = (1/nx) sum_x u_x(x, y)
 // from a kFields array (solid nodes hold 0), one block per row, FP64 tree sum.
 __global__ void ux_profile_kernel(const double* __restrict__ fields, Geom g, double* __restrict__ out)
@@ -1051,6 +1064,16 @@ static lbm_status read_record(lbm_ctx* c, const lbm_obs* rec, lbm_obs* out)
     if (out->nonfinite > 0) return fail(c, LBM_ENAN, "%lld non-finite fluid nodes at step %lld",
                                         (long long)out->nonfinite, (long long)out->step);
     return LBM_OK;
+}
+
+lbm_status lbm_selftest_timeout(lbm_ctx* c)
+{
+    if (!c) return LBM_EINVAL;
+    wait_selftest_kernel<<<1, 32, 0, c->stream>>>(c->status);
+    lbm_status s = check_launch(c, "self-test kernel launch");
+    if (s) return s;
+    if ((s = check_cuda(c, cudaStreamSynchronize(c->stream), "self-test sync"))) return s;
+    return check_status(c);
 }
 
 lbm_status lbm_observables(lbm_ctx* c, lbm_obs* out)

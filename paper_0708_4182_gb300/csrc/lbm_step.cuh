@@ -60,7 +60,7 @@ constexpr int kHalo = 4;                       // staged halo columns per side
 constexpr int kRowLen = kW + 2 * kHalo;        // floats per staged plane row
 constexpr int kStages = 6;                     // ring depth (rows)
 constexpr int kPartialStride = 8;              // doubles per CTA in the partials array
-constexpr uint32_t kWaitLimit = 1u << 22;      // try_wait rounds before giving up
+constexpr uint32_t kWaitLimit = 1u << 18;      // try_wait rounds before giving up (about 1 s on a GB300)
 
 enum Storage { kF32 = 0, kF32Dev = 1, kF16Dev = 2, kBF16Dev = 3 };
 

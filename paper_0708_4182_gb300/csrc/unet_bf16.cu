@@ -39,7 +39,7 @@ using bf16 = __nv_bfloat16;
 constexpr int kT = 256;                      // threads of the SIMT kernels
 constexpr int kTcThreads = 128;              // threads of the tensor-core kernels (4 warps = 128 TMEM lanes)
 constexpr int kStages = 4;                   // operand ring depth of the tensor-core kernels
-constexpr uint32_t kWaitLimit = 1u << 22;    // try_wait rounds before giving up
+constexpr uint32_t kWaitLimit = 1u << 18;    // try_wait rounds before giving up (about 1 s on a GB300)
 constexpr int kTileRows = 4, kTileCols = 32; // output pixels of one conv CTA (M = 128)
 constexpr int kSmemPerSm = 233472;           // shared memory of one SM (bytes)
 

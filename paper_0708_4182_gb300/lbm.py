@@ -88,6 +88,7 @@ def load():
             "lbm_obs_latest": (ctypes.c_int, [vp, O]),
             "lbm_run_to_steady": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int64, ctypes.c_int64, O]),
             "lbm_time": (ctypes.c_int64, [vp]),
+            "lbm_selftest_timeout": (ctypes.c_int, [vp]),
             "lbm_last_error": (ctypes.c_char_p, [vp]),
             "lbm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "lbm_destroy": (None, [vp]),
@@ -146,6 +147,11 @@ def lbm_get_field(ctx, which: int, out_ptr: int, on_device: bool):
 
 def lbm_step(ctx, nsteps: int):
     _check(ctx, load().lbm_step(ctx, int(nsteps)))
+
+
+def lbm_selftest_timeout(ctx) -> int:
+    """Status of the timeout self-test (LBM_ETIMEOUT when the path works)."""
+    return int(load().lbm_selftest_timeout(ctx))
 
 
 def lbm_observables(ctx, check_finite: bool = True) -> dict:

@@ -376,3 +376,24 @@ def test_full_size_sampled_parity(lbm):
     assert o["nonfinite"] == 0
     assert abs(o["mass"] - m0) <= 1e-6 * m0
     assert lat.obs_latest()["step"] == 0
+
+
+def test_bounded_wait_times_out_and_context_survives(lbm):
+    """The device-side timeout path, without a fault: a kernel waits on an
+    mbarrier phase that nothing completes, gives up after its bounded number
+    of polls, and the host reads LBM_ETIMEOUT; the context then steps on and
+    matches an undisturbed run bitwise."""
+    w = wl.droplet_128x64(0.125)
+    lat = lbm.Lattice(w.nx, w.ny, **w.params)
+    lat.set_geometry(w.mask)
+    lat.set_rho_u(w.rho)
+    lat.step(10)
+    assert lbm.lbm_selftest_timeout(lat.ctx) == lbm.LBM_ETIMEOUT
+    assert "gave up" in lbm.lbm_last_error(lat.ctx)
+    lat.step(40)
+    assert lat.observables()["nonfinite"] == 0
+    ref = lbm.Lattice(w.nx, w.ny, **w.params)
+    ref.set_geometry(w.mask)
+    ref.set_rho_u(w.rho)
+    ref.step(50)
+    assert np.array_equal(lat.populations(), ref.populations())
