@@ -5,7 +5,7 @@ states that the method itself produces (flat-wall channels of varying
 height, electric-force level and fill). Its prediction initialises a batched
 run through LBM_RHO_U_PHYS, and the method runs on to its usual convergence
 criterion (|dQ|/|Q| < 1e-7 per 1000 steps), so the surrogate's error is
-judged by the converged flux: every warm-started channel must reach the
+measured by the converged flux: every warm-started channel must reach the
 cold start's steady flux within 1e-3, in fewer steps than the cold start.
 Rough-wall channels keep their cold start (their steady flux depends on the
 path, through where vapor pockets settle) and must come out exactly as the

@@ -1,4 +1,4 @@
-"""Brute-force pin of one whole oracle step on tiny lattices (SURVEY T0).
+"""Brute-force pin of one whole oracle step on tiny lattices.
 
 An independent restatement of one time step in 50-digit arithmetic (mpmath),
 node by node from the paper's definitions:
