@@ -276,6 +276,29 @@ def test_fused_observables_match_separate_pass(lbm):
     assert o25["mass"] == pytest.approx(o0["mass"], rel=1e-6)
 
 
+@pytest.mark.parametrize("obs_every", [0, 37, 100])
+def test_graph_stepping_equals_single_steps(lbm, obs_every):
+    """lbm_step replays runs of 32 steps as a CUDA graph, stopping the graph
+    windows at fused-observables steps: one call of 523 steps equals 523
+    calls of one step bitwise, at any obs_every, and the latest fused record
+    is that of the last observed step."""
+    w = wl.rough_channel(nx=256, ny=64, amp=6, level=12, seed=2, body_fx=1e-5)
+    runs = []
+    for chunks in ([523], [1] * 523, [5, 64, 33, 421]):
+        lat = lbm.Lattice(w.nx, w.ny, obs_every=obs_every, **w.params)
+        lat.set_geometry(w.mask)
+        lat.set_rho_u(w.rho)
+        for n in chunks:
+            lat.step(n)
+        assert lat.time == 523
+        runs.append((lat.populations(), lat.obs_latest() if obs_every else None))
+    for pops, rec in runs[1:]:
+        assert np.array_equal(pops, runs[0][0])
+        if obs_every:
+            assert rec["step"] == (522 // obs_every) * obs_every
+            assert rec == runs[0][1]
+
+
 def test_device_buffers(lbm):
     import torch
     w = wl.droplet_128x64(0.0625)
