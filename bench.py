@@ -326,7 +326,7 @@ def run_ours(args, rank, world, local_rank):
     return line
 
 
-KERNEL_VERSION = "step-v6"
+KERNEL_VERSION = "step-v7"
 
 
 def run_e2e(args, w, params, lbm, stream, world):

@@ -64,14 +64,15 @@ bool params_valid(const lbm_params* p, const char** why)
     return true;
 }
 
-int ctas_x(int nx) { return (nx + kW - 1) / kW; }
+// CTAs across a domain of nx columns (strips of strip_cols(storage) columns)
+int ctas_x(int nx, int storage) { return (nx + strip_cols(storage) - 1) / strip_cols(storage); }
 
 Layout layout_of(const lbm_params* p)
 {
     Layout L{};
     const int pitch = pitch_of(p->nx);
     L.pops_bytes = size_t(9) * p->ny * pitch * sizeof(float);
-    L.max_ctas = ctas_x(p->nx) * ((p->ny + 3) / 4);
+    L.max_ctas = ctas_x(p->nx, p->storage) * ((p->ny + 3) / 4);
     size_t o = 0;
     L.off_a = o; o = align_up(o + L.pops_bytes, 256);
     L.off_b = o; o = align_up(o + L.pops_bytes, 256);
@@ -87,7 +88,7 @@ Layout layout_of(const lbm_params* p)
     return L;
 }
 
-int auto_tile_rows(int nx, int ny, int sm_count)
+int auto_tile_rows(int nx, int ny, int storage, int sm_count)
 {
     // Segment height. Each CTA re-stages 4 halo rows, so taller segments waste
     // less, but several waves of CTAs (3 per SM) balance the slower seam
@@ -99,7 +100,7 @@ int auto_tile_rows(int nx, int ny, int sm_count)
     // segment pays the pipeline start and halo rows for a few rows.
     const long long slots = 3LL * sm_count;
     int rows = 64;
-    while (rows > 4 && (long long)ctas_x(nx) * ((ny + rows - 1) / rows) < 4 * slots) rows >>= 1;
+    while (rows > 4 && (long long)ctas_x(nx, storage) * ((ny + rows - 1) / rows) < 4 * slots) rows >>= 1;
     const int nseg = (ny + rows - 1) / rows;
     const int even = (ny + nseg - 1) / nseg;
     return even >= 4 ? even : rows;
@@ -856,8 +857,8 @@ lbm_status lbm_create(const lbm_params* p, void* d_workspace, size_t bytes, void
     c->g.ny = p->ny;
     c->g.pitch = pitch_of(p->nx);
     c->g.plane = p->ny * c->g.pitch;
-    c->g.tile_rows = p->tile_rows ? p->tile_rows : auto_tile_rows(p->nx, p->ny, c->sm_count);
-    c->grid = dim3(ctas_x(p->nx), (p->ny + c->g.tile_rows - 1) / c->g.tile_rows);
+    c->g.tile_rows = p->tile_rows ? p->tile_rows : auto_tile_rows(p->nx, p->ny, p->storage, c->sm_count);
+    c->grid = dim3(ctas_x(p->nx, p->storage), (p->ny + c->g.tile_rows - 1) / c->g.tile_rows);
     c->ph = make_phys(*p);
     *out = c;
     return LBM_OK;
@@ -1292,7 +1293,7 @@ bool batch_layout(const lbm_params* p, int count, BatchLayout* L, const char** w
         if (p[i].storage != p[0].storage) { *why = "all domains of a batch share one storage form"; return false; }
         L->off[i] = o;
         o = align_up(o + layout_of(&p[i]).total, 256);
-        L->max_tiles += ctas_x(p[i].nx) * ((p[i].ny + 3) / 4);
+        L->max_tiles += ctas_x(p[i].nx, p[i].storage) * ((p[i].ny + 3) / 4);
     }
     L->off_dom = o; o = align_up(o + count * sizeof(DomainDev), 256);
     L->off_tiles = o; o = align_up(o + size_t(L->max_tiles) * sizeof(int4), 256);
@@ -1334,7 +1335,7 @@ void build_tiles(lbm_batch* b, bool all)
     for (int d : order) {
         const lbm_ctx* c = b->ctx[d];
         const int rows = domain_tile_rows(b, c);
-        const int tx = ctas_x(c->g.nx), ty = (c->g.ny + rows - 1) / rows;
+        const int tx = ctas_x(c->g.nx, c->prm.storage), ty = (c->g.ny + rows - 1) / rows;
         for (int by = 0; by < ty; ++by)
             for (int bx = 0; bx < tx; ++bx) b->h_tiles.push_back(make_int4(d, bx, by, by * tx + bx));
     }
@@ -1484,7 +1485,7 @@ lbm_status batch_observe(lbm_batch* b, const std::vector<unsigned char>& want, l
         const lbm_ctx* c = b->ctx[d];
         const int rows = domain_tile_rows(b, c);
         parts[d] = c->partials;
-        nct[d] = ctas_x(c->g.nx) * ((c->g.ny + rows - 1) / rows);
+        nct[d] = ctas_x(c->g.nx, c->prm.storage) * ((c->g.ny + rows - 1) / rows);
         invnx[d] = 1.0 / c->g.nx;
         steps[d] = c->t;
     }

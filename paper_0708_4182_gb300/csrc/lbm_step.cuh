@@ -12,21 +12,27 @@
 // pattern kSolidBits in every plane; a pull that meets it knows the source
 // node is solid, so no wall mask is read on the hot path.
 //
-// Work decomposition (HBM-bound stencil, no tensor cores):
-//  - a CTA owns a strip of kW columns and a segment of tile_rows rows;
-//  - one producer warp streams every row the segment needs (all 9 planes,
-//    columns x0-4 .. x0+kW+4) into a kStages-deep ring in shared memory:
-//    one cp.async.bulk per plane row (completion counted on the stage's
-//    "full" mbarrier); at the periodic seam and on ragged strips the
-//    16-byte-aligned body goes in bulk and the few remaining columns by
-//    4-byte cp.async that arrive on the same barrier, so the producer never
-//    waits for a load;
-//  - kW/32 consumer warps pull each node's 9 populations out of the ring
-//    (bounce-back values come from the same stage, no dependent loads), form
-//    rho and psi, write psi into a 4-row ring, meet at a named barrier, then
-//    compute the 8-neighbour forces of the previous row, collide and store f*
-//    with coalesced stores; each warp then frees its ring stage on the
-//    stage's "empty" mbarrier;
+// Work decomposition (no tensor cores; the FP32 form is bound by DRAM, the
+// 16-bit forms by instruction issue):
+//  - a CTA owns a strip of columns and a segment of tile_rows rows;
+//  - one producer warp streams every row the segment needs (all 9 planes of
+//    a window a few columns wider than the strip) into a kStages-deep ring in
+//    shared memory with cp.async.bulk copies whose completion is counted on
+//    the stage's "full" mbarrier; pieces that cannot move in 16-byte units
+//    (periodic seam, ragged strips of the FP32 forms) go by 4-byte cp.async
+//    that arrive on the same barrier, so the producer never waits for a load;
+//  - kW/32 consumer warps pull one node's 9 populations per thread out of the
+//    ring (bounce-back values come from the same stage, no dependent loads),
+//    form rho and psi, write psi into a 4-row ring, meet at a named barrier,
+//    then compute the 8-neighbour forces of the previous row, collide and
+//    store f* with coalesced stores; each warp then frees its ring stage on
+//    the stage's "empty" mbarrier. The psi of the strip's two halo columns
+//    comes from an extra pull by the threads at the strip's ends (32-bit
+//    forms) or from two extra threads of overlapping strips (16-bit forms);
+//    see run_tile;
+//  - the pulled state of two consecutive rows lives in two register sets used
+//    in turn, and a node whose 9 pulled values sum to a non-NaN value has no
+//    solid neighbour and skips the per-direction bounce-back checks;
 //  - every mbarrier wait is bounded: on timeout the kernel sets a flag in
 //    global memory, stops waiting and runs to completion, and the host
 //    reports LBM_ETIMEOUT.
@@ -53,32 +59,37 @@
 namespace lbm {
 
 constexpr uint32_t kSolidBits = 0xFFBADA55u;  // a NaN payload arithmetic never produces
-constexpr int kW = 256;                        // interior columns per CTA
+constexpr int kW = 256;                        // consumer threads per CTA (one pulled column each)
 constexpr int kConsumerWarps = kW / 32;
 constexpr int kThreads = kW + 32;              // consumers + one producer warp
-constexpr int kHalo = 4;                       // staged halo columns per side
-constexpr int kRowLen = kW + 2 * kHalo;        // floats per staged plane row
-constexpr int kStages = 6;                     // ring depth (rows)
+constexpr int kRowLen = kW + 8;                // staged columns per plane row (window + alignment)
+constexpr int kPsiStride = kW + 2;             // floats per psi ring row
+constexpr int kStages = 6;                     // staging ring depth (rows)
 constexpr int kPartialStride = 8;              // doubles per CTA in the partials array
 constexpr uint32_t kWaitLimit = 1u << 18;      // try_wait rounds before giving up (about 1 s on a GB300)
 
 enum Storage { kF32 = 0, kF32Dev = 1, kF16Dev = 2, kBF16Dev = 3 };
 
+// T: type of planes 1..8; align: columns per 16 bytes of the narrowest plane
+// (every staging copy starts and ends on such a boundary); overlap: the
+// strip layout (see run_tile), 0 for the 32-bit forms, 1 for the 16-bit ones
 template <int ST> struct StoreT;
-template <> struct StoreT<kF32> { using T = float; static constexpr int halo = 4; };
-template <> struct StoreT<kF32Dev> { using T = float; static constexpr int halo = 4; };
-template <> struct StoreT<kF16Dev> { using T = __half; static constexpr int halo = 8; };
-template <> struct StoreT<kBF16Dev> { using T = __nv_bfloat16; static constexpr int halo = 8; };
+template <> struct StoreT<kF32> { using T = float; static constexpr int align = 4, overlap = 0; };
+template <> struct StoreT<kF32Dev> { using T = float; static constexpr int align = 4, overlap = 0; };
+template <> struct StoreT<kF16Dev> { using T = __half; static constexpr int align = 8, overlap = 1; };
+template <> struct StoreT<kBF16Dev> { using T = __nv_bfloat16; static constexpr int align = 8, overlap = 1; };
 
-// staged row: plane 0 (FP32, row_len floats) then planes 1..8 (type T)
-template <int ST> __host__ __device__ constexpr int row_len() { return kW + 2 * StoreT<ST>::halo; }
+// Columns a CTA collides: kW, or kW - 2 where neighbouring strips overlap.
+__host__ __device__ constexpr int strip_cols(int st) { return (st == kF16Dev || st == kBF16Dev) ? kW - 2 : kW; }
+
+// staged row: plane 0 (FP32, kRowLen floats) then planes 1..8 (type T)
 template <int ST> __host__ __device__ constexpr size_t stage_bytes()
 {
-    return size_t(row_len<ST>()) * (sizeof(float) + 8 * sizeof(typename StoreT<ST>::T));
+    return size_t(kRowLen) * (sizeof(float) + 8 * sizeof(typename StoreT<ST>::T));
 }
 template <int ST> __host__ __device__ constexpr size_t smem_bytes()
 {
-    return kStages * stage_bytes<ST>() + 4 * (kW + 2) * sizeof(float) + 2 * kStages * sizeof(uint64_t) + 128;
+    return kStages * (stage_bytes<ST>() + 2 * sizeof(uint64_t)) + 4 * kPsiStride * sizeof(float) + 128;
 }
 // bytes of one node's state in global memory (plane 0 + planes 1..8)
 template <int ST> __host__ __device__ constexpr int node_bytes() { return 4 + 8 * int(sizeof(typename StoreT<ST>::T)); }
@@ -220,6 +231,7 @@ __device__ __forceinline__ float div_corrected(float n, float d, float r)
     return fmaf(e, r, q0);
 }
 
+// The consumer warps (once per staged row, and the observables reduction).
 __device__ __forceinline__ void consumer_sync()
 {
     asm volatile("bar.sync 1, %0;" ::"n"(kW) : "memory");
@@ -252,18 +264,26 @@ __device__ __forceinline__ void pull_smem(const float* __restrict__ sm, const fl
     v[7] = sp[7 * R + c + 1];  // e7 = (-1,-1): source (x+1, y+1)
     v[8] = sp[8 * R + c - 1];  // e8 = ( 1,-1): source (x-1, y+1)
     constexpr int opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+    auto density = [&v]() { return ((v[0] + (v[1] + v[3])) + (v[2] + v[4])) + ((v[5] + v[7]) + (v[6] + v[8])); };
     uint32_t sb = 0;
+    float rho = density();
+    // a solid source holds a NaN sentinel, so a sum that is not NaN has no
+    // solid source; only a NaN sum (a wall nearby, or a state gone
+    // non-finite) takes the per-direction checks
+    if (isnan(rho)) {
 #pragma unroll
-    for (int a = 1; a < 9; ++a) {
-        if (is_solid(v[a])) {
-            sb |= 1u << a;
-            v[a] = sc[opp[a] * R + c];  // half-way bounce-back
+        for (int a = 1; a < 9; ++a) {
+            if (is_solid(v[a])) {
+                sb |= 1u << a;
+                v[a] = sc[opp[a] * R + c];  // half-way bounce-back
+            }
         }
+        rho = density();
     }
 #pragma unroll
     for (int a = 0; a < 9; ++a) n.f[a] = v[a];
     n.sb = sb;
-    n.rho = ((v[0] + (v[1] + v[3])) + (v[2] + v[4])) + ((v[5] + v[7]) + (v[6] + v[8]));
+    n.rho = rho;
     n.jx = (v[1] - v[3]) + (v[5] - v[7]) + (v[8] - v[6]);
     n.jy = (v[2] - v[4]) + (v[5] - v[7]) + (v[6] - v[8]);
 }
@@ -432,16 +452,34 @@ struct PulledDev {
     bool solid;
 };
 
+// Stored deviations in raw units: FP16 planes hold d_a * kF16Scale, the
+// other forms d_a itself. The deviation arithmetic below runs on raw values
+// and applies the power-of-two factor kUnscale<T> once per sum; a
+// power-of-two scaling commutes with FP32 rounding (no value here comes near
+// FP32's range limits), so the results equal those of the unscaled sums bit
+// for bit.
+__device__ __forceinline__ float to_raw(float v) { return v; }
+__device__ __forceinline__ float to_raw(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_raw(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <typename T> __device__ __forceinline__ T from_raw(float v);
+template <> __device__ __forceinline__ float from_raw<float>(float v) { return v; }
+template <> __device__ __forceinline__ __half from_raw<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_raw<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <typename T> struct RawScale { static constexpr float scale = 1.f, unscale = 1.f; };
+template <> struct RawScale<__half> { static constexpr float scale = kF16Scale, unscale = kF16Unscale; };
+
 // Pull in deviation form: s0* are plane-0 rows (rho*) r-1, r, r+1; sd* the
 // same rows' deviation planes 1..8 (plane a at (a-1)*R); c the node column.
 // f_a(x) = w_a rho*(x - e_a) + d_a(x - e_a), or, if x - e_a is solid,
 // f*_opp(a)(x) = w_a rho*(x) + d_opp(a)(x); f_0 = w_0 rho*(x) - sum_b d_b(x).
+// n.g (tau != 1 only) is in raw units.
 template <typename T, int R>
 __device__ __forceinline__ void pull_dev(const float* __restrict__ s0m, const float* __restrict__ s0c,
                                          const float* __restrict__ s0p, const T* __restrict__ sdm,
                                          const T* __restrict__ sdc, const T* __restrict__ sdp, int c,
                                          bool need_g, PulledDev& n)
 {
+    constexpr float U = RawScale<T>::unscale, S = RawScale<T>::scale;
     const float r0 = s0c[c];
     n.solid = is_solid(r0);
     if (n.solid) {
@@ -450,50 +488,59 @@ __device__ __forceinline__ void pull_dev(const float* __restrict__ s0m, const fl
         return;
     }
     float rs[9], d[9], own[9];
-    rs[1] = s0c[c - 1];  d[1] = to_f(sdc[0 * R + c - 1]);  // e1: source (x-1, y)
-    rs[2] = s0m[c];      d[2] = to_f(sdm[1 * R + c]);      // e2: source (x, y-1)
-    rs[3] = s0c[c + 1];  d[3] = to_f(sdc[2 * R + c + 1]);  // e3: source (x+1, y)
-    rs[4] = s0p[c];      d[4] = to_f(sdp[3 * R + c]);      // e4: source (x, y+1)
-    rs[5] = s0m[c - 1];  d[5] = to_f(sdm[4 * R + c - 1]);  // e5: source (x-1, y-1)
-    rs[6] = s0m[c + 1];  d[6] = to_f(sdm[5 * R + c + 1]);  // e6: source (x+1, y-1)
-    rs[7] = s0p[c + 1];  d[7] = to_f(sdp[6 * R + c + 1]);  // e7: source (x+1, y+1)
-    rs[8] = s0p[c - 1];  d[8] = to_f(sdp[7 * R + c - 1]);  // e8: source (x-1, y+1)
+    rs[1] = s0c[c - 1];  d[1] = to_raw(sdc[0 * R + c - 1]);  // e1: source (x-1, y)
+    rs[2] = s0m[c];      d[2] = to_raw(sdm[1 * R + c]);      // e2: source (x, y-1)
+    rs[3] = s0c[c + 1];  d[3] = to_raw(sdc[2 * R + c + 1]);  // e3: source (x+1, y)
+    rs[4] = s0p[c];      d[4] = to_raw(sdp[3 * R + c]);      // e4: source (x, y+1)
+    rs[5] = s0m[c - 1];  d[5] = to_raw(sdm[4 * R + c - 1]);  // e5: source (x-1, y-1)
+    rs[6] = s0m[c + 1];  d[6] = to_raw(sdm[5 * R + c + 1]);  // e6: source (x+1, y-1)
+    rs[7] = s0p[c + 1];  d[7] = to_raw(sdp[6 * R + c + 1]);  // e7: source (x+1, y+1)
+    rs[8] = s0p[c - 1];  d[8] = to_raw(sdp[7 * R + c - 1]);  // e8: source (x-1, y+1)
 #pragma unroll
-    for (int b = 1; b < 9; ++b) own[b] = to_f(sdc[(b - 1) * R + c]);
+    for (int b = 1; b < 9; ++b) own[b] = to_raw(sdc[(b - 1) * R + c]);
     constexpr int opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+    auto qsum = [&rs, r0](float& q1, float& q2) {
+        q1 = ((rs[1] - r0) + (rs[3] - r0)) + ((rs[2] - r0) + (rs[4] - r0));
+        q2 = ((rs[5] - r0) + (rs[7] - r0)) + ((rs[6] - r0) + (rs[8] - r0));
+    };
     uint32_t sb = 0;
+    float q1, q2;
+    qsum(q1, q2);
+    // a solid source holds a NaN sentinel in plane 0: only a NaN sum (a
+    // wall nearby, or a state gone non-finite) takes the per-direction checks
+    if (isnan(q1 + q2)) {
 #pragma unroll
-    for (int a = 1; a < 9; ++a) {
-        if (is_solid(rs[a])) {  // half-way bounce-back: the node's own f*_opp(a)
-            sb |= 1u << a;
-            rs[a] = r0;
-            d[a] = own[opp[a]];
+        for (int a = 1; a < 9; ++a) {
+            if (is_solid(rs[a])) {  // half-way bounce-back: the node's own f*_opp(a)
+                sb |= 1u << a;
+                rs[a] = r0;
+                d[a] = own[opp[a]];
+            }
         }
+        qsum(q1, q2);
     }
     constexpr float w1 = 1.f / 9.f, w2 = 1.f / 36.f;
     // rho - rho*(x) = sum_a w_a (rho*_src - rho*(x)) + sum_a d_a(src) - sum_b d_b(x)
-    const float q1 = ((rs[1] - r0) + (rs[3] - r0)) + ((rs[2] - r0) + (rs[4] - r0));
-    const float q2 = ((rs[5] - r0) + (rs[7] - r0)) + ((rs[6] - r0) + (rs[8] - r0));
     const float dsrc = ((d[1] + d[3]) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8]));
     const float down = ((own[1] + own[3]) + (own[2] + own[4])) + ((own[5] + own[7]) + (own[6] + own[8]));
-    const float drho = fmaf(w1, q1, fmaf(w2, q2, dsrc - down));
+    const float drho = fmaf(w1, q1, fmaf(w2, q2, (dsrc - down) * U));
     const float rho = r0 + drho;
     n.rho = rho;
     n.jx = fmaf(w1, rs[1] - rs[3], fmaf(w2, (rs[5] - rs[7]) + (rs[8] - rs[6]),
-                                        (d[1] - d[3]) + (d[5] - d[7]) + (d[8] - d[6])));
+                                        ((d[1] - d[3]) + (d[5] - d[7]) + (d[8] - d[6])) * U));
     n.jy = fmaf(w1, rs[2] - rs[4], fmaf(w2, (rs[5] - rs[7]) + (rs[6] - rs[8]),
-                                        (d[2] - d[4]) + (d[5] - d[7]) + (d[6] - d[8])));
-    // g_a = f_a - w_a rho = w_a ((rho*_src - rho*(x)) - drho) + d_a(src);
-    // only the relaxation with tau != 1 reads it
+                                        ((d[2] - d[4]) + (d[5] - d[7]) + (d[6] - d[8])) * U));
+    // g_a = f_a - w_a rho = w_a ((rho*_src - rho*(x)) - drho) + d_a(src), in
+    // raw units; only the relaxation with tau != 1 reads it
     if (need_g) {
 #pragma unroll
-        for (int a = 1; a < 9; ++a) n.g[a] = fmaf(a <= 4 ? w1 : w2, (rs[a] - r0) - drho, d[a]);
+        for (int a = 1; a < 9; ++a) n.g[a] = fmaf((a <= 4 ? w1 : w2) * S, (rs[a] - r0) - drho, d[a]);
     }
     n.g[0] = 0.f;
     n.sb = sb;
 }
 
-// Collision in deviation form: stores rho in plane 0 and
+// Collision in deviation form: stores rho in plane 0 and the raw
 // d*_a = f*_a - w_a rho in planes 1..8 (the equilibrium's deviation part
 // w_a rho (3 c + 4.5 c^2 - 1.5 u^2) is formed without its leading 1).
 template <int MODE, typename T>
@@ -510,7 +557,7 @@ __device__ __forceinline__ void collide_dev(const PulledDev& n, const float* pm,
         const float uy = div_corrected(fmaf(p.tau, Fy, n.jy), n.rho, rinv);
         const float usq = 1.5f * fmaf(ux, ux, uy * uy);
         const float r9 = div_corrected(n.rho, 9.f, 1.f / 9.f);
-        const float w1r = r9, w2r = 0.25f * r9;
+        const float w1r = r9 * RawScale<T>::scale, w2r = 0.25f * w1r;
         const float d5 = ux + uy, d6 = uy - ux;
         auto dpoly = [usq](float c) { return fmaf(c, fmaf(4.5f, c, 3.f), -usq); };
         float dq[9];
@@ -526,11 +573,11 @@ __device__ __forceinline__ void collide_dev(const PulledDev& n, const float* pm,
         fout0[o] = n.rho;
         if (p.tau == 1.f) {
 #pragma unroll
-            for (int a = 1; a < 9; ++a) foutd[(a - 1) * g.plane + o] = from_f<T>(dq[a]);
+            for (int a = 1; a < 9; ++a) foutd[(a - 1) * g.plane + o] = from_raw<T>(dq[a]);
         } else {
 #pragma unroll
             for (int a = 1; a < 9; ++a)
-                foutd[(a - 1) * g.plane + o] = from_f<T>(fmaf(dq[a] - n.g[a], p.inv_tau, n.g[a]));
+                foutd[(a - 1) * g.plane + o] = from_raw<T>(fmaf(dq[a] - n.g[a], p.inv_tau, n.g[a]));
         }
     }
     if constexpr (MODE != kStep) node_observe<MODE>(n.rho, rinv, n.jx, n.jy, Fx, Fy, g, fields, x, r, acc);
@@ -543,9 +590,23 @@ __device__ __forceinline__ void mbar_inval(uint64_t* bar)
     asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// One CTA's work: the strip of columns [bx*kW, bx*kW + kW) and the segment
-// of rows [by*tile_rows, (by+1)*tile_rows) of one domain; per-CTA
-// observables go to partials[slot]. smem_raw is the dynamic shared memory.
+// One CTA's work: a strip of columns of one domain and the segment of rows
+// [by*tile_rows, (by+1)*tile_rows); per-CTA observables go to
+// partials[slot]. smem_raw is the dynamic shared memory.
+//
+// Consumer thread t pulls node column x0 - P + t and writes its psi into
+// column t + 1 - P of the psi ring, whose columns 0 .. nint + 1 hold the
+// strip's columns x0 - 1 .. x0 + nint. Two layouts (P = StoreT<ST>::overlap):
+//  - P = 0 (32-bit forms, bound by DRAM): strips of kW columns at
+//    x0 = bx*kW. Thread t pulls and collides column x0 + t; threads 0 and
+//    nint - 1 also pull the halo columns x0 - 1 and x0 + nint. Warp stores
+//    cover whole 128-byte lines.
+//  - P = 1 (16-bit forms, bound by instruction issue): strips of kW - 2
+//    columns at x0 = bx*(kW-2). Thread t pulls column x0 - 1 + t, so the
+//    halo columns come from threads 0 and nint + 1 like every other column
+//    and all consumer warps do the same work; threads 1 .. nint collide.
+//    Neighbouring strips overlap by two pulled columns.
+// In both the producer warp only stages rows, running ahead of the consumers.
 template <int MODE, int ST>
 __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* __restrict__ fout, const Geom& g,
                                          const Phys& p, double* __restrict__ partials,
@@ -553,24 +614,34 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
                                          int slot, unsigned char* smem_raw)
 {
     using T = typename StoreT<ST>::T;
-    constexpr int H = StoreT<ST>::halo;  // staged halo columns per side
-    constexpr int R = row_len<ST>();     // staged columns per plane row
+    constexpr int A = StoreT<ST>::align;
+    constexpr int P = StoreT<ST>::overlap;
+    constexpr int R = kRowLen;
     constexpr size_t SB = stage_bytes<ST>();
     // ring stage s: plane 0 (FP32, R) then planes 1..8 (T, R each)
-    float* psi_ring = reinterpret_cast<float*>(smem_raw + kStages * SB);    // [4][kW + 2]
-    uint64_t* full = reinterpret_cast<uint64_t*>(psi_ring + 4 * (kW + 2));  // [kStages]
-    uint64_t* empty = full + kStages;                                       // [kStages]
-    auto stage0 = [&](int s) { return reinterpret_cast<float*>(smem_raw + size_t(s) * SB); };
-    auto staged = [&](int s) { return reinterpret_cast<T*>(smem_raw + size_t(s) * SB + R * sizeof(float)); };
+    float* psi_ring = reinterpret_cast<float*>(smem_raw + kStages * SB);      // [4][kPsiStride]
+    uint64_t* full = reinterpret_cast<uint64_t*>(psi_ring + 4 * kPsiStride);  // [kStages]
+    uint64_t* empty = full + kStages;                                         // [kStages]
+    auto stage_ptr = [&](int s) { return smem_raw + size_t(s) * SB; };
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int x0 = bx * kW;
-    const int nint = min(kW, g.nx - x0);     // interior columns of this strip
-    const int nbody = nint & ~3;             // columns moved by the bulk copies
+    const int x0 = bx * strip_cols(ST);
+    const int nint = min(strip_cols(ST), g.nx - x0);  // columns collided: x0 .. x0 + nint - 1
     const int y0 = by * g.tile_rows;
     const int y1 = min(y0 + g.tile_rows, g.ny);
-    const int nrows = (y1 - y0) + 4;         // staged rows y0-2 .. y1+1
+    const int nrows = (y1 - y0) + 4;                  // staged rows y0-2 .. y1+1
+    // Staged window: global columns ws .. ws + L - 1 (periodic in x), with ws
+    // the multiple of A at or below x0 - P - 1 and L a multiple of A, so that
+    // the pulls of columns x0 - P .. x0 - P + kW - 1 (which read one column
+    // more on each side) find their sources; node column x sits at staged
+    // column x - ws, so thread t's node at t + 1 + o with o = x0 - P - 1 - ws.
+    // P = 0: x0 is a multiple of kW, so o = A - 1 for every strip (a
+    // compile-time offset). P = 1: x0 - 2 >= -2 is even and o <= A - 2.
+    // L = kW + 2 + o rounded up to A <= kRowLen.
+    const int o = P == 0 ? A - 1 : (x0 >= 2 ? (x0 - 2) % A : A - 2);
+    const int ws = x0 - P - 1 - o;
+    const int L = ((kW + 2 + o) + A - 1) / A * A;
 
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -592,21 +663,44 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
         return x < 0 ? x + g.nx : x;
     };
 
+    using PT = std::conditional_t<ST == kF32, Pulled, PulledDev>;
+    // pull the node in staged column col of the row held by stage bc, whose
+    // neighbour rows are in stages bm (row - 1) and bp (row + 1)
+    auto pull = [&](const unsigned char* bm, const unsigned char* bc, const unsigned char* bp, int col, PT& n) {
+        const float* s0m = reinterpret_cast<const float*>(bm);
+        const float* s0c = reinterpret_cast<const float*>(bc);
+        const float* s0p = reinterpret_cast<const float*>(bp);
+        if constexpr (ST == kF32) {
+            pull_smem(s0m, s0c, s0p, col, n);
+        } else {
+            const T* sdm = reinterpret_cast<const T*>(bm + R * sizeof(float));
+            const T* sdc = reinterpret_cast<const T*>(bc + R * sizeof(float));
+            const T* sdp = reinterpret_cast<const T*>(bp + R * sizeof(float));
+            pull_dev<T, R>(s0m, s0c, s0p, sdm, sdc, sdp, col, p.tau != 1.f, n);
+        }
+    };
+    float* psi_w = psi_ring;
+
     if (warp == kConsumerWarps) {
         // ---------------- producer warp: fill ring stages with rows y0-2 .. y1+1
         bool ok = true;
-        if constexpr (sizeof(T) == 4) {
-            // FP32 planes. Interior strips (halos inside [0, nx) and a 16-byte
-            // multiple wide) take one bulk copy per plane row covering columns
-            // x0-4 .. x0+nint+4. Edge and ragged strips copy the aligned body in
-            // bulk and fetch the remaining <= 11 columns per plane with 4-byte
-            // cp.async; each lane's column is fixed for the whole segment.
+        // Staged row k goes to stage k % kStages.
+        if constexpr (P == 0) {
+            // 32-bit planes, strips at multiples of kW. Interior strips (the
+            // window x0-4 .. x0+nint+4 inside [0, nx) and a 16-byte multiple
+            // wide) take one bulk copy per plane row; edge and ragged strips
+            // copy the aligned body in bulk and fetch the remaining <= 11
+            // columns per plane with 4-byte cp.async (each lane's column is
+            // fixed for the whole segment). The producer runs ahead on its
+            // own, refilling each stage as soon as the consumers free it.
+            constexpr int H = A;                                 // staged columns left of x0 (o = H - 1)
+            const int nbody = nint & ~3;                         // columns moved by the bulk copies
             const bool whole = (x0 >= H) && (x0 + nint + H <= g.nx) && ((nint & 3) == 0);
-            const int b_col = whole ? -H : 0;                   // first bulk column (rel. x0)
-            const int b_len = whole ? nint + 2 * H : nbody;     // bulk columns
+            const int b_col = whole ? -H : 0;                    // first bulk column (rel. x0)
+            const int b_len = whole ? nint + 2 * H : nbody;      // bulk columns
             const uint32_t b_bytes = uint32_t(b_len) * sizeof(float);
-            const int n_right = nint + H - nbody;               // columns [x0+nbody, x0+nint+4)
-            const int n_scalar = whole ? 0 : H + n_right;       // <= 11
+            const int n_right = nint + H - nbody;                // columns [x0+nbody, x0+nint+4)
+            const int n_scalar = whole ? 0 : H + n_right;        // <= 11
             int my_sc = 0, my_gx = 0;
             const bool has_scalar = lane < n_scalar;
             if (has_scalar) {
@@ -614,11 +708,10 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
                 my_sc = H + col;
                 my_gx = wrap_x(x0 + col);
             }
-            for (int k = 0; k < nrows; ++k) {
+            auto fill = [&](int k) {
                 const int s = k % kStages;
-                if (k >= kStages) ok = mbar_wait(&empty[s], ((k / kStages) - 1) & 1, err) && ok;
                 const int row = wrap_y(y0 - 2 + k);
-                float* st = stage0(s);
+                float* st = reinterpret_cast<float*>(stage_ptr(s));
                 const float* src = fin + size_t(row) * g.pitch;
                 if (lane == 0 && b_len > 0) {
                     mbar_expect_tx(&full[s], 9 * b_bytes);
@@ -632,47 +725,59 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
                     for (int a = 0; a < 9; ++a) async_g2s_4(st + a * R + my_sc, src + size_t(a) * g.plane + my_gx);
                 }
                 async_arrive_noinc(&full[s]);
+            };
+            for (int k = 0; k < nrows; ++k) {
+                if (k >= kStages) ok = mbar_wait(&empty[k % kStages], ((k / kStages) - 1) & 1, err) && ok;
+                fill(k);
             }
         } else {
-            // 16-bit deviation planes (nx % 8 == 0, so every piece below starts
-            // and ends on a 16-byte boundary): one bulk copy per plane row for
-            // interior strips, else body + left halo + right halo (wrapped).
-            const bool whole = (x0 >= H) && (x0 + nint + H <= g.nx);
-            const uint32_t row_elems = uint32_t(nint + 2 * H);
-            const uint32_t tx = row_elems * uint32_t(sizeof(float) + 8 * sizeof(T));
-            const int xl = wrap_x(x0 - H), xr = wrap_x(x0 + nint);
+            // 16-bit deviation planes (nx % 8 == 0): the window splits at the
+            // periodic seam into pieces that start and end on 16-byte
+            // boundaries, the same for every row; lane l moves pieces l,
+            // l + 32, ... with one cp.async.bulk per plane. The producer runs
+            // ahead on its own, as above.
+            const uint32_t tx = uint32_t(L) * uint32_t(sizeof(float) + 8 * sizeof(T));
             const T* dbase = reinterpret_cast<const T*>(fin + g.plane);
-            for (int k = 0; k < nrows; ++k) {
+            // piece q covers window positions [max(ws, (m0+q) nx), min(ws+L, (m0+q+1) nx))
+            const int m0 = ws >= 0 ? ws / g.nx : -((-ws + g.nx - 1) / g.nx);
+            const int npieces = (ws + L - 1 - m0 * g.nx) / g.nx + 1;
+            auto piece = [&](int q, int& j, int& gx, int& len) {
+                const int base = (m0 + q) * g.nx;
+                const int start = max(ws, base), end = min(ws + L, base + g.nx);
+                j = start - ws;
+                gx = start - base;
+                len = end - start;
+            };
+            int pj = 0, pgx = 0, plen = 0;  // this lane's first piece
+            if (lane < npieces) piece(lane, pj, pgx, plen);
+            auto copy_piece = [&](float* s0, int row, int j, int gx, int len, uint64_t* bar) {
+                T* sd = reinterpret_cast<T*>(s0 + R);
+                const float* g0 = fin + size_t(row) * g.pitch;
+                const T* gd = dbase + size_t(row) * g.pitch;
+                bulk_g2s(s0 + j, g0 + gx, uint32_t(len) * 4u, bar);
+#pragma unroll 1
+                for (int a = 1; a < 9; ++a)
+                    bulk_g2s(sd + (a - 1) * R + j, gd + size_t(a - 1) * g.plane + gx,
+                             uint32_t(len) * uint32_t(sizeof(T)), bar);
+            };
+            auto fill = [&](int k) {
                 const int s = k % kStages;
-                if (k >= kStages) ok = mbar_wait(&empty[s], ((k / kStages) - 1) & 1, err) && ok;
-                const int row = wrap_y(y0 - 2 + k);
-                if (lane == 0) {
-                    mbar_expect_tx(&full[s], tx);
-                    float* s0 = stage0(s);
-                    T* sd = staged(s);
-                    const float* g0 = fin + size_t(row) * g.pitch;
-                    const T* gd = dbase + size_t(row) * g.pitch;
-                    if (whole) {
-                        bulk_g2s(s0, g0 + x0 - H, row_elems * sizeof(float), &full[s]);
-#pragma unroll 1
-                        for (int a = 1; a < 9; ++a)
-                            bulk_g2s(sd + (a - 1) * R, gd + size_t(a - 1) * g.plane + x0 - H,
-                                     row_elems * sizeof(T), &full[s]);
-                    } else {
-                        bulk_g2s(s0 + H, g0 + x0, nint * sizeof(float), &full[s]);
-                        bulk_g2s(s0, g0 + xl, H * sizeof(float), &full[s]);
-                        bulk_g2s(s0 + H + nint, g0 + xr, H * sizeof(float), &full[s]);
-#pragma unroll 1
-                        for (int a = 1; a < 9; ++a) {
-                            const T* pl = gd + size_t(a - 1) * g.plane;
-                            T* dl = sd + (a - 1) * R;
-                            bulk_g2s(dl + H, pl + x0, nint * sizeof(T), &full[s]);
-                            bulk_g2s(dl, pl + xl, H * sizeof(T), &full[s]);
-                            bulk_g2s(dl + H + nint, pl + xr, H * sizeof(T), &full[s]);
-                        }
-                    }
+                int row = y0 - 2 + k;
+                if (row < 0 || row >= g.ny) row = wrap_y(row);
+                float* s0 = reinterpret_cast<float*>(stage_ptr(s));
+                if (lane == 0) mbar_expect_tx(&full[s], tx);
+                __syncwarp();
+                if (lane < npieces) copy_piece(s0, row, pj, pgx, plen, &full[s]);
+                for (int q = lane + 32; q < npieces; q += 32) {  // windows wider than 31 domain widths
+                    int j, gx, len;
+                    piece(q, j, gx, len);
+                    copy_piece(s0, row, j, gx, len, &full[s]);
                 }
                 async_arrive_noinc(&full[s]);
+            };
+            for (int k = 0; k < nrows; ++k) {
+                if (k >= kStages) ok = mbar_wait(&empty[k % kStages], ((k / kStages) - 1) & 1, err) && ok;
+                fill(k);
             }
         }
         // drain: every armed fill has been waited on by the consumers in the
@@ -687,62 +792,63 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
     }
 
     // ---------------- consumer warps
-    using PT = std::conditional_t<ST == kF32, Pulled, PulledDev>;
-    const int t = tid;                  // column x0 + t
-    const bool interior = t < nint;
-    const int c = t + H;                // staged column of this node
-    const int x = x0 + t;
-    float* psi_w = psi_ring;            // ring row stride kW + 2, column t + 1
+    const int t = tid;
+    const bool active = t < nint + 2 * P;           // pulls node column x0 - P + t
+    const bool interior = t >= P && t < P + nint;   // and collides it
+    const int c = t + 1 + o;                        // its staged column
+    const int x = x0 - P + t;
+    const int tr = t + 1 - P;                       // its psi ring column
     ObsAcc acc;
-    PT cur, nxt;
     bool ok = true;
     // prologue: the two oldest staged rows (y0-2, y0-1) must be present
+    // (a segment stages at least 5 rows)
     ok = mbar_wait(&full[0], 0, err) && ok;
-    if (nrows > 1) ok = mbar_wait(&full[1 % kStages], (1 / kStages) & 1, err) && ok;
+    ok = mbar_wait(&full[1], 0, err) && ok;
 
-    auto pull = [&](int sm, int sc, int sp, int col, PT& n) {
-        if constexpr (ST == kF32)
-            pull_smem(stage0(sm), stage0(sc), stage0(sp), col, n);
-        else
-            pull_dev<T, R>(stage0(sm), stage0(sc), stage0(sp), staged(sm), staged(sc), staged(sp), col,
-                           p.tau != 1.f, n);
-    };
+    // ring position of staged rows k-1, k, k+1 (stage indices and bases) and
+    // the fill parity of row k+1; advanced by one row per body() call
+    int s_m = 0, s_p = 2;
+    uint32_t ph_p = 0;
+    const unsigned char* b_m = stage_ptr(0);
+    const unsigned char* b_c = stage_ptr(1);
+    const unsigned char* b_p = stage_ptr(2);
 
-    for (int k = 1; k <= nrows - 2; ++k) {
-        // pull row r = y0 - 2 + k, which needs staged rows k-1, k, k+1
+    // Row k: pull row r = y0 - 2 + k (staged rows k-1, k, k+1) into `into`,
+    // then collide row r - 1, pulled at row k - 1 into `prev`.
+    auto body = [&](int k, PT& into, const PT& prev) {
         const int r = y0 - 2 + k;
-        const int kn = k + 1;
-        ok = mbar_wait(&full[kn % kStages], (kn / kStages) & 1, err) && ok;
-        const int sm = (k - 1) % kStages, sc = k % kStages, sp = kn % kStages;
-        float* prow = psi_w + ((r + 4) & 3) * (kW + 2);
-        if (interior) {
-            pull(sm, sc, sp, c, nxt);
-            prow[t + 1] = pseudopotential(p, nxt);
-            if (t == 0) {  // left halo column x0 - 1
-                PT h;
-                pull(sm, sc, sp, c - 1, h);
-                prow[0] = pseudopotential(p, h);
-            }
-            if (t == nint - 1) {  // right halo column x0 + nint
-                PT h;
-                pull(sm, sc, sp, c + 1, h);
-                prow[nint + 1] = pseudopotential(p, h);
+        ok = mbar_wait(&full[s_p], ph_p, err) && ok;
+        if (active) {
+            pull(b_m, b_c, b_p, c, into);
+            float* prow = psi_w + ((r + 4) & 3) * kPsiStride;
+            prow[tr] = pseudopotential(p, into);
+            if constexpr (P == 0) {
+                if (t == 0) {  // left halo column x0 - 1
+                    PT h;
+                    pull(b_m, b_c, b_p, c - 1, h);
+                    prow[0] = pseudopotential(p, h);
+                }
+                if (t == nint - 1) {  // right halo column x0 + nint
+                    PT h;
+                    pull(b_m, b_c, b_p, c + 1, h);
+                    prow[nint + 1] = pseudopotential(p, h);
+                }
             }
         }
         consumer_sync();
         // staged row k-1 is no longer needed by any consumer
         __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[(k - 1) % kStages]);
-        if (k >= 3 && interior && !cur.solid) {
+        if (lane == 0) mbar_arrive(&empty[s_m]);
+        if (k >= 3 && interior && !prev.solid) {
             // collide row r-1 with psi rows r-2, r-1, r
             const int rc = r - 1;
-            const float* pm = psi_w + ((rc + 3) & 3) * (kW + 2);
-            const float* pc = psi_w + ((rc + 4) & 3) * (kW + 2);
-            const float* pp = psi_w + ((rc + 5) & 3) * (kW + 2);
+            const float* pm = psi_w + ((rc + 3) & 3) * kPsiStride;
+            const float* pc = psi_w + ((rc + 4) & 3) * kPsiStride;
+            const float* pp = psi_w + ((rc + 5) & 3) * kPsiStride;
             if constexpr (ST == kF32)
-                collide_node<MODE>(cur, pm, pc, pp, t + 1, p, g, fout, fields, x, rc, acc);
+                collide_node<MODE>(prev, pm, pc, pp, tr, p, g, fout, fields, x, rc, acc);
             else
-                collide_dev<MODE, T>(cur, pm, pc, pp, t + 1, p, g, fout, reinterpret_cast<T*>(fout + g.plane),
+                collide_dev<MODE, T>(prev, pm, pc, pp, tr, p, g, fout, reinterpret_cast<T*>(fout + g.plane),
                                      fields, x, rc, acc);
         } else if constexpr (MODE == kFields) {
             if (k >= 3 && interior) {
@@ -752,7 +858,21 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
                 fields[2 * nn + i] = 0.0;
             }
         }
-        cur = nxt;
+        // advance the ring by one row
+        s_m = (s_m == kStages - 1) ? 0 : s_m + 1;
+        s_p = (s_p == kStages - 1) ? 0 : s_p + 1;
+        ph_p ^= (s_p == 0) ? 1u : 0u;
+        b_m = b_c;
+        b_c = b_p;
+        b_p = stage_ptr(s_p);
+    };
+
+    // two pulled-node registers used in turn, so that no copy is made
+    PT n0, n1;
+    n0.solid = n1.solid = true;
+    for (int k = 1; k <= nrows - 2; k += 2) {
+        body(k, n0, n1);
+        if (k + 1 <= nrows - 2) body(k + 1, n1, n0);
     }
     (void)ok;
 
@@ -843,7 +963,7 @@ __global__ void __launch_bounds__(kThreads, 3)
         __syncthreads();
         if (threadIdx.x == 0) {
             uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + kStages * stage_bytes<ST>() +
-                                                         4 * (kW + 2) * sizeof(float));
+                                                         4 * kPsiStride * sizeof(float));
             for (int s = 0; s < 2 * kStages; ++s) mbar_inval(&bars[s]);
         }
         __syncthreads();
