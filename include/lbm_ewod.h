@@ -199,6 +199,16 @@ lbm_status lbm_run_to_steady(lbm_ctx *ctx, double rel_tol, int64_t check_every, 
  * LBM_ENAN as for lbm_observables. */
 lbm_status lbm_obs_latest(lbm_ctx *ctx, lbm_obs *out);
 
+/* As lbm_obs_latest without the synchronisation: enqueues the copy of that
+ * record into *out (host memory) on the context's stream and returns. *out
+ * is valid once the stream has passed this point (e.g. after an event
+ * recorded next completes) and must stay allocated until then; page-locked
+ * memory keeps the copy asynchronous (pageable memory makes it synchronous,
+ * as for any CUDA copy). The caller checks out->nonfinite itself. Lets a
+ * host loop read every step's result while the next step runs. LBM_ESTATE
+ * if no record exists yet. */
+lbm_status lbm_obs_latest_async(lbm_ctx *ctx, lbm_obs *out);
+
 /* Current time index (steps taken since the last lbm_set_geometry). */
 int64_t lbm_time(const lbm_ctx *ctx);
 

@@ -142,6 +142,27 @@ __device__ __forceinline__ double feq_d(int a, double rho, double ux, double uy)
     return kW[a] * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * (ux * ux + uy * uy));
 }
 
+// The 9 equilibria f_a^eq(rho, u) of Eq. 3 in FP64, each rounded once to
+// FP32: w_a rho (1 + 3 c + 4.5 c^2 - 1.5 u^2) with c = e_a . u, the
+// polynomial as two FMAs around the shared 1 - 1.5 u^2 (the device has few
+// FP64 units, so the set-up time follows the FP64 operation count).
+__device__ __forceinline__ void feq_all_d(double rho, double ux, double uy, float* __restrict__ f, size_t plane)
+{
+    const double om = 1.0 - 1.5 * (ux * ux + uy * uy);
+    const double w0r = kW[0] * rho, w1r = kW[1] * rho, w2r = kW[5] * rho;
+    auto q = [om](double c) { return fma(c, fma(4.5, c, 3.0), om); };
+    const double d5 = ux + uy, d6 = uy - ux;
+    f[0] = float(w0r * om);
+    f[plane] = float(w1r * q(ux));
+    f[2 * plane] = float(w1r * q(uy));
+    f[3 * plane] = float(w1r * q(-ux));
+    f[4 * plane] = float(w1r * q(-uy));
+    f[5 * plane] = float(w2r * q(d5));
+    f[6 * plane] = float(w2r * q(d6));
+    f[7 * plane] = float(w2r * q(-d5));
+    f[8 * plane] = float(w2r * q(-d6));
+}
+
 // Initial state from (rho, ux, uy): the post-streaming populations
 // f_a = f_a^eq(rho, u) of Eq. 3 (evaluated in FP64, rounded once), written
 // into buffer `f` in plane layout; solid nodes get the sentinel.
@@ -158,9 +179,7 @@ __global__ void feq_kernel(const double* __restrict__ ru, const uint8_t* __restr
             for (int a = 0; a < 9; ++a) f[a * g.plane + o] = __uint_as_float(kSolidBits);
             continue;
         }
-        const double rho = ru[i], ux = ru[n + i], uy = ru[2 * n + i];
-#pragma unroll
-        for (int a = 0; a < 9; ++a) f[a * g.plane + o] = float(feq_d(a, rho, ux, uy));
+        feq_all_d(ru[i], ru[n + i], ru[2 * n + i], f + o, size_t(g.plane));
     }
 }
 
@@ -1118,6 +1137,17 @@ lbm_status lbm_obs_latest(lbm_ctx* c, lbm_obs* out)
     if (!out) return fail(c, LBM_EINVAL, "output is NULL");
     if (c->ring_count == 0) return fail(c, LBM_ESTATE, "no fused observables recorded yet (obs_every = %d)", c->prm.obs_every);
     return read_record(c, c->ring + ((c->ring_count - 1) % kRing), out);
+}
+
+lbm_status lbm_obs_latest_async(lbm_ctx* c, lbm_obs* out)
+{
+    lbm_status s = ready(c);
+    if (s) return s;
+    if (!out) return fail(c, LBM_EINVAL, "output is NULL");
+    if (c->ring_count == 0) return fail(c, LBM_ESTATE, "no fused observables recorded yet (obs_every = %d)", c->prm.obs_every);
+    return check_cuda(c, cudaMemcpyAsync(out, c->ring + ((c->ring_count - 1) % kRing), sizeof(lbm_obs),
+                                         cudaMemcpyDeviceToHost, c->stream),
+                      "observables download");
 }
 
 int64_t lbm_time(const lbm_ctx* c) { return c ? c->t : -1; }

@@ -7,7 +7,7 @@ workspace tensor) and for the CUDA stream the context enqueues on.
 
 Low level: ``lbm_workspace_bytes``, ``lbm_create``, ``lbm_set_geometry``,
 ``lbm_set_field``, ``lbm_get_field``, ``lbm_step``, ``lbm_observables``,
-``lbm_obs_latest``, ``lbm_time``, ``lbm_last_error``, ``lbm_status_string``,
+``lbm_obs_latest``, ``lbm_obs_latest_async``, ``lbm_time``, ``lbm_last_error``, ``lbm_status_string``,
 ``lbm_destroy``; each raises ``LbmError`` on a non-zero status.
 High level: ``Lattice`` owns a workspace tensor and a context.
 """
@@ -86,6 +86,7 @@ def load():
             "lbm_step": (ctypes.c_int, [vp, ctypes.c_int64]),
             "lbm_observables": (ctypes.c_int, [vp, O]),
             "lbm_obs_latest": (ctypes.c_int, [vp, O]),
+            "lbm_obs_latest_async": (ctypes.c_int, [vp, vp]),
             "lbm_run_to_steady": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int64, ctypes.c_int64, O]),
             "lbm_time": (ctypes.c_int64, [vp]),
             "lbm_selftest_timeout": (ctypes.c_int, [vp]),
@@ -168,6 +169,18 @@ def lbm_obs_latest(ctx, check_finite: bool = True) -> dict:
     if st != LBM_ENAN or check_finite:
         _check(ctx, st)
     return o.as_dict()
+
+
+def lbm_obs_latest_async(ctx, out_ptr: int) -> None:
+    """Enqueue the copy of the latest fused record into host memory at
+    ``out_ptr`` (an ``lbm_obs``, preferably page-locked); no synchronisation.
+    Read it with ``obs_from_buffer`` once the stream has passed this point."""
+    _check(ctx, load().lbm_obs_latest_async(ctx, ctypes.c_void_p(out_ptr)))
+
+
+def obs_from_buffer(ptr: int) -> dict:
+    """The ``lbm_obs`` record at host address ``ptr`` as a dict."""
+    return lbm_obs.from_address(ptr).as_dict()
 
 
 def lbm_run_to_steady(ctx, rel_tol: float, check_every: int, max_steps: int) -> tuple[dict, bool]:

@@ -420,3 +420,22 @@ def test_bounded_wait_times_out_and_context_survives(lbm):
     ref.set_rho_u(w.rho)
     ref.step(50)
     assert np.array_equal(lat.populations(), ref.populations())
+
+
+@pytest.mark.gpu
+def test_obs_latest_async_matches_synchronous_read(lbm):
+    """The enqueued copy of the latest fused record (no synchronisation in
+    the call) equals the record the synchronising read returns."""
+    import ctypes
+    import torch
+    w = wl.droplet_128x64(0.125)
+    lat = lbm.Lattice(w.nx, w.ny, obs_every=1, **w.params)
+    lat.set_geometry(w.mask)
+    lat.set_rho_u(w.rho)
+    buf = torch.empty(ctypes.sizeof(lbm.lbm_obs), dtype=torch.uint8).pin_memory()
+    for _ in range(3):
+        lat.step(7)
+        lbm.lbm_obs_latest_async(lat.ctx, buf.data_ptr())
+        torch.cuda.synchronize()
+        assert lbm.obs_from_buffer(buf.data_ptr()) == lbm.lbm_obs_latest(lat.ctx)
+    lat.close()
