@@ -201,7 +201,29 @@ def cpu_baseline(w, target_s, cores):
     return {"value": s.cx * s.cy * steps / t / 1e6, "unit": "MLUPS", "cores": used,
             "kind": "oracle", "sample": s.describe(steps, t),
             "one_core": {"value": round(s.cx * s.cy * steps1 / t1 / 1e6, 3), "unit": "MLUPS", "cores": 1,
-                         "sample": s.describe(steps1, t1)}}
+                         "sample": s.describe(steps1, t1)},
+            "small_configs": oracle_small_configs(s.oracle)}
+
+
+def oracle_small_configs(oracle, seconds=2.0):
+    """The oracle on the two small single-domain configurations of
+    `small_configs` (all host cores; doubling the step count until one run
+    takes at least a quarter of `seconds`)."""
+    from paper_0708_4182_gb300 import workloads as wl
+    out = {}
+    for name, w in (("droplet_128x64_f0.25", wl.droplet_128x64(0.25)),
+                    ("rough_channel_1024x128_level15", wl.rough_channel(level=15))):
+        p = oracle.Params(w.nx, w.ny, **w.params)
+        mask = np.ascontiguousarray(w.mask)
+        f = oracle.equilibrium(p, mask, np.where(mask == 1, 0.0, w.rho), 0, 0)
+        steps, t = 4, 0.0
+        while t < 0.25 * seconds and steps < 10 ** 6:
+            steps *= 2
+            t0 = time.perf_counter()
+            f = oracle.step(p, mask, f, steps)
+            t = time.perf_counter() - t0
+        out[name] = {"mlups": round(w.nx * w.ny * steps / t / 1e6, 2), "steps": steps, "seconds": round(t, 2)}
+    return out
 
 
 # ----------------------------------------------------------------- arms
