@@ -39,6 +39,7 @@ using bf16 = __nv_bfloat16;
 constexpr int kT = 256;                      // threads of the SIMT kernels
 constexpr int kTcThreads = 128;              // threads of the tensor-core kernels (4 warps = 128 TMEM lanes)
 constexpr int kStages = 4;                   // operand ring depth of the tensor-core kernels
+constexpr int kWgradStep = 64;               // pixels per K-step of the weight gradient where the row allows
 constexpr uint32_t kWaitLimit = 1u << 18;    // try_wait rounds before giving up (about 1 s on a GB300)
 constexpr int kTileRows = 4, kTileCols = 32; // output pixels of one conv CTA (M = 128)
 constexpr int kSmemPerSm = 233472;           // shared memory of one SM (bytes)
@@ -425,16 +426,18 @@ __global__ void conv_pack_kernel(const float* __restrict__ w, int co, int ci, in
 }
 
 // ------------------------------------------------------------------ tensor-core weight gradient
-// Weight gradient, one CTA per tap row: per K-step of 16 pixels of one image
-// row, dy (A, 128 output channels x 16 pixels) is staged once and x as a halo
-// row of 18 pixels x NT channels (B, MN-major, pixels at a uniform 16-byte
-// pitch within a channel group: SBO = 18 pixels, LBO = 8 pixels); the three
-// taps (dy, dx = -1, 0, 1) of the row are three MMAs whose B descriptors start
-// dx pixels in, into three accumulators of NT columns (3 NT <= 128 tensor-memory
-// columns, so four CTAs share an SM).
-constexpr int kWHaloPix = 18;
+// Weight gradient, one CTA per tap row: per K-step of P pixels of one image
+// row (P = 16, 32 or 64, dividing the row), dy (A, 128 output channels x P
+// pixels, MN-major: 8 channels of a pixel in 16 bytes, pixels at a 16-byte
+// pitch, so LBO = 8 pixels and SBO = P pixels) is staged once, and x as a
+// halo row of P + 2 pixels x NT channels (B, MN-major likewise: SBO = P + 2
+// pixels). Each 16-pixel piece j of the step gives three MMAs, one per tap
+// (dy, dx = -1, 0, 1) of the row: A starts 16 j pixels in, B 16 j + dx pixels
+// in, into three accumulators of NT columns (3 NT <= 128 tensor-memory
+// columns). Wider steps stage more bytes per ring slot and wait less often.
+template <int P> __host__ __device__ constexpr int wgrad_halo_pix() { return P + 2; }
 
-template <int NT>
+template <int NT, int P>
 __global__ void __launch_bounds__(kTcThreads) wgrad_tc_taps_kernel(const bf16* __restrict__ x, int ct_x, int ci,
                                                                    const bf16* __restrict__ dy, int ct_dy, int co,
                                                                    float* __restrict__ dw, int H, int W, int npix,
@@ -442,9 +445,11 @@ __global__ void __launch_bounds__(kTcThreads) wgrad_tc_taps_kernel(const bf16* _
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     static_assert(3 * NT <= int(tmem_cols(3 * NT)), "three accumulators must fit the allocation");
+    static_assert(P == 16 || P == 32 || P == 64, "K-step of 16, 32 or 64 pixels");
     constexpr int G = NT / 8;                              // 8-channel groups of B
-    constexpr int kABytes = 128 * 16 * 2;                  // 128 output channels x 16 pixels
-    constexpr int kBBytes = G * kWHaloPix * 16;            // one halo row of B
+    constexpr int HP = wgrad_halo_pix<P>();                // halo row pixels
+    constexpr int kABytes = 128 * P * 2;                   // 128 output channels x P pixels
+    constexpr int kBBytes = G * HP * 16;                   // one halo row of B
     constexpr uint32_t kCols = tmem_cols(3 * NT);
     unsigned char* sa = smem;
     unsigned char* sb = smem + kStages * kABytes;
@@ -457,7 +462,7 @@ __global__ void __launch_bounds__(kTcThreads) wgrad_tc_taps_kernel(const bf16* _
     const int co_here = co - co0 < 128 ? co - co0 : 128;
     const int ci_here = ci - ci0 < NT ? ci - ci0 : NT;
     const long long p_begin = (long long)(blockIdx.z / 3) * npix;
-    const int KT = npix / 16;
+    const int KT = npix / P;
 
     // rows of A beyond co_here and channel groups of B beyond ci_here are never loaded: zero them once
     for (int i = tid; i < kStages * (kABytes + kBBytes) / 16; i += kTcThreads)
@@ -475,24 +480,24 @@ __global__ void __launch_bounds__(kTcThreads) wgrad_tc_taps_kernel(const bf16* _
     const int ga = co_here / 8, gb = (ci_here + 7) / 8;
     auto load = [&](int it) {
         const int s = it % kStages;
-        const long long p0 = p_begin + (long long)it * 16;
+        const long long p0 = p_begin + (long long)it * P;
         const int bimg = int(p0 / ((long long)H * W));
         const int rem = int(p0 % ((long long)H * W));
         const int yy = rem / W, x0 = rem % W;
         unsigned char* da = sa + s * kABytes;
         unsigned char* db = sb + s * kBBytes;
-        for (int q = tid; q < 16 * ga; q += kTcThreads) {
-            const int k = q % 16, g = q / 16;
+        for (int q = tid; q < P * ga; q += kTcThreads) {
+            const int k = q % P, g = q / P;
             const bf16* src = dy + (size_t(bimg * H + yy) * W + x0 + k) * ct_dy + co0 + g * 8;
-            cp_async16_cg(da + g * 256 + (k >> 3) * 128 + (k & 7) * 16, src, 16u);
+            cp_async16_cg(da + g * (P * 16) + k * 16, src, 16u);
         }
         const int ys = yy + trow - 1;
         const bool ok = ys >= 0 && ys < H;
-        for (int q = tid; q < kWHaloPix * gb; q += kTcThreads) {
-            const int pix = q % kWHaloPix, g = q / kWHaloPix;
+        for (int q = tid; q < HP * gb; q += kTcThreads) {
+            const int pix = q % HP, g = q / HP;
             const int xs = wrapx(x0 + pix - 1, W);
             const bf16* src = ok ? x + (size_t(bimg * H + ys) * W + xs) * ct_x + ci0 + g * 8 : x;
-            cp_async16_ca(db + g * (kWHaloPix * 16) + pix * 16, src, ok ? 16u : 0u);
+            cp_async16_ca(db + g * (HP * 16) + pix * 16, src, ok ? 16u : 0u);
         }
     };
 
@@ -510,12 +515,16 @@ __global__ void __launch_bounds__(kTcThreads) wgrad_tc_taps_kernel(const bf16* _
         __syncthreads();
         if (tid == 0) {
             tc_fence_after();
-            const uint64_t da = smem_desc(smem_u32(sa + s * kABytes), 128, 256);
+            const uint32_t a0 = smem_u32(sa + s * kABytes);
             const uint32_t b0 = smem_u32(sb + s * kBBytes);
-#pragma unroll 1
-            for (int dx = 0; dx < 3; ++dx) {
-                const uint64_t db = smem_desc(b0 + dx * 16, 128, kWHaloPix * 16);
-                mma_bf16(tmem + dx * NT, da, db, idesc, it > 0 ? 1u : 0u);
+#pragma unroll
+            for (int j = 0; j < P / 16; ++j) {
+                const uint64_t da = smem_desc(a0 + j * 256, 128, P * 16);
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx) {
+                    const uint64_t db = smem_desc(b0 + (16 * j + dx) * 16, 128, HP * 16);
+                    mma_bf16(tmem + dx * NT, da, db, idesc, (it > 0 || j > 0) ? 1u : 0u);
+                }
             }
             mma_commit(&bars[s]);
         }
@@ -883,15 +892,25 @@ int launch_conv(const void* x, int ct_in, int kc, const void* wt, const float* b
     return status(cudaGetLastError());
 }
 
+template <int NT, int P>
+int launch_wgrad_taps_p(const void* x, int ct_x, int ci, const void* dy, int ct_dy, int co, float* dw, int h, int wd,
+                        int npix, long long total, cudaStream_t st)
+{
+    constexpr int needed = kStages * (128 * P * 2 + (NT / 8) * wgrad_halo_pix<P>() * 16) + kStages * 8 + 16;
+    const int smem = smem_for_tmem(int(tmem_cols(3 * NT)), needed);
+    auto k = wgrad_tc_taps_kernel<NT, P>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return int(e);
+    dim3 grid((co + 127) / 128, (ci + NT - 1) / NT, int(3 * (total / npix)));
+    k<<<grid, kTcThreads, smem, st>>>((const bf16*)x, ct_x, ci, (const bf16*)dy, ct_dy, co, dw, h, wd, npix,
+                                      err_ptr());
+    return status(cudaGetLastError());
+}
+
 template <int NT>
 int launch_wgrad_taps(const void* x, int ct_x, int ci, const void* dy, int ct_dy, int co, float* dw, int n, int h,
                       int wd, cudaStream_t st)
 {
-    constexpr int needed = kStages * (128 * 32 + (NT / 8) * kWHaloPix * 16) + kStages * 8 + 16;
-    const int smem = smem_for_tmem(int(tmem_cols(3 * NT)), needed);
-    auto k = wgrad_tc_taps_kernel<NT>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return int(e);
     // pixels per CTA: a power of two (whole 16-pixel row pieces) dividing the
     // total, at most 2048, halved while the grid has fewer than four CTAs per
     // SM (at least 64 pixels per CTA)
@@ -902,10 +921,11 @@ int launch_wgrad_taps(const void* x, int ct_x, int ci, const void* dy, int ct_dy
     int npix = 2048;
     while (npix > 16 && total % npix) npix >>= 1;
     while (npix > 64 && tiles * (total / npix) < 4LL * (sms > 0 ? sms : 148) && total % (npix / 2) == 0) npix >>= 1;
-    dim3 grid((co + 127) / 128, (ci + NT - 1) / NT, int(3 * (total / npix)));
-    k<<<grid, kTcThreads, smem, st>>>((const bf16*)x, ct_x, ci, (const bf16*)dy, ct_dy, co, dw, h, wd, npix,
-                                      err_ptr());
-    return status(cudaGetLastError());
+    // K-step: kWgradStep pixels if that divides both the row and
+    // the CTA's pixel range (every step stays inside one image row), else 16
+    if (wd % kWgradStep == 0 && npix % kWgradStep == 0)
+        return launch_wgrad_taps_p<NT, kWgradStep>(x, ct_x, ci, dy, ct_dy, co, dw, h, wd, npix, total, st);
+    return launch_wgrad_taps_p<NT, 16>(x, ct_x, ci, dy, ct_dy, co, dw, h, wd, npix, total, st);
 }
 
 }  // namespace
