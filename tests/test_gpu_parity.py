@@ -122,7 +122,7 @@ def _blob_field(nx, ny, mask, seed):
 
 
 RAGGED = [
-    # nx, ny, walls, tile_rows : strips of 254 columns and segments of tile_rows
+    # nx, ny, walls, tile_rows : strips of 256 columns and segments of tile_rows
     # rows with ragged ends, a single CTA, a single column, a single row
     (5, 4, False, 0),
     (1, 9, True, 0),

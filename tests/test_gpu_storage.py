@@ -107,6 +107,48 @@ def test_deviation_storage_conserves_mass(lbm, storage):
     assert abs(o["mass"] / m0 - 1) <= 1e-5
 
 
+RAGGED16 = [
+    # nx, ny, walls, tile_rows: widths a multiple of 8 (the 16-bit forms' rule);
+    # overlapping strips of 254 columns with ragged ends, an 8-column domain
+    # (the staged window wraps 33 times: 34 pieces, so lanes move a second
+    # piece), a single row, a single CTA
+    (8, 16, True, 0),
+    (16, 9, True, 4),
+    (24, 30, True, 8),
+    (248, 13, True, 0),
+    (256, 20, True, 4),
+    (512, 17, True, 0),
+    (600, 1, False, 0),
+]
+
+
+@pytest.mark.parametrize("form", ["fp16", "bf16"])
+@pytest.mark.parametrize("nx,ny,walls,tile_rows", RAGGED16)
+def test_16bit_storage_ragged_and_tiny_domains(lbm, form, nx, ny, walls, tile_rows):
+    """The 16-bit forms' staging (window pieces at the periodic seam, strips
+    overlapping by two columns) against the oracle on ragged and tiny domains.
+    A misplaced column gives errors of order 0.1 to 1. The bounds sit well
+    below that and above the rounding of these blob fields after 40 steps:
+    the single-row domain, the largest, measured 8.4e-4 (FP16) and 5.2e-3
+    (BF16) relative L2 on a GB300, the others less."""
+    from tests.test_gpu_parity import _blob_field
+    mask = np.zeros((ny, nx), np.uint8)
+    if walls and ny >= 3:
+        mask[0] = mask[-1] = 1
+        if nx >= 8 and ny >= 8:
+            mask[ny // 2:ny // 2 + 2, nx // 3:nx // 3 + 3] = 1  # an interior block
+    rho = _blob_field(nx, ny, mask, nx * 1000 + ny)
+    params = dict(wl.PAPER, tau=1.0, f_elec=0.2, body_fx=1e-5, body_fy=-2e-6)
+    storage = lbm.LBM_FP16_DEV if form == "fp16" else lbm.LBM_BF16_DEV
+    p, f_ref, lat = run_both(lbm, mask, rho, params, 40, storage=storage, tile_rows=tile_rows)
+    _, _, l2 = pop_err(lat.populations(), f_ref, mask)
+    o = lat.observables()
+    r = oracle.observables(p, mask, f_ref)
+    assert o["nonfinite"] == 0
+    assert l2 <= {"fp16": 2e-3, "bf16": 1e-2}[form], l2
+    assert abs(o["mass"] / r["mass"] - 1) <= 1e-6
+
+
 def test_16bit_storage_rejects_ragged_width(lbm):
     assert lbm.lbm_workspace_bytes(lbm.make_params(300, 48, storage=lbm.LBM_FP16_DEV)) == 0
     assert lbm.lbm_workspace_bytes(lbm.make_params(304, 48, storage=lbm.LBM_FP16_DEV)) > 0
