@@ -73,6 +73,27 @@ def test_16bit_storage_errors_within_stated_bounds(lbm, form, name, make):
         assert e <= b, (form, name, errs)
 
 
+@pytest.mark.parametrize("form", ["fp16", "bf16"])
+def test_16bit_storage_tau_not_one(lbm, form):
+    """tau != 1: the relaxation reads g_a = f_a - w_a rho, which the FP16 form
+    keeps in its raw (2^12-scaled) units. Errors against the oracle stay
+    within twice the tau = 1 bounds."""
+    w = wl.droplet_128x64(0.15)
+    params = dict(w.params, tau=0.95)
+    storage = lbm.LBM_FP16_DEV if form == "fp16" else lbm.LBM_BF16_DEV
+    p, f_ref, lat = run_both(lbm, w.mask, w.rho, params, 100, storage=storage)
+    _, _, l2 = pop_err(lat.populations(), f_ref, w.mask)
+    o = lat.observables()
+    r = oracle.observables(p, w.mask, f_ref)
+    _, ux, _ = oracle.fields(p, w.mask, f_ref)
+    q_scale = np.abs(ux[w.mask == 0]).sum() / p.nx
+    errs = (l2, abs(o["mass"] / r["mass"] - 1), abs(o["flux_Q"] - r["flux_Q"]) / q_scale,
+            abs(o["max_u"] / r["max_u"] - 1))
+    print(f"{form} tau=0.95: L2 {errs[0]:.2e} mass {errs[1]:.2e} Q {errs[2]:.2e} max_u {errs[3]:.2e}")
+    for e, b in zip(errs, BOUNDS16[form]):
+        assert e <= 2 * b, (form, errs)
+
+
 @pytest.mark.parametrize("storage", [1, 2, 3])
 def test_deviation_storage_round_trip_and_tiling(lbm, storage):
     w = wl.rough_channel(nx=304, ny=48, amp=6, level=15, seed=9, body_fx=1e-5)
