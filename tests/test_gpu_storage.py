@@ -94,6 +94,28 @@ def test_16bit_storage_tau_not_one(lbm, form):
         assert e <= 2 * b, (form, errs)
 
 
+@pytest.mark.parametrize("form", ["fp32dev", "fp16", "bf16"])
+def test_deviation_storage_fields_and_profile(lbm, form):
+    """Density, velocity and the x-averaged u_x(y) read back from the
+    deviation forms on a two-strip rough channel (the 16-bit forms' strips
+    overlap): against the oracle's fields within the forms' rounding, zero
+    on solid nodes, and the profile summing to the fused flux."""
+    storage = {"fp32dev": lbm.LBM_FP32_DEV, "fp16": lbm.LBM_FP16_DEV, "bf16": lbm.LBM_BF16_DEV}[form]
+    tol = {"fp32dev": 1e-5, "fp16": 1e-3, "bf16": 1e-2}[form]
+    w = wl.rough_channel(nx=304, ny=48, amp=6, level=12, seed=5, body_fx=1e-5)
+    p, f_ref, lat = run_both(lbm, w.mask, w.rho, w.params, 100, storage=storage)
+    rho_g, ux_g, uy_g = lat.fields()
+    rho_r, ux_r, uy_r = oracle.fields(p, w.mask, f_ref)
+    solid = w.mask == 1
+    assert np.all(rho_g[solid] == 0) and np.all(ux_g[solid] == 0) and np.all(uy_g[solid] == 0)
+    assert np.abs(rho_g - rho_r).max() <= tol * rho_r.max()
+    umax = np.abs(np.r_[ux_r.ravel(), uy_r.ravel()]).max()
+    assert np.abs(ux_g - ux_r).max() <= 10 * tol * umax
+    assert np.abs(uy_g - uy_r).max() <= 10 * tol * umax
+    prof = lat.ux_profile()
+    assert prof.sum() == pytest.approx(lat.observables()["flux_Q"], rel=1e-9, abs=1e-12)
+
+
 @pytest.mark.parametrize("storage", [1, 2, 3])
 def test_deviation_storage_round_trip_and_tiling(lbm, storage):
     w = wl.rough_channel(nx=304, ny=48, amp=6, level=15, seed=9, body_fx=1e-5)
