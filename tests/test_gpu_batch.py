@@ -42,7 +42,7 @@ def specs_of(ws, storage=0):
     return [dict(nx=w.nx, ny=w.ny, storage=storage, **w.params) for w in ws]
 
 
-@pytest.mark.parametrize("storage", [0, 1, 2])
+@pytest.mark.parametrize("storage", [0, 1, 2, 3])
 def test_batch_equals_single_domain_runs(lbm, storage):
     ws = sweep_workloads(storage=storage)
     b = lbm.Batch(specs_of(ws, storage))
@@ -63,6 +63,35 @@ def test_batch_equals_single_domain_runs(lbm, storage):
         single = d.observables()
         for k in ("mass", "flux_Q", "mom_x", "mom_y", "max_u", "min_rho"):
             assert o[k] == pytest.approx(single[k], rel=1e-12, abs=1e-15), k
+    b.close()
+
+
+@pytest.mark.parametrize("storage", [0, 2])
+def test_batch_tiny_and_ragged_domains_equal_single_runs(lbm, storage):
+    """Tiny and ragged domains in one batch (an 8-column domain whose staged
+    window wraps many times, a single row, strips with ragged ends): each
+    equals the same domain stepped alone, bitwise."""
+    from tests.test_gpu_parity import _blob_field
+    shapes = [(8, 16), (24, 30), (248, 13), (600, 1), (264, 20)]
+    params = dict(wl.PAPER, tau=1.0, f_elec=0.2, body_fx=1e-5, body_fy=-2e-6)
+    cases = []
+    for nx, ny in shapes:
+        mask = np.zeros((ny, nx), np.uint8)
+        if ny >= 3:
+            mask[0] = mask[-1] = 1
+        cases.append((mask, _blob_field(nx, ny, mask, nx * 1000 + ny)))
+    b = lbm.Batch([dict(nx=m.shape[1], ny=m.shape[0], storage=storage, **params) for m, _ in cases])
+    b.set_tile_rows(8)
+    for (m, rho), d in zip(cases, b.domains):
+        d.set_geometry(m)
+        d.set_rho_u(rho)
+    b.step(21)
+    for (m, rho), d in zip(cases, b.domains):
+        lat = lbm.Lattice(m.shape[1], m.shape[0], storage=storage, **params)
+        lat.set_geometry(m)
+        lat.set_rho_u(rho)
+        lat.step(21)
+        assert np.array_equal(d.populations(), lat.populations()), m.shape
     b.close()
 
 
