@@ -195,3 +195,32 @@ def test_16bit_storage_ragged_and_tiny_domains(lbm, form, nx, ny, walls, tile_ro
 def test_16bit_storage_rejects_ragged_width(lbm):
     assert lbm.lbm_workspace_bytes(lbm.make_params(300, 48, storage=lbm.LBM_FP16_DEV)) == 0
     assert lbm.lbm_workspace_bytes(lbm.make_params(304, 48, storage=lbm.LBM_FP16_DEV)) > 0
+
+
+@pytest.mark.parametrize("storage", [1, 2, 3])
+def test_deviation_forms_fused_observables_and_graph_stepping(lbm, storage):
+    """The deviation forms' step with fused observables gives the record of a
+    separate observables pass on the same state, and one call of 75 steps
+    (32-step CUDA graphs between the fused-observables steps) equals 75 calls
+    of one step bitwise, with the same latest record."""
+    w = wl.rough_channel(nx=304, ny=48, amp=6, level=12, seed=5, body_fx=1e-5)
+    lat = lbm.Lattice(w.nx, w.ny, storage=storage, obs_every=10, **w.params)
+    lat.set_geometry(w.mask)
+    lat.set_rho_u(w.rho)
+    lat.step(30)
+    sep = lat.observables()
+    lat.step(1)
+    fused = lat.obs_latest()
+    assert fused["step"] == sep["step"] == 30
+    for k in ("mass", "flux_Q", "mom_x", "mom_y", "max_u", "min_rho"):
+        assert fused[k] == pytest.approx(sep[k], rel=1e-12, abs=1e-15), k
+    runs = []
+    for chunks in ([75], [1] * 75):
+        lat = lbm.Lattice(w.nx, w.ny, storage=storage, obs_every=10, **w.params)
+        lat.set_geometry(w.mask)
+        lat.set_rho_u(w.rho)
+        for n in chunks:
+            lat.step(n)
+        runs.append((lat.populations(), lat.obs_latest()))
+    assert np.array_equal(runs[0][0], runs[1][0])
+    assert runs[0][1] == runs[1][1] and runs[0][1]["step"] == 70
