@@ -306,8 +306,9 @@ __global__ void pops_out_kernel(const float* __restrict__ fs, const uint8_t* __r
 }
 
 // Plain post-collision planes f* (FP32) -> deviation form: plane 0 gets
-// rho* = sum_a f*_a, planes 1..8 (type T) get d_a = f*_a - w_a rho*
-// (FP64 arithmetic, one rounding each). Solid nodes get the sentinel.
+// rho* = sum_a f*_a, the deviations (type T, laid out by dev_index) get
+// d_a = f*_a - w_a rho* (FP64 arithmetic, one rounding each). Solid nodes get
+// the sentinel.
 template <typename T>
 __global__ void plain_to_dev_kernel(const float* __restrict__ fs, const uint8_t* __restrict__ mask,
                                     float* __restrict__ out, Geom g)
@@ -326,7 +327,9 @@ __global__ void plain_to_dev_kernel(const float* __restrict__ fs, const uint8_t*
         for (int a = 0; a < 9; ++a) r += fs[a * g.plane + o];
         const float r32 = float(r);
         out[o] = r32;
-        for (int a = 1; a < 9; ++a) od[(a - 1) * g.plane + o] = from_f<T>(float(double(fs[a * g.plane + o]) - kW[a] * double(r32)));
+        for (int a = 1; a < 9; ++a)
+            od[dev_index<T>(size_t(o), a, size_t(g.plane))] =
+                from_f<T>(float(double(fs[a * g.plane + o]) - kW[a] * double(r32)));
     }
 }
 
@@ -349,7 +352,7 @@ __global__ void dev_to_plain_kernel(const float* __restrict__ in, const uint8_t*
         const double r = in[o];
         double dsum = 0.0;
         for (int a = 1; a < 9; ++a) {
-            const double d = to_f(id[(a - 1) * g.plane + o]);
+            const double d = to_f(id[dev_index<T>(size_t(o), a, size_t(g.plane))]);
             dsum += d;
             fs[a * g.plane + o] = float(kW[a] * r + d);
         }

@@ -45,7 +45,8 @@
 //              per-step changes of a slow flow are representable in d_a,
 //              where a plain FP32 f*_a of size ~w_a rho rounds them away;
 //  - kF16Dev / kBF16Dev: as kF32Dev with d_a stored in 16 bits (FP16 or
-//              BF16, rounded to nearest); 20 instead of 36 bytes per node.
+//              BF16, rounded to nearest), the 8 of a node interleaved in 16
+//              bytes after plane 0 (dev_index); 20 instead of 36 bytes per node.
 // In the deviation forms the pull rebuilds f_a = w_a rho*(src) + d_a(src),
 // and the kernel forms rho - rho*(x) and rho u from sums of small terms.
 #pragma once
@@ -82,7 +83,17 @@ template <> struct StoreT<kBF16Dev> { using T = __nv_bfloat16; static constexpr 
 // Columns a CTA collides: kW, or kW - 2 where neighbouring strips overlap.
 __host__ __device__ constexpr int strip_cols(int st) { return (st == kF16Dev || st == kBF16Dev) ? kW - 2 : kW; }
 
-// staged row: plane 0 (FP32, kRowLen floats) then planes 1..8 (type T)
+// Element index of deviation a (1..8) of the node at o = y * pitch + x among
+// the deviation values that follow plane 0 (plane = ny * pitch): FP32
+// deviations in 8 planes of `plane` elements; 16-bit deviations interleaved,
+// the 8 of a node in 16 contiguous bytes (one vector store per node). The
+// staged rows in shared memory use the same two layouts with R for plane.
+template <typename T> __host__ __device__ __forceinline__ size_t dev_index(size_t o, int a, size_t plane)
+{
+    return sizeof(T) == 2 ? o * 8 + size_t(a - 1) : size_t(a - 1) * plane + o;
+}
+
+// staged row: plane 0 (FP32, kRowLen floats) then 8 x kRowLen deviations (type T)
 template <int ST> __host__ __device__ constexpr size_t stage_bytes()
 {
     return size_t(kRowLen) * (sizeof(float) + 8 * sizeof(typename StoreT<ST>::T));
@@ -488,16 +499,30 @@ __device__ __forceinline__ void pull_dev(const float* __restrict__ s0m, const fl
         return;
     }
     float rs[9], d[9], own[9];
-    rs[1] = s0c[c - 1];  d[1] = to_raw(sdc[0 * R + c - 1]);  // e1: source (x-1, y)
-    rs[2] = s0m[c];      d[2] = to_raw(sdm[1 * R + c]);      // e2: source (x, y-1)
-    rs[3] = s0c[c + 1];  d[3] = to_raw(sdc[2 * R + c + 1]);  // e3: source (x+1, y)
-    rs[4] = s0p[c];      d[4] = to_raw(sdp[3 * R + c]);      // e4: source (x, y+1)
-    rs[5] = s0m[c - 1];  d[5] = to_raw(sdm[4 * R + c - 1]);  // e5: source (x-1, y-1)
-    rs[6] = s0m[c + 1];  d[6] = to_raw(sdm[5 * R + c + 1]);  // e6: source (x+1, y-1)
-    rs[7] = s0p[c + 1];  d[7] = to_raw(sdp[6 * R + c + 1]);  // e7: source (x+1, y+1)
-    rs[8] = s0p[c - 1];  d[8] = to_raw(sdp[7 * R + c - 1]);  // e8: source (x-1, y+1)
+    auto dv = [](const T* sd, int col, int a) { return to_raw(sd[dev_index<T>(size_t(col), a, size_t(R))]); };
+    rs[1] = s0c[c - 1];  d[1] = dv(sdc, c - 1, 1);  // e1: source (x-1, y)
+    rs[2] = s0m[c];      d[2] = dv(sdm, c, 2);      // e2: source (x, y-1)
+    rs[3] = s0c[c + 1];  d[3] = dv(sdc, c + 1, 3);  // e3: source (x+1, y)
+    rs[4] = s0p[c];      d[4] = dv(sdp, c, 4);      // e4: source (x, y+1)
+    rs[5] = s0m[c - 1];  d[5] = dv(sdm, c - 1, 5);  // e5: source (x-1, y-1)
+    rs[6] = s0m[c + 1];  d[6] = dv(sdm, c + 1, 6);  // e6: source (x+1, y-1)
+    rs[7] = s0p[c + 1];  d[7] = dv(sdp, c + 1, 7);  // e7: source (x+1, y+1)
+    rs[8] = s0p[c - 1];  d[8] = dv(sdp, c - 1, 8);  // e8: source (x-1, y+1)
+    if constexpr (sizeof(T) == 2) {
+        // the node's own 8 deviations: one 16-byte load
+        const uint4 q = *reinterpret_cast<const uint4*>(sdc + size_t(c) * 8);
+        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-    for (int b = 1; b < 9; ++b) own[b] = to_raw(sdc[(b - 1) * R + c]);
+        for (int b = 1; b < 9; ++b) {
+            const unsigned short bits = (unsigned short)(w[(b - 1) >> 1] >> (16 * ((b - 1) & 1)));
+            T v;
+            memcpy(&v, &bits, sizeof(T));
+            own[b] = to_raw(v);
+        }
+    } else {
+#pragma unroll
+        for (int b = 1; b < 9; ++b) own[b] = dv(sdc, c, b);
+    }
     constexpr int opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
     auto qsum = [&rs, r0](float& q1, float& q2) {
         q1 = ((rs[1] - r0) + (rs[3] - r0)) + ((rs[2] - r0) + (rs[4] - r0));
@@ -571,13 +596,30 @@ __device__ __forceinline__ void collide_dev(const PulledDev& n, const float* pm,
         dq[8] = w2r * dpoly(-d6);
         const int o = r * g.pitch + x;
         fout0[o] = n.rho;
+        float v[9];
         if (p.tau == 1.f) {
 #pragma unroll
-            for (int a = 1; a < 9; ++a) foutd[(a - 1) * g.plane + o] = from_raw<T>(dq[a]);
+            for (int a = 1; a < 9; ++a) v[a] = dq[a];
         } else {
 #pragma unroll
-            for (int a = 1; a < 9; ++a)
-                foutd[(a - 1) * g.plane + o] = from_raw<T>(fmaf(dq[a] - n.g[a], p.inv_tau, n.g[a]));
+            for (int a = 1; a < 9; ++a) v[a] = fmaf(dq[a] - n.g[a], p.inv_tau, n.g[a]);
+        }
+        if constexpr (sizeof(T) == 2) {
+            // the node's 8 deviations in one 16-byte store (paired conversions,
+            // each value rounded to nearest as alone)
+            uint32_t w[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                T lo = from_raw<T>(v[2 * k + 1]), hi = from_raw<T>(v[2 * k + 2]);
+                unsigned short bl, bh;
+                memcpy(&bl, &lo, 2);
+                memcpy(&bh, &hi, 2);
+                w[k] = uint32_t(bl) | (uint32_t(bh) << 16);
+            }
+            *reinterpret_cast<uint4*>(foutd + size_t(o) * 8) = make_uint4(w[0], w[1], w[2], w[3]);
+        } else {
+#pragma unroll
+            for (int a = 1; a < 9; ++a) foutd[(a - 1) * g.plane + o] = from_raw<T>(v[a]);
         }
     }
     if constexpr (MODE != kStep) node_observe<MODE>(n.rho, rinv, n.jx, n.jy, Fx, Fy, g, fields, x, r, acc);
@@ -618,7 +660,8 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
     constexpr int P = StoreT<ST>::overlap;
     constexpr int R = kRowLen;
     constexpr size_t SB = stage_bytes<ST>();
-    // ring stage s: plane 0 (FP32, R) then planes 1..8 (T, R each)
+    // ring stage s: plane 0 (FP32, R) then the deviations in the layout of
+    // dev_index with plane = R (8 planes of R for FP32, 8 per node for 16 bits)
     float* psi_ring = reinterpret_cast<float*>(smem_raw + kStages * SB);      // [4][kPsiStride]
     uint64_t* full = reinterpret_cast<uint64_t*>(psi_ring + 4 * kPsiStride);  // [kStages]
     uint64_t* empty = full + kStages;                                         // [kStages]
@@ -731,11 +774,12 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
                 fill(k);
             }
         } else {
-            // 16-bit deviation planes (nx % 8 == 0): the window splits at the
+            // 16-bit deviations (nx % 8 == 0): the window splits at the
             // periodic seam into pieces that start and end on 16-byte
             // boundaries, the same for every row; lane l moves pieces l,
-            // l + 32, ... with one cp.async.bulk per plane. The producer runs
-            // ahead on its own, as above.
+            // l + 32, ... with two cp.async.bulk copies each (plane 0 and the
+            // node-interleaved deviations). The producer runs ahead on its
+            // own, as above.
             const uint32_t tx = uint32_t(L) * uint32_t(sizeof(float) + 8 * sizeof(T));
             const T* dbase = reinterpret_cast<const T*>(fin + g.plane);
             // piece q covers window positions [max(ws, (m0+q) nx), min(ws+L, (m0+q+1) nx))
@@ -750,15 +794,13 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
             };
             int pj = 0, pgx = 0, plen = 0;  // this lane's first piece
             if (lane < npieces) piece(lane, pj, pgx, plen);
+            // plane 0 and the node-interleaved deviations (16 bytes a node)
             auto copy_piece = [&](float* s0, int row, int j, int gx, int len, uint64_t* bar) {
                 T* sd = reinterpret_cast<T*>(s0 + R);
                 const float* g0 = fin + size_t(row) * g.pitch;
-                const T* gd = dbase + size_t(row) * g.pitch;
+                const T* gd = dbase + size_t(row) * g.pitch * 8;
                 bulk_g2s(s0 + j, g0 + gx, uint32_t(len) * 4u, bar);
-#pragma unroll 1
-                for (int a = 1; a < 9; ++a)
-                    bulk_g2s(sd + (a - 1) * R + j, gd + size_t(a - 1) * g.plane + gx,
-                             uint32_t(len) * uint32_t(sizeof(T)), bar);
+                bulk_g2s(sd + size_t(j) * 8, gd + size_t(gx) * 8, uint32_t(len) * 16u, bar);
             };
             auto fill = [&](int k) {
                 const int s = k % kStages;
