@@ -596,15 +596,15 @@ __device__ __forceinline__ void collide_dev(const PulledDev& n, const float* pm,
         dq[8] = w2r * dpoly(-d6);
         const int o = r * g.pitch + x;
         fout0[o] = n.rho;
-        float v[9];
-        if (p.tau == 1.f) {
-#pragma unroll
-            for (int a = 1; a < 9; ++a) v[a] = dq[a];
-        } else {
-#pragma unroll
-            for (int a = 1; a < 9; ++a) v[a] = fmaf(dq[a] - n.g[a], p.inv_tau, n.g[a]);
-        }
         if constexpr (sizeof(T) == 2) {
+            float v[9];
+            if (p.tau == 1.f) {
+#pragma unroll
+                for (int a = 1; a < 9; ++a) v[a] = dq[a];
+            } else {
+#pragma unroll
+                for (int a = 1; a < 9; ++a) v[a] = fmaf(dq[a] - n.g[a], p.inv_tau, n.g[a]);
+            }
             // the node's 8 deviations in one 16-byte store (paired conversions,
             // each value rounded to nearest as alone)
             uint32_t w[4];
@@ -617,9 +617,13 @@ __device__ __forceinline__ void collide_dev(const PulledDev& n, const float* pm,
                 w[k] = uint32_t(bl) | (uint32_t(bh) << 16);
             }
             *reinterpret_cast<uint4*>(foutd + size_t(o) * 8) = make_uint4(w[0], w[1], w[2], w[3]);
+        } else if (p.tau == 1.f) {
+#pragma unroll
+            for (int a = 1; a < 9; ++a) foutd[(a - 1) * g.plane + o] = from_raw<T>(dq[a]);
         } else {
 #pragma unroll
-            for (int a = 1; a < 9; ++a) foutd[(a - 1) * g.plane + o] = from_raw<T>(v[a]);
+            for (int a = 1; a < 9; ++a)
+                foutd[(a - 1) * g.plane + o] = from_raw<T>(fmaf(dq[a] - n.g[a], p.inv_tau, n.g[a]));
         }
     }
     if constexpr (MODE != kStep) node_observe<MODE>(n.rho, rinv, n.jx, n.jy, Fx, Fy, g, fields, x, r, acc);
