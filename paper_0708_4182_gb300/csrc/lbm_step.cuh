@@ -71,9 +71,10 @@ constexpr uint32_t kWaitLimit = 1u << 18;      // try_wait rounds before giving 
 
 enum Storage { kF32 = 0, kF32Dev = 1, kF16Dev = 2, kBF16Dev = 3 };
 
-// T: type of planes 1..8; align: columns per 16 bytes of the narrowest plane
-// (every staging copy starts and ends on such a boundary); overlap: the
-// strip layout (see run_tile), 0 for the 32-bit forms, 1 for the 16-bit ones
+// T: type of the 8 values after plane 0 (populations or deviations); align:
+// columns per 16 bytes of the narrowest plane (every staging copy starts and
+// ends on such a boundary); overlap: the strip layout (see run_tile), 0 for
+// the 32-bit forms, 1 for the 16-bit ones
 template <int ST> struct StoreT;
 template <> struct StoreT<kF32> { using T = float; static constexpr int align = 4, overlap = 0; };
 template <> struct StoreT<kF32Dev> { using T = float; static constexpr int align = 4, overlap = 0; };
@@ -102,7 +103,7 @@ template <int ST> __host__ __device__ constexpr size_t smem_bytes()
 {
     return kStages * (stage_bytes<ST>() + 2 * sizeof(uint64_t)) + 4 * kPsiStride * sizeof(float) + 128;
 }
-// bytes of one node's state in global memory (plane 0 + planes 1..8)
+// bytes of one node's state in global memory (plane 0 + the other 8 values)
 template <int ST> __host__ __device__ constexpr int node_bytes() { return 4 + 8 * int(sizeof(typename StoreT<ST>::T)); }
 
 // FP16 deviations are stored scaled by 2^12 (an exact scaling): |d| up to 16
@@ -480,7 +481,7 @@ template <typename T> struct RawScale { static constexpr float scale = 1.f, unsc
 template <> struct RawScale<__half> { static constexpr float scale = kF16Scale, unscale = kF16Unscale; };
 
 // Pull in deviation form: s0* are plane-0 rows (rho*) r-1, r, r+1; sd* the
-// same rows' deviation planes 1..8 (plane a at (a-1)*R); c the node column.
+// same rows' deviations (laid out by dev_index with plane R); c the node column.
 // f_a(x) = w_a rho*(x - e_a) + d_a(x - e_a), or, if x - e_a is solid,
 // f*_opp(a)(x) = w_a rho*(x) + d_opp(a)(x); f_0 = w_0 rho*(x) - sum_b d_b(x).
 // n.g (tau != 1 only) is in raw units.
@@ -566,7 +567,7 @@ __device__ __forceinline__ void pull_dev(const float* __restrict__ s0m, const fl
 }
 
 // Collision in deviation form: stores rho in plane 0 and the raw
-// d*_a = f*_a - w_a rho in planes 1..8 (the equilibrium's deviation part
+// d*_a = f*_a - w_a rho after it (the equilibrium's deviation part
 // w_a rho (3 c + 4.5 c^2 - 1.5 u^2) is formed without its leading 1).
 template <int MODE, typename T>
 __device__ __forceinline__ void collide_dev(const PulledDev& n, const float* pm, const float* pc,
