@@ -299,10 +299,10 @@ void lbm_batch_destroy(lbm_batch *b);
 /* Observables without a context and without any allocation. The paper has
  * no counterpart to this entry point: it exists for callers that cannot
  * allocate device memory at the moment they need the numbers. Examples are
- * code that runs while a CUDA graph is being captured (cudaMalloc is not
- * allowed during capture), a host process working inside a fixed device
- * memory budget that is already spent, and monitoring or checkpoint tools
- * that hold a state in their own buffers and must not touch the allocator.
+ * a host process working inside a fixed device memory budget that is
+ * already spent (an allocation there would fail or evict something else),
+ * and monitoring or checkpoint tools that hold a state in their own buffers
+ * and must not touch the allocator of the application they observe.
  *
  * Inputs (device memory, owned by the caller): d_pops, the post-streaming
  * populations as double[9][ny][nx] (the LBM_POPS layout of lbm_get_field);
@@ -318,9 +318,10 @@ void lbm_batch_destroy(lbm_batch *b);
  * statically (1024 per-CTA partial slots and one result record); every GPU
  * that loads the library holds it until the process exits. Domains of more
  * than 16,777,216 nodes (nx * ny) are rejected with LBM_EINVAL. The first
- * call on a device looks up the array's device address (once per device,
- * with that device current); make that first call before any stream
- * capture. All calls share the array and each call overwrites what it
+ * call in a device's context sets up: it looks up the array's device
+ * address (once per context, normally once per device, with that device
+ * current); make that first call before any stream capture begins on the
+ * device. All calls share the array and each call overwrites what it
  * reads, so nothing needs clearing; calls that overlap on the GPU (other
  * streams, other host threads) race on it and must be serialised by the
  * caller. No cudaMalloc, cudaFree or allocating library routine is called.

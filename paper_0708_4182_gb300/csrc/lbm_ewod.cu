@@ -1174,26 +1174,69 @@ const char* lbm_status_string(int s)
 
 void lbm_destroy(lbm_ctx* c) { delete c; }
 
-// Device address of g_noalloc_scratch on the current device, looked up once
-// per device with that device current. Returns nullptr on failure.
-static double* noalloc_scratch(int dev, cudaError_t* err)
+// Device address of g_noalloc_scratch in the current context, looked up once
+// per context (normally once per device) with that context current. The cache
+// is keyed on the context's unique id, so a context that replaces an earlier
+// one on the same device (after cudaDeviceReset, say) gets its own lookup and
+// never a stale address. The driver calls are reached through the runtime's
+// entry-point query, so the library does not link the driver library.
+// Returns nullptr on failure.
+static double* noalloc_scratch(cudaError_t* err)
 {
-    constexpr int kMaxDevices = 64;
+    using ctx_current_fn = int (*)(void**);
+    using ctx_id_fn = int (*)(void*, unsigned long long*);
+    constexpr int kMaxContexts = 64;
     static std::mutex mu;
-    static double* addr[kMaxDevices] = {};
-    *err = cudaSuccess;
-    if (dev < 0 || dev >= kMaxDevices) {
-        *err = cudaErrorInvalidDevice;
+    static ctx_current_fn ctx_current = nullptr;
+    static ctx_id_fn ctx_id = nullptr;
+    static unsigned long long ids[kMaxContexts] = {};
+    static double* addr[kMaxContexts] = {};
+    static int used = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ctx_current || !ctx_id) {
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        *err = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+        if (*err == cudaSuccess)
+            *err = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (*err != cudaSuccess) return nullptr;
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
+            *err = cudaErrorNotSupported;
+            return nullptr;
+        }
+        ctx_current = reinterpret_cast<ctx_current_fn>(f1);
+        ctx_id = reinterpret_cast<ctx_id_fn>(f2);
+    }
+    void* ctx = nullptr;
+    void* ptr = nullptr;
+    if (ctx_current(&ctx) != 0) {
+        *err = cudaErrorInvalidContext;
         return nullptr;
     }
-    std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
-        void* ptr = nullptr;
+    if (!ctx) {
+        // no context current yet: the runtime's lookup makes the device's
+        // primary context current, then the context is known
         *err = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (*err != cudaSuccess) return nullptr;
-        addr[dev] = static_cast<double*>(ptr);
+        if (ctx_current(&ctx) != 0 || !ctx) {
+            *err = cudaErrorInvalidContext;
+            return nullptr;
+        }
     }
-    return addr[dev];
+    unsigned long long id = 0;
+    if (ctx_id(ctx, &id) != 0) {
+        *err = cudaErrorInvalidContext;
+        return nullptr;
+    }
+    for (int i = 0; i < used; ++i)
+        if (ids[i] == id) return addr[i];
+    if (!ptr) *err = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (*err != cudaSuccess) return nullptr;
+    const int slot = used < kMaxContexts ? used++ : int(id % kMaxContexts);  // reuse a slot past 64 contexts
+    ids[slot] = id;
+    addr[slot] = static_cast<double*>(ptr);
+    return addr[slot];
 }
 
 static thread_local char g_noalloc_err[256];
@@ -1217,9 +1260,8 @@ lbm_status lbm_observables_noalloc(const lbm_params* p, const double* d_pops, co
                  "domain of %lld nodes exceeds the allocation-free limit of %lld nodes", n, kNoAllocMaxNodes);
         return LBM_EINVAL;
     }
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    double* scratch = e == cudaSuccess ? noalloc_scratch(dev, &e) : nullptr;
+    cudaError_t e = cudaSuccess;
+    double* scratch = noalloc_scratch(&e);
     if (!scratch) {
         cudaGetLastError();
         snprintf(g_noalloc_err, sizeof(g_noalloc_err), "scratch address: %s", cudaGetErrorString(e));

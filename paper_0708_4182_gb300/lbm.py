@@ -356,10 +356,13 @@ def lbm_observables_noalloc(params: lbm_params, d_pops: int, d_solid: int, step:
     """Observables of device-resident post-streaming populations (double
     [9][ny][nx]) and mask (uint8 [ny][nx]) without a context and without any
     device allocation: for callers that cannot allocate when they need the
-    numbers (inside CUDA graph capture, within a spent memory budget, in
-    monitoring tools). The library keeps the scratch in a fixed 64 KB static
-    device array shared by all calls, so calls that overlap on the GPU race;
-    domains above 16,777,216 nodes are rejected. Synchronises cuda_stream."""
+    numbers (a process whose device memory budget is spent, monitoring or
+    checkpoint tools that must not touch the application's allocator). The
+    library keeps the scratch in a fixed 64 KB static device array shared by
+    all calls, so calls that overlap on the GPU race; domains above
+    16,777,216 nodes are rejected. The first call in a device's context looks
+    up the array's address and should come before any stream capture on that
+    device. Synchronises cuda_stream."""
     lib = load()
     fn = lib.lbm_observables_noalloc
     fn.restype = ctypes.c_int

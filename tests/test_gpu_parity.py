@@ -51,7 +51,11 @@ def pop_err(f_gpu, f_ref, mask, rho_v=wl.RHO_V):
 
 
 def assert_pops(f_gpu, f_ref, mask):
+    import os
     field, elem, l2 = pop_err(f_gpu, f_ref, mask)
+    # the measured values, for the record (shown with pytest -s)
+    print(f"\npopulation error [{os.environ.get('PYTEST_CURRENT_TEST', '?').split(' ')[0]}]: "
+          f"rel_l2={l2:.3e} field_max={field:.3e} self_max={elem:.3e}")
     assert l2 <= TOL_L2 and field <= TOL_FIELD and elem <= TOL_ELEM, (l2, field, elem)
     assert np.all(f_gpu[:, mask == 1] == 0)
 
