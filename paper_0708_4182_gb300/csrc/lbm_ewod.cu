@@ -1211,7 +1211,7 @@ static double* noalloc_scratch(cudaError_t* err)
     void* ctx = nullptr;
     void* ptr = nullptr;
     if (ctx_current(&ctx) != 0) {
-        *err = cudaErrorInvalidContext;
+        *err = cudaErrorDeviceUninitialized;
         return nullptr;
     }
     if (!ctx) {
@@ -1220,13 +1220,13 @@ static double* noalloc_scratch(cudaError_t* err)
         *err = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (*err != cudaSuccess) return nullptr;
         if (ctx_current(&ctx) != 0 || !ctx) {
-            *err = cudaErrorInvalidContext;
+            *err = cudaErrorDeviceUninitialized;
             return nullptr;
         }
     }
     unsigned long long id = 0;
     if (ctx_id(ctx, &id) != 0) {
-        *err = cudaErrorInvalidContext;
+        *err = cudaErrorDeviceUninitialized;
         return nullptr;
     }
     for (int i = 0; i < used; ++i)
