@@ -72,6 +72,14 @@ typedef enum {
  * Eq. 4 (2G axis, G diagonal), which diverges at G = -0.52. */
 enum { LBM_GREEN_MC = 0, LBM_GREEN_PRINTED = 1 };
 
+/* Direction of the electric force f n of Eq. 9 at a wall-layer node.
+ * LBM_NORMAL_FACES (the default): f per solid axis face, pointing into that
+ * face, summed (a concave corner where two perpendicular faces meet gets f
+ * along each). LBM_NORMAL_UNIT: the same sum of face directions scaled to
+ * unit length (a concave corner gets f along the diagonal). The two differ
+ * only where two perpendicular solid faces meet. */
+enum { LBM_NORMAL_FACES = 0, LBM_NORMAL_UNIT = 1 };
+
 /* Population storage in device memory (arithmetic is FP32 in all forms).
  * LBM_FP32:     the post-collision populations f*_a, FP32 (36 B per node).
  * LBM_FP32_DEV: rho* = sum_a f*_a (FP32) and the deviations
@@ -85,9 +93,9 @@ enum { LBM_GREEN_MC = 0, LBM_GREEN_PRINTED = 1 };
  *               stay below 16); nx must be a multiple of 8. */
 enum { LBM_FP32 = 0, LBM_FP32_DEV = 1, LBM_FP16_DEV = 2, LBM_BF16_DEV = 3 };
 
-/* Field selectors for lbm_set_field / lbm_get_field (LBM_RHO_U_PHYS: set
- * only; LBM_UX_PROFILE: get only). */
-enum { LBM_RHO_U = 0, LBM_POPS = 1, LBM_RHO_U_PHYS = 2, LBM_UX_PROFILE = 3 };
+/* Field selectors for lbm_set_field / lbm_get_field (LBM_RHO_U_PHYS and
+ * LBM_RHO: set only; LBM_UX_PROFILE: get only). */
+enum { LBM_RHO_U = 0, LBM_POPS = 1, LBM_RHO_U_PHYS = 2, LBM_UX_PROFILE = 3, LBM_RHO = 4 };
 
 typedef struct {
     int32_t nx, ny;    /* lattice size; x and y are periodic, walls come
@@ -106,6 +114,7 @@ typedef struct {
                           also reduces the observables of state t, fused into
                           the step kernel (read with lbm_obs_latest); 0: off */
     int32_t tile_rows; /* rows per CTA segment of the step kernel (>= 4), 0 = auto */
+    int32_t normal;    /* LBM_NORMAL_FACES or LBM_NORMAL_UNIT */
 } lbm_params;
 
 typedef struct {
@@ -148,6 +157,9 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const uint8_t *solid, int on_device);
  *            returns (rho, u) up to storage rounding, so a run restarted
  *            from a (rho, u) snapshot does not receive the momentum kick
  *            F/2 per node that LBM_RHO_U gives at interfaces.
+ * LBM_RHO:   data = double[ny][nx], the density of a fluid at rest: every
+ *            fluid node gets f_a = w_a rho (Eq. 3 at u = 0), the same state
+ *            LBM_RHO_U gives with zero velocity, from a third of the data.
  * LBM_POPS:  data = double[9][ny][nx], the populations f_a(x, t) after
  *            streaming (the f of Eq. 2). Values on solid nodes are ignored.
  * Populations are rounded to the storage type. Needs lbm_set_geometry first
@@ -267,8 +279,10 @@ int32_t lbm_batch_tile_rows(const lbm_batch *b);
 lbm_status lbm_batch_autotune(lbm_batch *b, const int32_t *candidates, int32_t n, int32_t steps,
                               int32_t *chosen, double *ms_per_step);
 
-/* Resident CTAs per SM of the persistent grid (1, 2 or 3; default 3, the
- * most the step kernel's shared memory allows). */
+/* Resident CTAs per SM of the persistent grid: 1 up to the most that fit
+ * on one SM (shared memory and registers of the batch's step kernel, from
+ * the CUDA occupancy query at creation; that maximum is the default).
+ * LBM_EINVAL outside that range. */
 lbm_status lbm_batch_set_ctas_per_sm(lbm_batch *b, int32_t ctas);
 int32_t lbm_batch_ctas_per_sm(const lbm_batch *b);
 

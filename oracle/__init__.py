@@ -28,6 +28,8 @@ _LIB_PATH = os.path.join(_BUILD, "liblbm_oracle.so")
 
 GREEN_MC = 0        # Martys-Chen magnitudes: G on axis links, G/2 on diagonals
 GREEN_PRINTED = 1   # weights as printed with Eq. 4: 2G on axis links, G on diagonals
+NORMAL_FACES = 0    # electric force f per solid axis face (a corner gets both faces)
+NORMAL_UNIT = 1     # electric force f along the unit sum of the face directions
 
 # D2Q9 velocity set in the paper's order.
 EX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
@@ -51,6 +53,7 @@ class Params:
     body_fx: float = 0.0
     body_fy: float = 0.0
     green: int = GREEN_MC
+    normal: int = NORMAL_FACES
 
 
 class _CParams(ctypes.Structure):
@@ -59,7 +62,7 @@ class _CParams(ctypes.Structure):
         ("tau", ctypes.c_double), ("G", ctypes.c_double), ("G_wall", ctypes.c_double),
         ("rho0", ctypes.c_double), ("rho_c", ctypes.c_double), ("f_elec", ctypes.c_double),
         ("body_fx", ctypes.c_double), ("body_fy", ctypes.c_double),
-        ("green", ctypes.c_int32),
+        ("green", ctypes.c_int32), ("normal", ctypes.c_int32),
     ]
 
 
@@ -107,7 +110,7 @@ def _load():
 
 def _cp(p: Params) -> _CParams:
     return _CParams(p.nx, p.ny, p.tau, p.G, p.G_wall, p.rho0, p.rho_c, p.f_elec,
-                    p.body_fx, p.body_fy, p.green)
+                    p.body_fx, p.body_fy, p.green, p.normal)
 
 
 def _dptr(a: np.ndarray):

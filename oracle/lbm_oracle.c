@@ -31,7 +31,11 @@
  *   - The electric force acts on fluid nodes with rho >= rho_c that have at
  *     least one solid axis neighbour; per solid axis face it contributes f
  *     along that face's outward direction towards the wall (the electrode), so
- *     a flat bottom wall gives (0,-f) and a concave corner gets both faces.
+ *     a flat bottom wall gives (0,-f) and a concave corner gets both faces
+ *     (normal = ORC_NORMAL_FACES). normal = ORC_NORMAL_UNIT takes the other
+ *     reading of "f n" with n a unit vector: the same sum of face directions
+ *     scaled to length 1, so a concave corner gets f along the diagonal;
+ *     the two readings differ only where two perpendicular faces meet.
  *   - The body force is rho*(body_fx, body_fy) on every fluid node and enters
  *     through the same tau-shift as Eq. 10.
  *   - Walls use half-way link bounce-back (not stated in the paper).
@@ -64,9 +68,11 @@ typedef struct {
     double body_fx;   /* body-force acceleration (channel runs) */
     double body_fy;
     int32_t green;    /* ORC_GREEN_MC or ORC_GREEN_PRINTED */
+    int32_t normal;   /* ORC_NORMAL_FACES or ORC_NORMAL_UNIT (electric-force direction) */
 } orc_params;
 
 enum { ORC_GREEN_MC = 0, ORC_GREEN_PRINTED = 1 };
+enum { ORC_NORMAL_FACES = 0, ORC_NORMAL_UNIT = 1 };
 
 static const int EX[Q9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 static const int EY[Q9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
@@ -173,8 +179,11 @@ static void forces(const orc_params *p, const uint8_t *solid, const double *rho,
                 t[2] = -psi[i] * swx;
                 t[3] = -psi[i] * swy;
                 if (rho[i] >= p->rho_c) {
-                    t[4] = p->f_elec * sex;
-                    t[5] = p->f_elec * sey;
+                    double len = 1.0;
+                    if (p->normal == ORC_NORMAL_UNIT && (sex != 0.0 || sey != 0.0))
+                        len = sqrt(sex * sex + sey * sey);
+                    t[4] = p->f_elec * sex / len;
+                    t[5] = p->f_elec * sey / len;
                 }
                 t[6] = rho[i] * p->body_fx;
                 t[7] = rho[i] * p->body_fy;
@@ -260,6 +269,7 @@ static int check(const orc_params *p)
 {
     if (p->nx < 1 || p->ny < 1) return -1;
     if (!(p->tau > 0.5) || !(p->rho0 > 0)) return -1;
+    if (p->normal != ORC_NORMAL_FACES && p->normal != ORC_NORMAL_UNIT) return -1;
     return 0;
 }
 

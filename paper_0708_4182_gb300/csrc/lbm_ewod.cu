@@ -48,6 +48,7 @@ bool params_valid(const lbm_params* p, const char** why)
     if (!(p->tau > 0.5) || !(p->tau < 1e6)) { *why = "tau must be > 0.5"; return false; }
     if (!(p->rho0 > 0.0)) { *why = "rho0 must be > 0"; return false; }
     if (p->green != LBM_GREEN_MC && p->green != LBM_GREEN_PRINTED) { *why = "unknown green convention"; return false; }
+    if (p->normal != LBM_NORMAL_FACES && p->normal != LBM_NORMAL_UNIT) { *why = "unknown normal reading"; return false; }
     if (p->storage < LBM_FP32 || p->storage > LBM_BF16_DEV) { *why = "unsupported storage"; return false; }
     if ((p->storage == LBM_FP16_DEV || p->storage == LBM_BF16_DEV) && (p->nx % 8) != 0) {
         *why = "16-bit storage needs nx to be a multiple of 8"; return false;
@@ -98,7 +99,7 @@ int auto_tile_rows(int nx, int ny, int storage, int sm_count)
     // the grid has fewer than 4 waves; then even the segments out (same
     // count, heights differing by at most one row) so that no short last
     // segment pays the pipeline start and halo rows for a few rows.
-    const long long slots = 3LL * sm_count;
+    const long long slots = (long long)ctas_of(storage) * sm_count;
     int rows = 64;
     while (rows > 4 && (long long)ctas_x(nx, storage) * ((ny + rows - 1) / rows) < 4 * slots) rows >>= 1;
     const int nseg = (ny + rows - 1) / rows;
@@ -183,10 +184,29 @@ __global__ void feq_kernel(const double* __restrict__ ru, const uint8_t* __restr
     }
 }
 
+// Initial state of a fluid at rest from its density alone (Eq. 3 at u = 0):
+// f_a = w_a rho, evaluated in FP64 and rounded once (the values feq_kernel
+// gives for u = 0); solid nodes get the sentinel.
+__global__ void feq_rest_kernel(const double* __restrict__ rho, const uint8_t* __restrict__ mask,
+                                float* __restrict__ f, Geom g)
+{
+    const long long n = (long long)g.nx * g.ny;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int y = int(i / g.nx), x = int(i % g.nx);
+        const int o = y * g.pitch + x;
+        const bool solid = mask[i] != 0;
+        const double r = rho[i];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) f[a * g.plane + o] = solid ? __uint_as_float(kSolidBits) : float(kW[a] * r);
+    }
+}
+
 // Model constants in FP64 for the force-corrected initial state.
 struct PhysD {
     double rho0, rho_c, f_elec, bfx, bfy;
     double g_axis, g_diag, w_axis, w_diag;
+    int unit_normal;  // LBM_NORMAL_UNIT: the electric force along the unit face normal
 };
 
 __device__ __forceinline__ double psi_in(const double* __restrict__ rho, const uint8_t* __restrict__ mask,
@@ -231,8 +251,10 @@ __global__ void feq_phys_kernel(const double* __restrict__ ru, const uint8_t* __
                           p.w_axis * (sN - sS) + p.w_diag * ((sNE + sNW) - (sSE + sSW));
         double Fx = -psi * gx + rho * p.bfx, Fy = -psi * gy + rho * p.bfy;
         if (rho >= p.rho_c) {
-            Fx += p.f_elec * (sE - sW);
-            Fy += p.f_elec * (sN - sS);
+            const double ex = sE - sW, ey = sN - sS;
+            const double len = (p.unit_normal && ex != 0.0 && ey != 0.0) ? sqrt(2.0) : 1.0;
+            Fx += p.f_elec * ex / len;
+            Fy += p.f_elec * ey / len;
         }
         const double vx = ux - 0.5 * Fx / rho, vy = uy - 0.5 * Fy / rho;
 #pragma unroll
@@ -667,14 +689,27 @@ Phys make_phys(const lbm_params& p)
     h.g_diag = float(kd * p.G);
     h.w_axis = float(ka * p.G_wall);
     h.w_diag = float(kd * p.G_wall);
+    // a corner's two face directions add up to length sqrt 2
+    h.e_corner = p.normal == LBM_NORMAL_UNIT ? float(std::sqrt(0.5)) : 1.f;
     return h;
 }
 
+// The kernel instance: the tau = 1 specialisation unless a step relaxes
+// with tau != 1 (the observing modes never relax).
 template <int MODE, int ST>
 lbm_status launch_step_st(lbm_ctx* c, const float* fin, float* fout, double* fields)
 {
-    step_kernel<MODE, ST><<<c->grid, kThreads, smem_bytes<ST>(), c->stream>>>(fin, fout, c->g, c->ph,
-                                                                               c->partials, fields, c->status);
+    bool t1 = true;
+    if constexpr (MODE == kStep || MODE == kStepObs) {
+        if (c->ph.tau != 1.f) {
+            t1 = false;
+            step_kernel<MODE, ST, false><<<c->grid, threads_of(ST), smem_bytes<ST>(), c->stream>>>(
+                fin, fout, c->g, c->ph, c->partials, fields, c->status);
+        }
+    }
+    if (t1)
+        step_kernel<MODE, ST, true><<<c->grid, threads_of(ST), smem_bytes<ST>(), c->stream>>>(
+            fin, fout, c->g, c->ph, c->partials, fields, c->status);
     return check_launch(c, "step kernel launch");
 }
 
@@ -690,15 +725,19 @@ lbm_status launch_step(lbm_ctx* c, const float* fin, float* fout, double* fields
 }
 
 // Step kernel (plain step, no observables) of a storage form.
-template <int ST> const void* plain_step_ptr() { return reinterpret_cast<const void*>(&step_kernel<kStep, ST>); }
+template <int ST> const void* plain_step_ptr(bool t1)
+{
+    return t1 ? reinterpret_cast<const void*>(&step_kernel<kStep, ST, true>)
+              : reinterpret_cast<const void*>(&step_kernel<kStep, ST, false>);
+}
 
-const void* plain_step_kernel(int storage)
+const void* plain_step_kernel(int storage, bool t1)
 {
     switch (storage) {
-    case LBM_FP32_DEV: return plain_step_ptr<kF32Dev>();
-    case LBM_FP16_DEV: return plain_step_ptr<kF16Dev>();
-    case LBM_BF16_DEV: return plain_step_ptr<kBF16Dev>();
-    default: return plain_step_ptr<kF32>();
+    case LBM_FP32_DEV: return plain_step_ptr<kF32Dev>(t1);
+    case LBM_FP16_DEV: return plain_step_ptr<kF16Dev>(t1);
+    case LBM_BF16_DEV: return plain_step_ptr<kBF16Dev>(t1);
+    default: return plain_step_ptr<kF32>(t1);
     }
 }
 
@@ -732,9 +771,9 @@ lbm_status step_graph(lbm_ctx* c, cudaGraphExec_t* out)
         float* fout = (k & 1) ? c->cur : c->nxt;
         void* args[] = {&fin, &fout, &c->g, &c->ph, &c->partials, &no_fields, &c->status};
         cudaKernelNodeParams kp{};
-        kp.func = const_cast<void*>(plain_step_kernel(c->prm.storage));
+        kp.func = const_cast<void*>(plain_step_kernel(c->prm.storage, c->ph.tau == 1.f));
         kp.gridDim = c->grid;
-        kp.blockDim = dim3(kThreads);
+        kp.blockDim = dim3(threads_of(c->prm.storage));
         kp.sharedMemBytes = static_cast<unsigned>(step_smem(c->prm.storage));
         kp.kernelParams = args;
         cudaGraphNode_t node;
@@ -752,8 +791,14 @@ lbm_status step_graph(lbm_ctx* c, cudaGraphExec_t* out)
 template <int MODE, int ST>
 cudaError_t allow_smem_st()
 {
-    return cudaFuncSetAttribute(step_kernel<MODE, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                int(smem_bytes<ST>()));
+    cudaError_t e = cudaFuncSetAttribute(step_kernel<MODE, ST, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(smem_bytes<ST>()));
+    if constexpr (MODE == kStep || MODE == kStepObs) {
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(step_kernel<MODE, ST, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(smem_bytes<ST>()));
+    }
+    return e;
 }
 
 template <int MODE>
@@ -912,26 +957,29 @@ lbm_status lbm_set_field(lbm_ctx* c, int which, const double* data, int on_devic
     if (!c->has_geometry) return fail(c, LBM_ESTATE, "lbm_set_geometry must come before lbm_set_field");
     const size_t n = size_t(c->g.nx) * c->g.ny;
     lbm_status s;
-    if (which == LBM_RHO_U || which == LBM_RHO_U_PHYS) {
+    if (which == LBM_RHO_U || which == LBM_RHO_U_PHYS || which == LBM_RHO) {
         // (rho, u) -> f_eq into the current buffer -> un-streamed into the
         // spare one, which becomes current; both end with solid sentinels
         const double* src = data;
+        const size_t comps = which == LBM_RHO ? 1 : 3;
         if (!on_device) {
             // (rho, ux, uy) in FP64 fits in the spare population buffer
             double* tmp = reinterpret_cast<double*>(c->nxt);
-            if ((s = check_cuda(c, cudaMemcpyAsync(tmp, data, 3 * n * sizeof(double), cudaMemcpyHostToDevice,
+            if ((s = check_cuda(c, cudaMemcpyAsync(tmp, data, comps * n * sizeof(double), cudaMemcpyHostToDevice,
                                                    c->stream), "field upload")))
                 return s;
             src = tmp;
         }
-        if (which == LBM_RHO_U) {
+        if (which == LBM_RHO) {
+            feq_rest_kernel<<<aux_blocks(n, c->sm_count), kAuxThreads, 0, c->stream>>>(src, c->mask, c->cur, c->g);
+        } else if (which == LBM_RHO_U) {
             feq_kernel<<<aux_blocks(n, c->sm_count), kAuxThreads, 0, c->stream>>>(src, c->mask, c->cur, c->g);
         } else {
             const lbm_params& q = c->prm;
             const double ka = q.green == LBM_GREEN_PRINTED ? 2.0 : 1.0;
             const double kd = q.green == LBM_GREEN_PRINTED ? 1.0 : 0.5;
             const PhysD pd{q.rho0, q.rho_c, q.f_elec, q.body_fx, q.body_fy,
-                           ka * q.G, kd * q.G, ka * q.G_wall, kd * q.G_wall};
+                           ka * q.G, kd * q.G, ka * q.G_wall, kd * q.G_wall, q.normal == LBM_NORMAL_UNIT};
             feq_phys_kernel<<<aux_blocks(n, c->sm_count), kAuxThreads, 0, c->stream>>>(src, c->mask, c->cur, c->g,
                                                                                      pd);
         }
@@ -1308,7 +1356,9 @@ struct lbm_batch {
     cudaStream_t stream = nullptr;
     int sm_count = 0;
     int tile_rows = 0;                   // 0 = each domain's own choice
-    int ctas_per_sm = 3;                 // resident CTAs per SM of the persistent grid (1..3)
+    int ctas_per_sm = 3;                 // resident CTAs per SM of the persistent grid (1..max_ctas)
+    int max_ctas = 3;                    // CTAs of the step kernel instance that fit on one SM
+    bool tau1 = true;                    // every domain relaxes with tau = 1 (the tau = 1 kernel instance)
     // device tables (in the batch's own workspace region)
     DomainDev* d_dom = nullptr;
     int4* d_tiles = nullptr;
@@ -1446,22 +1496,22 @@ lbm_status upload_tables(lbm_batch* b, bool all)
     return LBM_OK;
 }
 
+// t1: every domain of the batch relaxes with tau = 1
 template <int ST>
-const void* batch_kernel_ptr(int mode)
+const void* batch_kernel_ptr(int mode, bool t1)
 {
-    switch (mode) {
-    case kObs: return reinterpret_cast<const void*>(&batch_step_kernel<kObs, ST>);
-    default: return reinterpret_cast<const void*>(&batch_step_kernel<kStep, ST>);
-    }
+    if (mode == kObs) return reinterpret_cast<const void*>(&batch_step_kernel<kObs, ST, true>);
+    return t1 ? reinterpret_cast<const void*>(&batch_step_kernel<kStep, ST, true>)
+              : reinterpret_cast<const void*>(&batch_step_kernel<kStep, ST, false>);
 }
 
-const void* batch_kernel(int storage, int mode)
+const void* batch_kernel(int storage, int mode, bool t1)
 {
     switch (storage) {
-    case LBM_FP32_DEV: return batch_kernel_ptr<kF32Dev>(mode);
-    case LBM_FP16_DEV: return batch_kernel_ptr<kF16Dev>(mode);
-    case LBM_BF16_DEV: return batch_kernel_ptr<kBF16Dev>(mode);
-    default: return batch_kernel_ptr<kF32>(mode);
+    case LBM_FP32_DEV: return batch_kernel_ptr<kF32Dev>(mode, t1);
+    case LBM_FP16_DEV: return batch_kernel_ptr<kF16Dev>(mode, t1);
+    case LBM_BF16_DEV: return batch_kernel_ptr<kBF16Dev>(mode, t1);
+    default: return batch_kernel_ptr<kF32>(mode, t1);
     }
 }
 
@@ -1486,7 +1536,8 @@ lbm_status launch_batch(lbm_batch* b, int mode, int parity)
     if (b->ntiles == 0) return LBM_OK;
     int nt = b->ntiles;
     void* args[] = {&b->d_dom, &b->d_tiles, &nt, &parity, &b->d_status};
-    return bcheck(b, cudaLaunchKernel(batch_kernel(b->storage, mode), dim3(batch_grid(b)), dim3(kThreads), args,
+    return bcheck(b, cudaLaunchKernel(batch_kernel(b->storage, mode, b->tau1), dim3(batch_grid(b)),
+                                      dim3(threads_of(b->storage)), args,
                                       batch_smem(b->storage), b->stream),
                   "batch step launch");
 }
@@ -1507,9 +1558,9 @@ lbm_status batch_graph(lbm_batch* b)
     for (int k = 0; k < 2; ++k) {
         void* args[] = {&b->d_dom, &b->d_tiles, &nt, &parities[k], &b->d_status};
         cudaKernelNodeParams kp{};
-        kp.func = const_cast<void*>(batch_kernel(b->storage, kStep));
+        kp.func = const_cast<void*>(batch_kernel(b->storage, kStep, b->tau1));
         kp.gridDim = dim3(grid);
-        kp.blockDim = dim3(kThreads);
+        kp.blockDim = dim3(threads_of(b->storage));
         kp.sharedMemBytes = unsigned(batch_smem(b->storage));
         kp.kernelParams = args;
         cudaGraphNode_t node;
@@ -1633,11 +1684,21 @@ lbm_status lbm_batch_create(const lbm_params* params, int32_t count, void* d_wor
     b->d_want = ws + L.off_want;
     b->max_tiles = L.max_tiles;
     cudaError_t e = cudaSuccess;
+    for (int d = 0; d < count; ++d)
+        if (b->ctx[d]->ph.tau != 1.f) b->tau1 = false;
     for (int st = 0; st < 4 && e == cudaSuccess; ++st) {
-        e = cudaFuncSetAttribute(batch_kernel(st, kStep), cudaFuncAttributeMaxDynamicSharedMemorySize, int(batch_smem(st)));
+        for (int t1 = 0; t1 < 2 && e == cudaSuccess; ++t1)
+            e = cudaFuncSetAttribute(batch_kernel(st, kStep, t1 != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(batch_smem(st)));
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(batch_kernel(st, kObs), cudaFuncAttributeMaxDynamicSharedMemorySize, int(batch_smem(st)));
+            e = cudaFuncSetAttribute(batch_kernel(st, kObs, true), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(batch_smem(st)));
     }
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->max_ctas, batch_kernel(b->storage, kStep, b->tau1),
+                                                          threads_of(b->storage), batch_smem(b->storage));
+    if (e == cudaSuccess && b->max_ctas < 1) e = cudaErrorInvalidConfiguration;
+    b->ctas_per_sm = b->max_ctas;
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -1805,7 +1866,8 @@ lbm_status lbm_batch_autotune(lbm_batch* b, const int32_t* candidates, int32_t n
 lbm_status lbm_batch_set_ctas_per_sm(lbm_batch* b, int32_t ctas)
 {
     if (!b) return LBM_EINVAL;
-    if (ctas < 1 || ctas > 3) return bfail(b, LBM_EINVAL, "ctas_per_sm must be 1, 2 or 3");
+    if (ctas < 1 || ctas > b->max_ctas)
+        return bfail(b, LBM_EINVAL, "ctas_per_sm must be 1 .. %d for this batch", b->max_ctas);
     b->ctas_per_sm = ctas;  // the graph is rebuilt when the grid changes
     return LBM_OK;
 }
@@ -1821,7 +1883,8 @@ lbm_status lbm_batch_autotune_grid(lbm_batch* b, const int32_t* rows, int32_t nr
     if (!rows || nrows < 1 || !ctas || nctas < 1 || steps < 1 || !chosen_rows || !chosen_ctas)
         return bfail(b, LBM_EINVAL, "bad arguments");
     for (int j = 0; j < nctas; ++j)
-        if (ctas[j] < 1 || ctas[j] > 3) return bfail(b, LBM_EINVAL, "ctas_per_sm must be 1, 2 or 3");
+        if (ctas[j] < 1 || ctas[j] > b->max_ctas)
+            return bfail(b, LBM_EINVAL, "ctas_per_sm must be 1 .. %d for this batch", b->max_ctas);
     double best = 1e300;
     int32_t best_rows = b->tile_rows, best_ctas = b->ctas_per_sm;
     std::vector<double> ms(nrows);

@@ -60,16 +60,51 @@
 namespace lbm {
 
 constexpr uint32_t kSolidBits = 0xFFBADA55u;  // a NaN payload arithmetic never produces
-constexpr int kW = 256;                        // consumer threads per CTA (one pulled column each)
-constexpr int kConsumerWarps = kW / 32;
-constexpr int kThreads = kW + 32;              // consumers + one producer warp
+constexpr int kW = 256;                        // strip width of the 32-bit forms; consumer threads of the 16-bit forms
 constexpr int kRowLen = kW + 8;                // staged columns per plane row (window + alignment)
-constexpr int kPsiStride = kW + 2;             // floats per psi ring row
-constexpr int kStages = 6;                     // staging ring depth (rows)
+constexpr int kPsiStride = kW + 4;             // floats per psi ring row
 constexpr int kPartialStride = 8;              // doubles per CTA in the partials array
 constexpr uint32_t kWaitLimit = 1u << 18;      // try_wait rounds before giving up (about 1 s on a GB300)
 
 enum Storage { kF32 = 0, kF32Dev = 1, kF16Dev = 2, kBF16Dev = 3 };
+
+// Staging ring depth (rows) and resident CTAs per SM the launch bounds aim
+// at. The 16-bit forms (288 threads): 6 and 3. The 32-bit forms (160
+// threads, a pair of nodes per thread): LBM_STAGES_F32 / LBM_CTAS_F32 and
+// LBM_STAGES_F32DEV / LBM_CTAS_F32DEV for the tau = 1 instances, whose
+// register needs are lower; the tau != 1 instances, and the persistent
+// batch kernel of the FP32 deviation form (which spills at 4), aim at 3.
+// Shared memory and registers must allow that many CTAs. Measured at
+// 16384x4096 (GLUPS, FP32 / FP32 deviations / batch FP32 / batch FP32
+// deviations): 6 stages x 3 CTAs 89.4 / 85.9 / 80.5 / 72.8; FP32 4 x 5 and
+// deviations 5 x 4: 89.8 / 89.7 / 81.4 / 55.6 (spilling).
+#ifndef LBM_STAGES_F32
+#define LBM_STAGES_F32 4
+#endif
+#ifndef LBM_CTAS_F32
+#define LBM_CTAS_F32 5
+#endif
+#ifndef LBM_STAGES_F32DEV
+#define LBM_STAGES_F32DEV 5
+#endif
+#ifndef LBM_CTAS_F32DEV
+#define LBM_CTAS_F32DEV 4
+#endif
+__host__ __device__ constexpr int stages_of(int st)
+{
+    return st == kF32 ? LBM_STAGES_F32 : st == kF32Dev ? LBM_STAGES_F32DEV : 6;
+}
+__host__ __device__ constexpr int ctas_of(int st, bool t1 = true)
+{
+    return st == kF32 ? (t1 ? LBM_CTAS_F32 : 3) : st == kF32Dev ? (t1 ? LBM_CTAS_F32DEV : 3) : 3;
+}
+__host__ __device__ constexpr int batch_ctas_of(int st, bool t1 = true) { return st == kF32Dev ? 3 : ctas_of(st, t1); }
+// the single-domain kernel of a mode: the observing modes keep their
+// reduction state too and aim at one CTA less (no spills)
+__host__ __device__ constexpr int step_ctas_of(int mode, int st, bool t1)
+{
+    return mode == 0 ? ctas_of(st, t1) : (ctas_of(st, t1) > 3 ? ctas_of(st, t1) - 1 : ctas_of(st, t1));
+}
 
 // T: type of the 8 values after plane 0 (populations or deviations); align:
 // columns per 16 bytes of the narrowest plane (every staging copy starts and
@@ -83,6 +118,12 @@ template <> struct StoreT<kBF16Dev> { using T = __nv_bfloat16; static constexpr 
 
 // Columns a CTA collides: kW, or kW - 2 where neighbouring strips overlap.
 __host__ __device__ constexpr int strip_cols(int st) { return (st == kF16Dev || st == kBF16Dev) ? kW - 2 : kW; }
+
+// Consumer threads per CTA: the 32-bit forms give each thread a pair of
+// neighbouring columns (packed two-lane FP32 arithmetic, see run_tile), the
+// 16-bit forms one column. One producer warp comes on top.
+__host__ __device__ constexpr int consumers(int st) { return (st == kF16Dev || st == kBF16Dev) ? kW : kW / 2; }
+__host__ __device__ constexpr int threads_of(int st) { return consumers(st) + 32; }
 
 // Element index of deviation a (1..8) of the node at o = y * pitch + x among
 // the deviation values that follow plane 0 (plane = ny * pitch): FP32
@@ -101,7 +142,7 @@ template <int ST> __host__ __device__ constexpr size_t stage_bytes()
 }
 template <int ST> __host__ __device__ constexpr size_t smem_bytes()
 {
-    return kStages * (stage_bytes<ST>() + 2 * sizeof(uint64_t)) + 4 * kPsiStride * sizeof(float) + 128;
+    return stages_of(ST) * (stage_bytes<ST>() + 2 * sizeof(uint64_t)) + 4 * kPsiStride * sizeof(float) + 128;
 }
 // bytes of one node's state in global memory (plane 0 + the other 8 values)
 template <int ST> __host__ __device__ constexpr int node_bytes() { return 4 + 8 * int(sizeof(typename StoreT<ST>::T)); }
@@ -137,6 +178,7 @@ struct Phys {
     float bfx, bfy;
     float g_axis, g_diag;  // G_a of Eq. 4 on |e| = 1 and |e| = sqrt 2 links
     float w_axis, w_diag;  // W_a of Eq. 6
+    float e_corner;        // electric force scale where two solid faces meet (1 or 1/sqrt 2)
 };
 
 enum Mode { kStep = 0, kStepObs = 1, kObs = 2, kFields = 3 };
@@ -243,10 +285,28 @@ __device__ __forceinline__ float div_corrected(float n, float d, float r)
     return fmaf(e, r, q0);
 }
 
-// The consumer warps (once per staged row, and the observables reduction).
-__device__ __forceinline__ void consumer_sync()
+// The NC consumer threads (once per staged row, and the observables reduction).
+template <int NC> __device__ __forceinline__ void consumer_sync()
 {
-    asm volatile("bar.sync 1, %0;" ::"n"(kW) : "memory");
+    asm volatile("bar.sync 1, %0;" ::"n"(NC) : "memory");
+}
+
+// ------------------------------------------------------------------ two-lane FP32
+// A float2 holds one value of each of two neighbouring nodes (lane x: the
+// left node A, lane y: the right node B). These map to Blackwell's paired
+// FP32 instructions (add/mul/fma .rn on f32x2): each lane is rounded exactly
+// as the scalar operation would be, and one instruction serves both nodes.
+__device__ __forceinline__ float2 splat(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b as fma(b, -1, a): the product is exact, so this is the rounded difference
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+__device__ __forceinline__ float lane_of(const float2& v, int k) { return k == 0 ? v.x : v.y; }
+__device__ __forceinline__ void set_lane(float2& v, int k, float a)
+{
+    if (k == 0) v.x = a; else v.y = a;
 }
 
 // ------------------------------------------------------------------ node math
@@ -365,8 +425,10 @@ __device__ __forceinline__ void node_force(const N& n, const float* pm, const fl
         Fy = -psi * (sgy + swy);
         // electric force f n on the conductive single layer next to a wall
         if (n.rho >= p.rho_c) {
-            Fx += p.f_elec * (sE - sW);
-            Fy += p.f_elec * (sN - sS);
+            const float ex = sE - sW, ey = sN - sS;
+            const float fe = (ex != 0.f && ey != 0.f) ? p.f_elec * p.e_corner : p.f_elec;
+            Fx += fe * ex;
+            Fy += fe * ey;
         }
     }
     // body force on every fluid node
@@ -569,7 +631,7 @@ __device__ __forceinline__ void pull_dev(const float* __restrict__ s0m, const fl
 // Collision in deviation form: stores rho in plane 0 and the raw
 // d*_a = f*_a - w_a rho after it (the equilibrium's deviation part
 // w_a rho (3 c + 4.5 c^2 - 1.5 u^2) is formed without its leading 1).
-template <int MODE, typename T>
+template <int MODE, typename T, bool T1>
 __device__ __forceinline__ void collide_dev(const PulledDev& n, const float* pm, const float* pc,
                                             const float* pp, int t, const Phys& p, const Geom& g,
                                             float* __restrict__ fout0, T* __restrict__ foutd,
@@ -599,7 +661,7 @@ __device__ __forceinline__ void collide_dev(const PulledDev& n, const float* pm,
         fout0[o] = n.rho;
         if constexpr (sizeof(T) == 2) {
             float v[9];
-            if (p.tau == 1.f) {
+            if (T1 || p.tau == 1.f) {
 #pragma unroll
                 for (int a = 1; a < 9; ++a) v[a] = dq[a];
             } else {
@@ -618,7 +680,7 @@ __device__ __forceinline__ void collide_dev(const PulledDev& n, const float* pm,
                 w[k] = uint32_t(bl) | (uint32_t(bh) << 16);
             }
             *reinterpret_cast<uint4*>(foutd + size_t(o) * 8) = make_uint4(w[0], w[1], w[2], w[3]);
-        } else if (p.tau == 1.f) {
+        } else if (T1 || p.tau == 1.f) {
 #pragma unroll
             for (int a = 1; a < 9; ++a) foutd[(a - 1) * g.plane + o] = from_raw<T>(dq[a]);
         } else {
@@ -628,6 +690,343 @@ __device__ __forceinline__ void collide_dev(const PulledDev& n, const float* pm,
         }
     }
     if constexpr (MODE != kStep) node_observe<MODE>(n.rho, rinv, n.jx, n.jy, Fx, Fy, g, fields, x, r, acc);
+}
+
+// ------------------------------------------------------------------ node pairs (32-bit forms)
+//
+// A consumer thread of the 32-bit forms owns two neighbouring columns, A at
+// staged column c (even) and B at c + 1, and carries their arithmetic in the
+// two lanes of float2 values. Each node's arithmetic is the single-node
+// arithmetic above, operation for operation; only the sources that lie on
+// 8-byte boundaries come in one 64-bit shared-memory load (plane 0, 2 and 4
+// and the node's own values), and both nodes store with one 64-bit store per
+// plane.
+
+struct Pulled2 {
+    float2 f[9];
+    float2 rho, jx, jy;
+    uint32_t sb[2];  // per lane: bit a set <=> the pull source x - e_a is solid
+    bool solid[2];   // per lane: solid node (B also when it lies past the pulled columns)
+};
+
+struct PulledDev2 {
+    float2 rho, jx, jy;
+    float2 g[9];     // f_a - w_a rho (a = 1..8, only with tau != 1)
+    uint32_t sb[2];
+    bool solid[2];
+};
+
+// Plain pull of the pair (c, c + 1) from the ring rows sm, sc, sp (see
+// pull_smem); b_ok = false marks lane B as unused.
+__device__ __forceinline__ void pull_pair(const float* __restrict__ sm, const float* __restrict__ sc,
+                                          const float* __restrict__ sp, int c, bool b_ok, Pulled2& n)
+{
+    constexpr int R = kRowLen;
+    const float2 v0 = ld2(sc + c);
+    n.solid[0] = is_solid(v0.x);
+    n.solid[1] = !b_ok || is_solid(v0.y);
+    n.sb[0] = n.sb[1] = 0;
+    if (n.solid[0] && n.solid[1]) {
+        n.rho = n.jx = n.jy = splat(0.f);
+        return;
+    }
+    float2 v[9];
+    v[0] = v0;
+    v[1] = make_float2(sc[1 * R + c - 1], sc[1 * R + c]);      // e1: source (x-1, y)
+    v[2] = ld2(sm + 2 * R + c);                                 // e2: source (x, y-1)
+    v[3] = make_float2(sc[3 * R + c + 1], sc[3 * R + c + 2]);  // e3: source (x+1, y)
+    v[4] = ld2(sp + 4 * R + c);                                 // e4: source (x, y+1)
+    v[5] = make_float2(sm[5 * R + c - 1], sm[5 * R + c]);      // e5: source (x-1, y-1)
+    v[6] = make_float2(sm[6 * R + c + 1], sm[6 * R + c + 2]);  // e6: source (x+1, y-1)
+    v[7] = make_float2(sp[7 * R + c + 1], sp[7 * R + c + 2]);  // e7: source (x+1, y+1)
+    v[8] = make_float2(sp[8 * R + c - 1], sp[8 * R + c]);      // e8: source (x-1, y+1)
+    auto density = [&v]() {
+        return add2(add2(add2(v[0], add2(v[1], v[3])), add2(v[2], v[4])), add2(add2(v[5], v[7]), add2(v[6], v[8])));
+    };
+    float2 rho = density();
+    const bool nan_a = !n.solid[0] && isnan(rho.x), nan_b = !n.solid[1] && isnan(rho.y);
+    if (nan_a || nan_b) {
+        constexpr int opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+#pragma unroll
+        for (int a = 1; a < 9; ++a) {
+            if (nan_a && is_solid(v[a].x)) {
+                n.sb[0] |= 1u << a;
+                v[a].x = sc[opp[a] * R + c];  // half-way bounce-back
+            }
+            if (nan_b && is_solid(v[a].y)) {
+                n.sb[1] |= 1u << a;
+                v[a].y = sc[opp[a] * R + c + 1];
+            }
+        }
+        rho = density();
+    }
+#pragma unroll
+    for (int a = 0; a < 9; ++a) n.f[a] = v[a];
+    n.rho = rho;
+    n.jx = add2(add2(sub2(v[1], v[3]), sub2(v[5], v[7])), sub2(v[8], v[6]));
+    n.jy = add2(add2(sub2(v[2], v[4]), sub2(v[5], v[7])), sub2(v[6], v[8]));
+}
+
+// Deviation-form pull of the pair (FP32 deviations; see pull_dev). The
+// node's own deviations are one 64-bit load per plane; B's east source is
+// A's own d_1 and A's west source is B's own d_3.
+__device__ __forceinline__ void pull_dev_pair(const float* __restrict__ s0m, const float* __restrict__ s0c,
+                                              const float* __restrict__ s0p, const float* __restrict__ sdm,
+                                              const float* __restrict__ sdc, const float* __restrict__ sdp, int c,
+                                              bool b_ok, bool need_g, PulledDev2& n)
+{
+    constexpr int R = kRowLen;
+    const float2 r0 = ld2(s0c + c);
+    n.solid[0] = is_solid(r0.x);
+    n.solid[1] = !b_ok || is_solid(r0.y);
+    n.sb[0] = n.sb[1] = 0;
+    if (n.solid[0] && n.solid[1]) {
+        n.rho = n.jx = n.jy = splat(0.f);
+        return;
+    }
+    const float2 mM = ld2(s0m + c), pM = ld2(s0p + c);
+    float2 rs[9], d[9], own[9];
+    rs[1] = make_float2(s0c[c - 1], r0.x);
+    rs[2] = mM;
+    rs[3] = make_float2(r0.y, s0c[c + 2]);
+    rs[4] = pM;
+    rs[5] = make_float2(s0m[c - 1], mM.x);
+    rs[6] = make_float2(mM.y, s0m[c + 2]);
+    rs[7] = make_float2(pM.y, s0p[c + 2]);
+    rs[8] = make_float2(s0p[c - 1], pM.x);
+#pragma unroll
+    for (int b = 1; b < 9; ++b) own[b] = ld2(sdc + (b - 1) * R + c);
+    d[1] = make_float2(sdc[0 * R + c - 1], own[1].x);
+    d[2] = ld2(sdm + 1 * R + c);
+    d[3] = make_float2(own[3].y, sdc[2 * R + c + 2]);
+    d[4] = ld2(sdp + 3 * R + c);
+    d[5] = make_float2(sdm[4 * R + c - 1], sdm[4 * R + c]);
+    d[6] = make_float2(sdm[5 * R + c + 1], sdm[5 * R + c + 2]);
+    d[7] = make_float2(sdp[6 * R + c + 1], sdp[6 * R + c + 2]);
+    d[8] = make_float2(sdp[7 * R + c - 1], sdp[7 * R + c]);
+    auto qsum = [&rs, r0](float2& q1, float2& q2) {
+        q1 = add2(add2(sub2(rs[1], r0), sub2(rs[3], r0)), add2(sub2(rs[2], r0), sub2(rs[4], r0)));
+        q2 = add2(add2(sub2(rs[5], r0), sub2(rs[7], r0)), add2(sub2(rs[6], r0), sub2(rs[8], r0)));
+    };
+    float2 q1, q2;
+    qsum(q1, q2);
+    const bool nan_a = !n.solid[0] && isnan(q1.x + q2.x), nan_b = !n.solid[1] && isnan(q1.y + q2.y);
+    if (nan_a || nan_b) {
+        constexpr int opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+#pragma unroll
+        for (int a = 1; a < 9; ++a) {
+            if (nan_a && is_solid(rs[a].x)) {  // half-way bounce-back: the node's own f*_opp(a)
+                n.sb[0] |= 1u << a;
+                rs[a].x = r0.x;
+                d[a].x = own[opp[a]].x;
+            }
+            if (nan_b && is_solid(rs[a].y)) {
+                n.sb[1] |= 1u << a;
+                rs[a].y = r0.y;
+                d[a].y = own[opp[a]].y;
+            }
+        }
+        qsum(q1, q2);
+    }
+    const float2 w1 = splat(1.f / 9.f), w2 = splat(1.f / 36.f);
+    const float2 dsrc = add2(add2(add2(d[1], d[3]), add2(d[2], d[4])), add2(add2(d[5], d[7]), add2(d[6], d[8])));
+    const float2 down =
+        add2(add2(add2(own[1], own[3]), add2(own[2], own[4])), add2(add2(own[5], own[7]), add2(own[6], own[8])));
+    const float2 drho = fma2(w1, q1, fma2(w2, q2, sub2(dsrc, down)));
+    n.rho = add2(r0, drho);
+    n.jx = fma2(w1, sub2(rs[1], rs[3]),
+                fma2(w2, add2(sub2(rs[5], rs[7]), sub2(rs[8], rs[6])),
+                     add2(add2(sub2(d[1], d[3]), sub2(d[5], d[7])), sub2(d[8], d[6]))));
+    n.jy = fma2(w1, sub2(rs[2], rs[4]),
+                fma2(w2, add2(sub2(rs[5], rs[7]), sub2(rs[6], rs[8])),
+                     add2(add2(sub2(d[2], d[4]), sub2(d[5], d[7])), sub2(d[6], d[8]))));
+    if (need_g) {
+#pragma unroll
+        for (int a = 1; a < 9; ++a) n.g[a] = fma2(a <= 4 ? w1 : w2, sub2(sub2(rs[a], r0), drho), d[a]);
+    }
+    n.g[0] = splat(0.f);
+}
+
+// Total force on the pair (see node_force): psi ring rows pm, pc, pp with
+// node A at ring column t (even) and B at t + 1.
+__device__ __forceinline__ void node_force2(float2 rho, const uint32_t (&sb)[2], const float* pm, const float* pc,
+                                            const float* pp, int t, const Phys& p, float2& Fx_out, float2& Fy_out)
+{
+    const float2 cM = ld2(pc + t), mM = ld2(pm + t), pM = ld2(pp + t);
+    const float cL = pc[t - 1], cR = pc[t + 2], mL = pm[t - 1], mR = pm[t + 2], pL = pp[t - 1], pR = pp[t + 2];
+    // lane A's left/right neighbours are (L, M.y), lane B's (M.x, R)
+    const float2 dxc = make_float2(cM.y - cL, cR - cM.x);
+    const float2 dxp = make_float2(pM.y - pL, pR - pM.x), dxm = make_float2(mM.y - mL, mR - mM.x);
+    const float2 sxp = make_float2(pM.y + pL, pR + pM.x), sxm = make_float2(mM.y + mL, mR + mM.x);
+    // Eq. 5: -sum_a G_a psi(x+e_a) e_a, the sign carried by the constants
+    // (round to nearest is symmetric, so this is exactly the negated sum)
+    const float2 nsgx = fma2(splat(-p.g_axis), dxc, mul2(splat(-p.g_diag), add2(dxp, dxm)));
+    const float2 nsgy = fma2(splat(-p.g_axis), sub2(pM, mM), mul2(splat(-p.g_diag), sub2(sxp, sxm)));
+    const float2 psi = cM;
+    float2 Fx = mul2(psi, nsgx), Fy = mul2(psi, nsgy);
+    if ((sb[0] | sb[1]) != 0) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const uint32_t b = sb[k];
+            if (b == 0) continue;
+            const float sE = (b >> 3) & 1, sW = (b >> 1) & 1;
+            const float sN = (b >> 4) & 1, sS = (b >> 2) & 1;
+            const float sNE = (b >> 7) & 1, sNW = (b >> 8) & 1;
+            const float sSW = (b >> 5) & 1, sSE = (b >> 6) & 1;
+            // Eq. 6: sum_a W_a S(x+e_a) e_a
+            const float swx = p.w_axis * (sE - sW) + p.w_diag * ((sNE - sNW) + (sSE - sSW));
+            const float swy = p.w_axis * (sN - sS) + p.w_diag * ((sNE + sNW) - (sSE + sSW));
+            const float ps = lane_of(psi, k);
+            float fx = ps * (lane_of(nsgx, k) - swx);
+            float fy = ps * (lane_of(nsgy, k) - swy);
+            // electric force f n on the conductive single layer next to a wall
+            if (lane_of(rho, k) >= p.rho_c) {
+                const float ex = sE - sW, ey = sN - sS;
+                const float fe = (ex != 0.f && ey != 0.f) ? p.f_elec * p.e_corner : p.f_elec;
+                fx += fe * ex;
+                fy += fe * ey;
+            }
+            set_lane(Fx, k, fx);
+            set_lane(Fy, k, fy);
+        }
+    }
+    // body force on every fluid node
+    Fx_out = fma2(rho, splat(p.bfx), Fx);
+    Fy_out = fma2(rho, splat(p.bfy), Fy);
+}
+
+// n / d by the corrected reciprocal (div_corrected) in both lanes; nd = -d.
+__device__ __forceinline__ float2 div2(float2 n, float2 nd, float2 r)
+{
+    const float2 q0 = mul2(n, r);
+    const float2 e = fma2(q0, nd, n);
+    return fma2(e, r, q0);
+}
+
+// Observables / fields epilogue of the lanes that are collided fluid nodes.
+template <int MODE>
+__device__ __forceinline__ void observe_pair(const float2& rho, const float2& rinv, const float2& jx,
+                                             const float2& jy, const float2& Fx, const float2& Fy, const bool (&use)[2],
+                                             const Geom& g, double* __restrict__ fields, int x, int r, ObsAcc& acc)
+{
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+        if (use[k])
+            node_observe<MODE>(lane_of(rho, k), lane_of(rinv, k), lane_of(jx, k), lane_of(jy, k), lane_of(Fx, k),
+                               lane_of(Fy, k), g, fields, x + k, r, acc);
+}
+
+// Shifted velocity (Eq. 10) of the pair from its force; rinv = 1/rho (approx).
+__device__ __forceinline__ void shifted_velocity(const float2& rho, const float2& jx, const float2& jy,
+                                                 const float2& Fx, const float2& Fy, const float2& rinv,
+                                                 const Phys& p, float2& ux, float2& uy)
+{
+    const float2 nrho = make_float2(-rho.x, -rho.y);
+    ux = div2(fma2(splat(p.tau), Fx, jx), nrho, rinv);
+    uy = div2(fma2(splat(p.tau), Fy, jy), nrho, rinv);
+}
+
+// Forces, velocity shift, collision and store of a pair in plain storage
+// (see collide_node); col[k]: lane k is a fluid node this CTA collides. Lane
+// A is column x. Both lanes collided and fluid: one 64-bit store per plane.
+template <int MODE, bool T1>
+__device__ __forceinline__ void collide_pair(const Pulled2& n, const bool (&col)[2], const float* pm, const float* pc,
+                                             const float* pp, int t, const Phys& p, const Geom& g,
+                                             float* __restrict__ fout, double* __restrict__ fields, int x, int r,
+                                             ObsAcc& acc)
+{
+    float2 Fx, Fy;
+    node_force2(n.rho, n.sb, pm, pc, pp, t, p, Fx, Fy);
+    const float2 rinv = make_float2(rcp_approx(n.rho.x), rcp_approx(n.rho.y));
+    if constexpr (MODE == kStep || MODE == kStepObs) {
+        float2 ux, uy;
+        shifted_velocity(n.rho, n.jx, n.jy, Fx, Fy, rinv, p, ux, uy);
+        const float2 om = fma2(splat(-1.5f), fma2(ux, ux, mul2(uy, uy)), splat(1.f));
+        const float2 r9 = div2(n.rho, splat(-9.f), splat(1.f / 9.f));
+        const float2 w0r = mul2(splat(4.f), r9), w2r = mul2(splat(0.25f), r9);
+        const float2 d5 = add2(ux, uy), d6 = sub2(uy, ux);
+        // f_eq_a = w_a rho (1 + 3 c + 4.5 c^2 - 1.5 u^2) with c = +-(e_a . u):
+        // (-c)(4.5(-c) + 3) = c (4.5 c - 3) exactly
+        auto polyp = [om](float2 c) { return fma2(c, fma2(splat(4.5f), c, splat(3.f)), om); };
+        auto polym = [om](float2 c) { return fma2(c, fma2(splat(4.5f), c, splat(-3.f)), om); };
+        float2 fs[9];
+        fs[0] = mul2(w0r, om);
+        fs[1] = mul2(r9, polyp(ux));
+        fs[2] = mul2(r9, polyp(uy));
+        fs[3] = mul2(r9, polym(ux));
+        fs[4] = mul2(r9, polym(uy));
+        fs[5] = mul2(w2r, polyp(d5));
+        fs[6] = mul2(w2r, polyp(d6));
+        fs[7] = mul2(w2r, polym(d5));
+        fs[8] = mul2(w2r, polym(d6));
+        if (!T1 && p.tau != 1.f) {
+#pragma unroll
+            for (int a = 0; a < 9; ++a) fs[a] = fma2(sub2(fs[a], n.f[a]), splat(p.inv_tau), n.f[a]);
+        }
+        float* o = fout + r * g.pitch + x;
+        if (col[0] && col[1]) {
+#pragma unroll
+            for (int a = 0; a < 9; ++a) *reinterpret_cast<float2*>(o + a * g.plane) = fs[a];
+        } else {
+#pragma unroll
+            for (int a = 0; a < 9; ++a) {
+                if (col[0]) o[a * g.plane] = fs[a].x;
+                if (col[1]) o[a * g.plane + 1] = fs[a].y;
+            }
+        }
+    }
+    if constexpr (MODE != kStep) observe_pair<MODE>(n.rho, rinv, n.jx, n.jy, Fx, Fy, col, g, fields, x, r, acc);
+}
+
+// The same in FP32 deviation storage (see collide_dev).
+template <int MODE, bool T1>
+__device__ __forceinline__ void collide_dev_pair(const PulledDev2& n, const bool (&col)[2], const float* pm,
+                                                 const float* pc, const float* pp, int t, const Phys& p,
+                                                 const Geom& g, float* __restrict__ fout0,
+                                                 float* __restrict__ foutd, double* __restrict__ fields, int x,
+                                                 int r, ObsAcc& acc)
+{
+    float2 Fx, Fy;
+    node_force2(n.rho, n.sb, pm, pc, pp, t, p, Fx, Fy);
+    const float2 rinv = make_float2(rcp_approx(n.rho.x), rcp_approx(n.rho.y));
+    if constexpr (MODE == kStep || MODE == kStepObs) {
+        float2 ux, uy;
+        shifted_velocity(n.rho, n.jx, n.jy, Fx, Fy, rinv, p, ux, uy);
+        const float2 nusq = mul2(splat(-1.5f), fma2(ux, ux, mul2(uy, uy)));
+        const float2 w1r = div2(n.rho, splat(-9.f), splat(1.f / 9.f));
+        const float2 w2r = mul2(splat(0.25f), w1r);
+        const float2 d5 = add2(ux, uy), d6 = sub2(uy, ux);
+        auto dpolyp = [nusq](float2 c) { return fma2(c, fma2(splat(4.5f), c, splat(3.f)), nusq); };
+        auto dpolym = [nusq](float2 c) { return fma2(c, fma2(splat(4.5f), c, splat(-3.f)), nusq); };
+        float2 dq[9];
+        dq[1] = mul2(w1r, dpolyp(ux));
+        dq[2] = mul2(w1r, dpolyp(uy));
+        dq[3] = mul2(w1r, dpolym(ux));
+        dq[4] = mul2(w1r, dpolym(uy));
+        dq[5] = mul2(w2r, dpolyp(d5));
+        dq[6] = mul2(w2r, dpolyp(d6));
+        dq[7] = mul2(w2r, dpolym(d5));
+        dq[8] = mul2(w2r, dpolym(d6));
+        if (!T1 && p.tau != 1.f) {
+#pragma unroll
+            for (int a = 1; a < 9; ++a) dq[a] = fma2(sub2(dq[a], n.g[a]), splat(p.inv_tau), n.g[a]);
+        }
+        const int o = r * g.pitch + x;
+        if (col[0] && col[1]) {
+            *reinterpret_cast<float2*>(fout0 + o) = n.rho;
+#pragma unroll
+            for (int a = 1; a < 9; ++a) *reinterpret_cast<float2*>(foutd + (a - 1) * g.plane + o) = dq[a];
+        } else {
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if (!col[k]) continue;
+                fout0[o + k] = lane_of(n.rho, k);
+#pragma unroll
+                for (int a = 1; a < 9; ++a) foutd[(a - 1) * g.plane + o + k] = lane_of(dq[a], k);
+            }
+        }
+    }
+    if constexpr (MODE != kStep) observe_pair<MODE>(n.rho, rinv, n.jx, n.jy, Fx, Fy, col, g, fields, x, r, acc);
 }
 
 // ------------------------------------------------------------------ kernel
@@ -654,13 +1053,14 @@ __device__ __forceinline__ void mbar_inval(uint64_t* bar)
 //    and all consumer warps do the same work; threads 1 .. nint collide.
 //    Neighbouring strips overlap by two pulled columns.
 // In both the producer warp only stages rows, running ahead of the consumers.
-template <int MODE, int ST>
+template <int MODE, int ST, bool T1>
 __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* __restrict__ fout, const Geom& g,
                                          const Phys& p, double* __restrict__ partials,
                                          double* __restrict__ fields, int* __restrict__ err, int bx, int by,
                                          int slot, unsigned char* smem_raw)
 {
     using T = typename StoreT<ST>::T;
+    constexpr int kStages = stages_of(ST);
     constexpr int A = StoreT<ST>::align;
     constexpr int P = StoreT<ST>::overlap;
     constexpr int R = kRowLen;
@@ -694,7 +1094,7 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 32);               // 32 producer-lane arrivals + tx bytes
-            mbar_init(&empty[s], kConsumerWarps);  // one arrival per consumer warp
+            mbar_init(&empty[s], consumers(ST) / 32);  // one arrival per consumer warp
         }
         fence_mbar_init();
     }
@@ -712,6 +1112,10 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
     };
 
     using PT = std::conditional_t<ST == kF32, Pulled, PulledDev>;
+    constexpr int NC = consumers(ST);
+    constexpr int NCW = NC / 32;
+    // the state of what a consumer thread pulls per row: a pair of nodes (P = 0) or one
+    using PT2 = std::conditional_t<P == 0, std::conditional_t<ST == kF32, Pulled2, PulledDev2>, PT>;
     // pull the node in staged column col of the row held by stage bc, whose
     // neighbour rows are in stages bm (row - 1) and bp (row + 1)
     auto pull = [&](const unsigned char* bm, const unsigned char* bc, const unsigned char* bp, int col, PT& n) {
@@ -724,12 +1128,12 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
             const T* sdm = reinterpret_cast<const T*>(bm + R * sizeof(float));
             const T* sdc = reinterpret_cast<const T*>(bc + R * sizeof(float));
             const T* sdp = reinterpret_cast<const T*>(bp + R * sizeof(float));
-            pull_dev<T, R>(s0m, s0c, s0p, sdm, sdc, sdp, col, p.tau != 1.f, n);
+            pull_dev<T, R>(s0m, s0c, s0p, sdm, sdc, sdp, col, !T1 && p.tau != 1.f, n);
         }
     };
     float* psi_w = psi_ring;
 
-    if (warp == kConsumerWarps) {
+    if (warp == NCW) {
         // ---------------- producer warp: fill ring stages with rows y0-2 .. y1+1
         bool ok = true;
         // Staged row k goes to stage k % kStages.
@@ -839,12 +1243,24 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
     }
 
     // ---------------- consumer warps
+    // P = 1: thread t pulls node column x0 - 1 + t (staged column t + 1 + o,
+    // psi ring column t) and collides it if it lies inside the strip.
+    // P = 0: thread t owns the pair of columns x0 + 2t (lane A) and
+    // x0 + 2t + 1 (lane B): staged columns c, c + 1 with c = 2t + 1 + o
+    // (even, as o = 3), psi ring columns 2t + 2 and 2t + 3. The pulled
+    // columns are x0 .. x0 + nint, the last one being the right halo; the left
+    // halo x0 - 1 (ring column 1) is one extra pull by thread 0, and a full
+    // strip's right halo x0 + kW (ring column kW + 2) one by the last thread.
     const int t = tid;
-    const bool active = t < nint + 2 * P;           // pulls node column x0 - P + t
-    const bool interior = t >= P && t < P + nint;   // and collides it
-    const int c = t + 1 + o;                        // its staged column
-    const int x = x0 - P + t;
-    const int tr = t + 1 - P;                       // its psi ring column
+    const int np = nint + 1;                                       // P = 0: pulled columns
+    const bool active = P == 0 ? 2 * t < np : t < nint + 2;         // pulls something
+    const bool b_ok = 2 * t + 1 < np;                               // P = 0: lane B pulled
+    const bool col_a = P == 0 ? 2 * t < nint : (t >= 1 && t <= nint);
+    const bool col_b = 2 * t + 1 < nint;                            // P = 0: lane B collided
+    const bool halo_r = P == 0 && t == NC - 1 && np > 2 * NC;
+    const int c = P == 0 ? 2 * t + 1 + o : t + 1 + o;              // staged column (of lane A)
+    const int x = P == 0 ? x0 + 2 * t : x0 - 1 + t;
+    const int tr = P == 0 ? 2 * t + 2 : t;                         // psi ring column (of lane A)
     ObsAcc acc;
     bool ok = true;
     // prologue: the two oldest staged rows (y0-2, y0-1) must be present
@@ -860,52 +1276,15 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
     const unsigned char* b_c = stage_ptr(1);
     const unsigned char* b_p = stage_ptr(2);
 
-    // Row k: pull row r = y0 - 2 + k (staged rows k-1, k, k+1) into `into`,
-    // then collide row r - 1, pulled at row k - 1 into `prev`.
-    auto body = [&](int k, PT& into, const PT& prev) {
-        const int r = y0 - 2 + k;
-        ok = mbar_wait(&full[s_p], ph_p, err) && ok;
-        if (active) {
-            pull(b_m, b_c, b_p, c, into);
-            float* prow = psi_w + ((r + 4) & 3) * kPsiStride;
-            prow[tr] = pseudopotential(p, into);
-            if constexpr (P == 0) {
-                if (t == 0) {  // left halo column x0 - 1
-                    PT h;
-                    pull(b_m, b_c, b_p, c - 1, h);
-                    prow[0] = pseudopotential(p, h);
-                }
-                if (t == nint - 1) {  // right halo column x0 + nint
-                    PT h;
-                    pull(b_m, b_c, b_p, c + 1, h);
-                    prow[nint + 1] = pseudopotential(p, h);
-                }
-            }
-        }
-        consumer_sync();
-        // staged row k-1 is no longer needed by any consumer
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[s_m]);
-        if (k >= 3 && interior && !prev.solid) {
-            // collide row r-1 with psi rows r-2, r-1, r
-            const int rc = r - 1;
-            const float* pm = psi_w + ((rc + 3) & 3) * kPsiStride;
-            const float* pc = psi_w + ((rc + 4) & 3) * kPsiStride;
-            const float* pp = psi_w + ((rc + 5) & 3) * kPsiStride;
-            if constexpr (ST == kF32)
-                collide_node<MODE>(prev, pm, pc, pp, tr, p, g, fout, fields, x, rc, acc);
-            else
-                collide_dev<MODE, T>(prev, pm, pc, pp, tr, p, g, fout, reinterpret_cast<T*>(fout + g.plane),
-                                     fields, x, rc, acc);
-        } else if constexpr (MODE == kFields) {
-            if (k >= 3 && interior) {
-                const size_t i = (size_t)(r - 1) * g.nx + x, nn = (size_t)g.nx * g.ny;
-                fields[i] = 0.0;
-                fields[nn + i] = 0.0;
-                fields[2 * nn + i] = 0.0;
-            }
-        }
-        // advance the ring by one row
+    auto psi_of = [&](bool solid, float rho) { return solid ? 0.f : -p.rho0 * expm1f(-rho * p.inv_rho0); };
+    // all-zero fields of the collided solid lanes (kFields)
+    auto zero_fields = [&](int xs, int rs) {
+        const size_t i = (size_t)rs * g.nx + xs, nn = (size_t)g.nx * g.ny;
+        fields[i] = 0.0;
+        fields[nn + i] = 0.0;
+        fields[2 * nn + i] = 0.0;
+    };
+    auto advance = [&]() {
         s_m = (s_m == kStages - 1) ? 0 : s_m + 1;
         s_p = (s_p == kStages - 1) ? 0 : s_p + 1;
         ph_p ^= (s_p == 0) ? 1u : 0u;
@@ -914,9 +1293,80 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
         b_p = stage_ptr(s_p);
     };
 
-    // two pulled-node registers used in turn, so that no copy is made
-    PT n0, n1;
-    n0.solid = n1.solid = true;
+    // Row k: pull row r = y0 - 2 + k (staged rows k-1, k, k+1) into `into`,
+    // then collide row r - 1, pulled at row k - 1 into `prev`.
+    auto body = [&](int k, PT2& into, const PT2& prev) {
+        const int r = y0 - 2 + k;
+        ok = mbar_wait(&full[s_p], ph_p, err) && ok;
+        float* prow = psi_w + ((r + 4) & 3) * kPsiStride;
+        if (active) {
+            if constexpr (P == 0) {
+                const float* s0m = reinterpret_cast<const float*>(b_m);
+                const float* s0c = reinterpret_cast<const float*>(b_c);
+                const float* s0p = reinterpret_cast<const float*>(b_p);
+                if constexpr (ST == kF32)
+                    pull_pair(s0m, s0c, s0p, c, b_ok, into);
+                else
+                    pull_dev_pair(s0m, s0c, s0p, s0m + R, s0c + R, s0p + R, c, b_ok, !T1 && p.tau != 1.f, into);
+                *reinterpret_cast<float2*>(prow + tr) =
+                    make_float2(psi_of(into.solid[0], into.rho.x), psi_of(into.solid[1], into.rho.y));
+                if (t == 0) {  // left halo column x0 - 1
+                    PT h;
+                    pull(b_m, b_c, b_p, c - 1, h);
+                    prow[1] = pseudopotential(p, h);
+                }
+                if (halo_r) {  // right halo column x0 + kW
+                    PT h;
+                    pull(b_m, b_c, b_p, c + 2, h);
+                    prow[tr + 2] = pseudopotential(p, h);
+                }
+            } else {
+                pull(b_m, b_c, b_p, c, into);
+                prow[tr] = pseudopotential(p, into);
+            }
+        }
+        consumer_sync<NC>();
+        // staged row k-1 is no longer needed by any consumer
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s_m]);
+        if (k >= 3) {
+            // collide row r-1 with psi rows r-2, r-1, r
+            const int rc = r - 1;
+            const float* pm = psi_w + ((rc + 3) & 3) * kPsiStride;
+            const float* pc = psi_w + ((rc + 4) & 3) * kPsiStride;
+            const float* pp = psi_w + ((rc + 5) & 3) * kPsiStride;
+            if constexpr (P == 0) {
+                const bool col[2] = {col_a && !prev.solid[0], col_b && !prev.solid[1]};
+                if (col[0] || col[1]) {
+                    if constexpr (ST == kF32)
+                        collide_pair<MODE, T1>(prev, col, pm, pc, pp, tr, p, g, fout, fields, x, rc, acc);
+                    else
+                        collide_dev_pair<MODE, T1>(prev, col, pm, pc, pp, tr, p, g, fout, fout + g.plane, fields, x,
+                                               rc, acc);
+                }
+                if constexpr (MODE == kFields) {
+                    if (col_a && prev.solid[0]) zero_fields(x, rc);
+                    if (col_b && prev.solid[1]) zero_fields(x + 1, rc);
+                }
+            } else {
+                if (col_a && !prev.solid)
+                    collide_dev<MODE, T, T1>(prev, pm, pc, pp, tr, p, g, fout, reinterpret_cast<T*>(fout + g.plane),
+                                         fields, x, rc, acc);
+                else if constexpr (MODE == kFields) {
+                    if (col_a) zero_fields(x, rc);
+                }
+            }
+        }
+        advance();
+    };
+
+    // two pulled-state register sets used in turn, so that no copy is made
+    PT2 n0, n1;
+    if constexpr (P == 0) {
+        n0.solid[0] = n0.solid[1] = n1.solid[0] = n1.solid[1] = true;
+    } else {
+        n0.solid = n1.solid = true;
+    }
     for (int k = 1; k <= nrows - 2; k += 2) {
         body(k, n0, n1);
         if (k + 1 <= nrows - 2) body(k + 1, n1, n0);
@@ -925,9 +1375,9 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
 
     if constexpr (MODE == kStepObs || MODE == kObs) {
         // deterministic CTA reduction: warp shuffles, then one thread over warps
-        __shared__ double red_d[4][kConsumerWarps];
-        __shared__ float red_f[2][kConsumerWarps];
-        __shared__ unsigned red_u[kConsumerWarps];
+        __shared__ double red_d[4][NCW];
+        __shared__ float red_f[2][NCW];
+        __shared__ unsigned red_u[NCW];
         double d[4] = {acc.mass.value(), acc.q.value(), acc.px.value(), acc.py.value()};
         float umax2 = acc.umax2, rmin = acc.rmin;
         unsigned bad = acc.bad;
@@ -946,12 +1396,12 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
             red_f[1][warp] = rmin;
             red_u[warp] = bad;
         }
-        consumer_sync();
+        consumer_sync<NC>();
         if (t == 0) {
             double s[4] = {0, 0, 0, 0};
             float um = 0.f, rm = __int_as_float(0x7f800000);
             unsigned b = 0;
-            for (int w = 0; w < kConsumerWarps; ++w) {
+            for (int w = 0; w < NCW; ++w) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) s[q] += red_d[q][w];
                 um = fmaxf(um, red_f[0][w]);
@@ -971,13 +1421,15 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
     }
 }
 
-template <int MODE, int ST = kF32>
-__global__ void __launch_bounds__(kThreads, 3)
+// T1: tau = 1 (the relaxation sets f* = f_eq, so no pulled population is
+// kept for it); the modes that only observe use T1 = true.
+template <int MODE, int ST = kF32, bool T1 = true>
+__global__ void __launch_bounds__(threads_of(ST), step_ctas_of(MODE, ST, T1))
     step_kernel(const float* __restrict__ fin, float* __restrict__ fout, Geom g, Phys p,
                 double* __restrict__ partials, double* __restrict__ fields, int* __restrict__ err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    run_tile<MODE, ST>(fin, fout, g, p, partials, fields, err, blockIdx.x, blockIdx.y,
+    run_tile<MODE, ST, T1>(fin, fout, g, p, partials, fields, err, blockIdx.x, blockIdx.y,
                        blockIdx.y * gridDim.x + blockIdx.x, smem_raw);
 }
 
@@ -994,8 +1446,8 @@ struct DomainDev {
 // segment, partial slot) with stride gridDim.x, so domains of any size share
 // one launch; buffers alternate with `parity`. Between tiles the CTA
 // invalidates and re-arms its mbarriers.
-template <int MODE, int ST = kF32>
-__global__ void __launch_bounds__(kThreads, 3)
+template <int MODE, int ST = kF32, bool T1 = true>
+__global__ void __launch_bounds__(threads_of(ST), batch_ctas_of(ST, T1))
     batch_step_kernel(const DomainDev* __restrict__ doms, const int4* __restrict__ tiles, int ntiles,
                       int parity, int* __restrict__ err)
 {
@@ -1005,13 +1457,13 @@ __global__ void __launch_bounds__(kThreads, 3)
         const DomainDev& d = doms[tl.x];
         const Geom g = d.g;
         const Phys p = d.p;
-        run_tile<MODE, ST>(d.buf[parity], d.buf[parity ^ 1], g, p, d.partials, nullptr, err, tl.y, tl.z, tl.w,
+        run_tile<MODE, ST, T1>(d.buf[parity], d.buf[parity ^ 1], g, p, d.partials, nullptr, err, tl.y, tl.z, tl.w,
                            smem_raw);
         __syncthreads();
         if (threadIdx.x == 0) {
-            uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + kStages * stage_bytes<ST>() +
+            uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + stages_of(ST) * stage_bytes<ST>() +
                                                          4 * kPsiStride * sizeof(float));
-            for (int s = 0; s < 2 * kStages; ++s) mbar_inval(&bars[s]);
+            for (int s = 0; s < 2 * stages_of(ST); ++s) mbar_inval(&bars[s]);
         }
         __syncthreads();
     }

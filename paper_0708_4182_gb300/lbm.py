@@ -24,7 +24,7 @@ from . import build as _build
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENAN, LBM_ETIMEOUT, LBM_ESTATE, LBM_ENOTCONV = range(8)
 LBM_GREEN_MC, LBM_GREEN_PRINTED = 0, 1
 LBM_FP32, LBM_FP32_DEV, LBM_FP16_DEV, LBM_BF16_DEV = 0, 1, 2, 3
-LBM_RHO_U, LBM_POPS, LBM_RHO_U_PHYS, LBM_UX_PROFILE = 0, 1, 2, 3
+LBM_RHO_U, LBM_POPS, LBM_RHO_U_PHYS, LBM_UX_PROFILE, LBM_RHO = 0, 1, 2, 3, 4
 
 
 class LbmUnavailable(RuntimeError):
@@ -45,6 +45,7 @@ class lbm_params(ctypes.Structure):
         ("body_fx", ctypes.c_double), ("body_fy", ctypes.c_double),
         ("green", ctypes.c_int32), ("storage", ctypes.c_int32),
         ("obs_every", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
+        ("normal", ctypes.c_int32),
     ]
 
 
@@ -115,10 +116,10 @@ def _check(ctx, status: int):
 
 def make_params(nx, ny, tau=1.0, G=-0.52, G_wall=-0.14, rho0=1.0, rho_c=1.0, f_elec=0.0,
                 body_fx=0.0, body_fy=0.0, green=LBM_GREEN_MC, storage=LBM_FP32, obs_every=0,
-                tile_rows=0) -> lbm_params:
+                tile_rows=0, normal=0) -> lbm_params:
     return lbm_params(int(nx), int(ny), float(tau), float(G), float(G_wall), float(rho0),
                       float(rho_c), float(f_elec), float(body_fx), float(body_fy), int(green),
-                      int(storage), int(obs_every), int(tile_rows))
+                      int(storage), int(obs_every), int(tile_rows), int(normal))
 
 
 # ---------------------------------------------------------------- low level
@@ -282,6 +283,13 @@ class Lattice:
             data = np.stack([np.broadcast_to(np.asarray(v, np.float64), (self.ny, self.nx))
                              for v in (rho, ux, uy)])
         self._set(LBM_RHO_U_PHYS if physical else LBM_RHO_U, data, 3)
+
+    def set_rho(self, rho):
+        """A fluid at rest: f = f_eq(rho, 0), from the density alone (LBM_RHO)."""
+        if hasattr(rho, "is_cuda") and rho.is_cuda:
+            self._set(LBM_RHO, rho.reshape(1, self.ny, self.nx), 1)
+        else:
+            self._set(LBM_RHO, np.asarray(rho, np.float64).reshape(1, self.ny, self.nx), 1)
 
     def set_rho_u_field(self, data, physical=False):
         """(rho, u_x, u_y) as one [3, ny, nx] array or device tensor (FP64)."""

@@ -210,6 +210,40 @@ def droplet_row_density(nx, ny, centres, radius, mask, width=4.0):
     return np.where(mask != 0, 0.0, rho)
 
 
+def stepped_channel_mask(nx: int, width: int, a: int, b: int, pitch: int) -> np.ndarray:
+    """Solid mask of the paper's rough-wall channel sketch: a periodic channel
+    of `width` fluid rows between two solid rows, both walls carrying
+    rectangular steps of width a and height b whose centres are `pitch` apart
+    (the same x positions on both walls); nx must be a multiple of pitch."""
+    if nx % pitch or a >= pitch or 2 * b + 1 > width:
+        raise ValueError("steps do not fit the channel")
+    ny = width + 2
+    mask = np.zeros((ny, nx), dtype=np.uint8)
+    mask[0, :] = 1
+    mask[ny - 1, :] = 1
+    x = np.arange(nx)
+    on = ((x - pitch // 2 + a // 2) % pitch) < a  # step centred at pitch/2 of each period
+    mask[1:b + 1, on] = 1
+    mask[ny - 1 - b:ny - 1, on] = 1
+    return mask
+
+
+def paper_channel(width: int, f_elec: float, nx: int = 256, a: int = 8, b: int = 8, pitch: int = 32,
+                  body_fx: float = 8e-6) -> Workload:
+    """The paper's electrowetting channel runs: rough-wall channel of width 160
+    or 80 under a rightward body force 8e-6, electric force 0, 0.15 or 0.25.
+    The paper gives neither the step sizes a, b, p nor the length; these are
+    chosen (a = b = 8, p = 32, length 256). Liquid fills the channel up to the
+    step crests, vapor fills the grooves between steps."""
+    mask = stepped_channel_mask(nx, width, a, b, pitch)
+    ny = width + 2
+    fill = 1.0 - 2.0 * (b + 1) / (ny - 2)
+    rho = slab_field(nx, ny, fill, mask=mask)
+    return Workload(f"paper_channel_w{width}", nx, ny, mask, rho,
+                    dict(PAPER, tau=1.0, f_elec=f_elec, body_fx=body_fx, body_fy=0.0),
+                    dict(width=width, a=a, b=b, pitch=pitch, fill=fill))
+
+
 def batched_channels(count=256, seed=0):
     """Sizes and levels of the batched sweep: width 32-256, length 512-2048,
     roughness amplitude 0-8 and electric-force level 0-15, from one seed."""

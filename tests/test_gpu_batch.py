@@ -146,8 +146,11 @@ def test_batch_autotune_grid_and_ctas_per_sm(lbm):
             assert set(table) == {(8, 2), (32, 2), (8, 3), (32, 3)} and all(v > 0 for v in table.values())
             assert table[(rows, cts)] == min(table.values())
             assert b.tile_rows == rows and b.ctas_per_sm == cts
+            probe = lbm.Batch(specs_of(ws))
+            top = probe.ctas_per_sm  # the default: the most that fit
+            probe.close()
             with pytest.raises(lbm.LbmError):
-                b.set_ctas_per_sm(4)
+                b.set_ctas_per_sm(top + 1)
         b.close()
     for a, c in zip(*outs):
         assert np.array_equal(a, c)

@@ -6,13 +6,16 @@ the FP64 oracle from the same seeded start):
 * relative 1e-6 on populations, as the relative L2 error of the field:
       ||f_gpu - f_ref||_2 / ||f_ref||_2 <= 1e-6;
 * element by element, every node and direction:
-      |f_gpu - f_ref| <= 4e-6 * max |f_ref|
+      |f_gpu - f_ref| <= 3e-6 * max |f_ref|
       |f_gpu - f_ref| / max(|f_ref|, w_a rho_v) <= 1e-5.
   The element bounds come from the arithmetic: with exact arithmetic and only
   the FP32 storage rounding, the first measure already reaches 6.5e-7 after
   100 steps on a rough channel (a static interface node rounds the same way
   every step, so the errors add up rather than cancel), and the FP32
-  collision multiplies that by about 3 at high-force interface nodes.
+  collision multiplies that by about 2 at high-force interface nodes. The
+  largest values measured over these cases on a GB300 are 2.2e-7 (L2),
+  1.4e-6 (field-relative) and 5.3e-6 (self-relative); each case prints its
+  three measures (pytest -s).
 Every case also checks the observables (mass, flux Q of Eq. 11, momentum).
 """
 import numpy as np
@@ -25,7 +28,7 @@ pytestmark = pytest.mark.gpu
 
 W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
 TOL_L2 = 1e-6      # relative L2 over the population field
-TOL_FIELD = 4e-6   # per element, relative to the field's maximum
+TOL_FIELD = 3e-6   # per element, relative to the field's maximum
 TOL_ELEM = 1e-5    # per element, relative to itself (vapor-scale floor)
 
 
@@ -443,3 +446,41 @@ def test_obs_latest_async_matches_synchronous_read(lbm):
         torch.cuda.synchronize()
         assert lbm.obs_from_buffer(buf.data_ptr()) == lbm.lbm_obs_latest(lat.ctx)
     lat.close()
+
+
+@pytest.mark.parametrize("storage", [0, 1, 2, 3])
+def test_density_only_setup_equals_rest_equilibrium(lbm, storage):
+    """LBM_RHO (a fluid at rest from its density alone) gives the state that
+    LBM_RHO_U gives with zero velocity, bit for bit, in every storage form,
+    before and after stepping."""
+    w = wl.rough_channel(nx=256, ny=48, amp=6, level=9, seed=5, body_fx=1e-5)
+    a = lbm.Lattice(w.nx, w.ny, storage=storage, **w.params)
+    b = lbm.Lattice(w.nx, w.ny, storage=storage, **w.params)
+    for lat in (a, b):
+        lat.set_geometry(w.mask)
+    a.set_rho_u(w.rho)
+    b.set_rho(w.rho)
+    assert np.array_equal(a.populations(), b.populations())
+    a.step(7)
+    b.step(7)
+    assert np.array_equal(a.populations(), b.populations())
+
+
+def test_unit_normal_reading_matches_oracle(lbm):
+    """The electric force along the unit face normal (LBM_NORMAL_UNIT) on a
+    rough channel, whose step corners are where the two readings differ:
+    populations after 100 steps within the gates, and different from the
+    per-face reading's."""
+    w = wl.rough_channel(nx=300, ny=48, amp=6, level=15, seed=5, body_fx=1e-5)
+    params = dict(w.params, normal=1)
+    p = oracle.Params(w.nx, w.ny, **params)
+    f_ref = oracle.step(p, w.mask, oracle.equilibrium(p, w.mask, w.rho, 0, 0), 100)
+    lat = lbm.Lattice(w.nx, w.ny, **params)
+    lat.set_geometry(w.mask)
+    lat.set_rho_u(w.rho)
+    lat.step(100)
+    assert_pops(lat.populations(), f_ref, w.mask)
+    check_obs(lat, p, w.mask, f_ref)
+    p_faces = oracle.Params(w.nx, w.ny, **w.params)
+    f_faces = oracle.step(p_faces, w.mask, oracle.equilibrium(p_faces, w.mask, w.rho, 0, 0), 100)
+    assert pop_err(f_faces, f_ref, w.mask)[0] > 1e-3

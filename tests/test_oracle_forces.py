@@ -128,6 +128,43 @@ def test_electric_force_layer():
     assert t[4][1, 3] == fe and t[5][1, 3] == -fe  # concave corner: both faces
 
 
+def test_electric_force_unit_normal_reading():
+    """The other reading of f n (n a unit vector): where two perpendicular
+    solid faces meet, the force has length f along the diagonal instead of
+    f per face; everywhere else it equals the per-face reading."""
+    nx, ny, mask = ewod_geometry()
+    rho = np.full((ny, nx), 1.5)
+    rho[mask == 1] = 0.0
+    fe = 0.2
+    pf = oracle.Params(nx, ny, G=G, G_wall=W, f_elec=fe)
+    pu = oracle.Params(nx, ny, G=G, G_wall=W, f_elec=fe, normal=oracle.NORMAL_UNIT)
+    _, _, _, tf = oracle.forces(pf, mask, state(pf, mask, rho))
+    _, _, _, tu = oracle.forces(pu, mask, state(pu, mask, rho))
+    corner = (tf[4] != 0) & (tf[5] != 0)
+    assert corner.sum() == 2 and corner[1, 3] and corner[1, 7]  # the step's two concave corners
+    s = np.sqrt(0.5)
+    assert tu[4][1, 3] == pytest.approx(fe * s, rel=1e-15) and tu[5][1, 3] == pytest.approx(-fe * s, rel=1e-15)
+    assert tu[4][1, 7] == pytest.approx(-fe * s, rel=1e-15) and tu[5][1, 7] == pytest.approx(-fe * s, rel=1e-15)
+    np.testing.assert_array_equal(tu[4][~corner], tf[4][~corner])
+    np.testing.assert_array_equal(tu[5][~corner], tf[5][~corner])
+    np.testing.assert_allclose(np.hypot(tu[4], tu[5])[tf[4] ** 2 + tf[5] ** 2 > 0], fe, rtol=1e-15)
+    # the other terms do not depend on the reading
+    for k in (0, 1, 2, 3, 6, 7):
+        np.testing.assert_array_equal(tu[k], tf[k])
+
+
+def test_unit_normal_reading_changes_nothing_on_flat_walls():
+    """A droplet on a smooth wall has no node where two solid faces meet, so
+    both readings give the same state step for step (the contact-angle law
+    of Eq. 9 cannot tell them apart there)."""
+    from paper_0708_4182_gb300 import workloads as wl
+    w = wl.droplet_128x64(0.25)
+    p0 = oracle.Params(w.nx, w.ny, **w.params)
+    p1 = oracle.Params(w.nx, w.ny, normal=oracle.NORMAL_UNIT, **w.params)
+    f0 = oracle.equilibrium(p0, w.mask, w.rho, 0, 0)
+    np.testing.assert_array_equal(oracle.step(p0, w.mask, f0, 200), oracle.step(p1, w.mask, f0, 200))
+
+
 def test_electric_force_threshold_is_inclusive():
     """rho == rho_c counts as conductive; the next double above does not."""
     nx, ny, mask = ewod_geometry()
