@@ -66,6 +66,10 @@ def parse():
     ap.add_argument("--tts-config3", action="store_true",
                     help="also measure time to steady flux on the full batched sweep (256 full-size rough "
                          "channels, body force 1e-6): one domain at a time vs one batch (several minutes)")
+    ap.add_argument("--warm-start-config5", action="store_true",
+                    help="also run the learned warm start on rough walls as stated: U-Net trained on 2000 "
+                         "steady states of 256x64 rough channels, 256 fresh channels warm-started with "
+                         "fallback (a few minutes)")
     ap.add_argument("--paper-channels", action="store_true",
                     help="also run the paper's channel experiments (widths 160 and 80, body force 8e-6, "
                          "electric force 0, 0.15, 0.25) to steady flux: Q/Q0 and the mean velocity profiles")
@@ -341,6 +345,8 @@ def run_ours(args, rank, world, local_rank):
         extra["paper_channels"] = extra_pc
     if args.tts_config3 and rank == 0:
         extra["time_to_steady_config3"] = time_to_steady_full(lbm, stream)
+    if args.warm_start_config5 and rank == 0:
+        extra["warm_start_config5"] = warm_start_config5(lbm, stream)
 
     line = {"metric": "MLUPS", "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 5),
@@ -626,6 +632,7 @@ def time_to_steady_full(lbm, stream, cap=400000, check=1000):
     for w, d in zip(ws, b.domains):
         d.set_geometry(w.mask)
         d.set_rho_u(w.rho)
+    b.set_tile_rows(64)  # halved by run_to_steady as converged domains leave
     steps, obs, _ = b.run_to_steady(1e-7, check, cap)
     torch.cuda.synchronize()
     t_batch = time.perf_counter() - t
@@ -815,7 +822,78 @@ def warm_start_sweep(lbm, stream, n_train=1024, epochs=40, n_eval=64):
         "steps_plain": int(sum(st for _, st in plain)), "steps_cold_batched": int(sum(cold_steps)),
         "steps_warm": int(sum(steps)), "restarted": int(sum(winfo["restarted"])),
         "converged": int(sum(1 for x in steps if x > 0)), "domains": n_eval,
-        "within_1e-3_of_plain": int((rel <= 1e-3).sum()), "max_rel_flux_difference_vs_plain": float(rel.max())}
+        "within_1e-3_of_plain": int((rel <= 1e-3).sum()), "max_rel_flux_difference_vs_plain": float(rel.max()),
+        "break_even_domains": break_even(info, t_cold, t_warm, n_eval)}
+
+
+def break_even(info, t_cold, t_warm, n):
+    """Domains a warm-started batch must run before the one-off cost of the
+    surrogate (steady-state generation plus training) is paid back by its
+    saving over the cold batch (None if it saves nothing)."""
+    saved = (t_cold - t_warm) / n
+    return int(np.ceil((info["generate_s"] + info["train_s"]) / saved)) if saved > 0 else None
+
+
+def warm_start_config5(lbm, stream, n_train=2000, epochs=40, n_eval=256, cap=60000):
+    """The learned warm start on rough walls as the workload states it: the
+    U-Net trained on 2000 steady states of the rough-channel recipe (256x64
+    tiles: roughness 0-8, level 0-15, liquid fill from the crests, body force
+    1e-6, seed 100), then 256 fresh channels of the same recipe (seed 7) run
+    to steady flux in one batch from its predictions, a domain falling back
+    to its cold start when its flux residual fails to drop over the first
+    two convergence intervals. Against the same batch from cold starts (the
+    plain method: every domain bitwise as if stepped alone): steps saved,
+    final flux error and fallback rate, over all domains and apart for flat
+    and rough walls."""
+    import torch
+    from paper_0708_4182_gb300 import surrogate as S
+    from paper_0708_4182_gb300 import workloads as wl
+    S.load_unet()
+    with torch.cuda.stream(stream):
+        net, info = S.fit(wl.warm_start_channels(n_train, seed=100, body_fx=1e-6), epochs=epochs,
+                          wc=(1.0, 4.0, 1.0), stream=stream, max_steps=cap)
+        ws = wl.warm_start_channels(n_eval, seed=7, body_fx=1e-6)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        cold_steps, cold_obs, _ = S.batch_run_to_steady(ws, stream=stream, max_steps=cap)
+        torch.cuda.synchronize()
+        t_cold = time.perf_counter() - t
+        t = time.perf_counter()
+        steps, obs, winfo = S.batch_run_to_steady(ws, net, stream=stream, max_steps=cap, policy=lambda m: True)
+        torch.cuda.synchronize()
+        t_warm = time.perf_counter() - t
+    flat = np.array([S.flat_walls(w.mask) for w in ws])
+    both = np.array([c > 0 and s_ > 0 for c, s_ in zip(cold_steps, steps)])
+    qc = np.array([o["flux_Q"] for o in cold_obs])
+    qw = np.array([o["flux_Q"] for o in obs])
+    rel = np.abs(qw / qc - 1)
+    restarted = np.array(winfo["restarted"])
+
+    def part(sel):
+        sel = sel & both
+        saved = sum(c - s_ for c, s_, k in zip(cold_steps, steps, sel) if k)
+        total = sum(c for c, k in zip(cold_steps, sel) if k)
+        return {"domains": int(sel.sum()),
+                "steps_saved_fraction": round(saved / total, 3) if total else None,
+                "within_1e-3_of_cold": int((rel[sel] <= 1e-3).sum()),
+                "median_rel_flux_error": float(np.median(rel[sel])) if sel.any() else None,
+                "max_rel_flux_error": float(rel[sel].max()) if sel.any() else None,
+                "fallback_rate": round(float(restarted[sel].mean()), 3) if sel.any() else None}
+
+    return {
+        "workload": f"{n_eval} rough channels 256x64 of the rough-channel recipe (roughness 0-8, level 0-15, "
+                    f"liquid fill from the crests, body force 1e-6, seed 7), FP32 deviation storage; steady when "
+                    f"|dQ|/|Q| < 1e-7 per 1000 steps, cap {cap}",
+        "surrogate": f"U-Net 4 levels, 32 base channels, BF16 storage / FP32 sums, trained {epochs} epochs on "
+                     f"{info['samples']} steady states of {n_train} channels (seed 100)",
+        "surrogate_generate_s": round(info["generate_s"], 2), "surrogate_train_s": round(info["train_s"], 2),
+        "surrogate_train_rel_l2": {k: round(v, 4) for k, v in info["train_rel_l2"].items()},
+        "batched_cold_s": round(t_cold, 3), "batched_warm_s": round(t_warm, 3),
+        "speedup_warm_vs_cold": round(t_cold / t_warm, 3),
+        "steps_cold": int(sum(x for x in cold_steps if x > 0)), "steps_warm": int(sum(x for x in steps if x > 0)),
+        "converged_cold": int(sum(1 for x in cold_steps if x > 0)), "converged_warm": int(sum(1 for x in steps if x > 0)),
+        "all": part(np.ones(len(ws), bool)), "flat_walls": part(flat), "rough_walls": part(~flat),
+        "break_even_domains": break_even(info, t_cold, t_warm, n_eval)}
 
 
 def main():

@@ -301,7 +301,11 @@ lbm_status lbm_batch_autotune_grid(lbm_batch *b, const int32_t *rows, int32_t nr
  * non-finite: such a domain is dropped and the others run on), out[count]
  * its last observables. LBM_ENAN if some domain became non-finite, else
  * LBM_ENOTCONV if some active domain did not converge within max_steps.
- * The caller's active set is restored on return. */
+ * With an explicit tile height (lbm_batch_set_tile_rows or the autotuners),
+ * the height is halved, down to 8 rows, whenever the domains still running
+ * give fewer than two waves of tiles for the persistent grid (a tiling
+ * change leaves every population bit for bit as it was). The caller's
+ * active set and tile height are restored on return. */
 lbm_status lbm_batch_run_to_steady(lbm_batch *b, double rel_tol, int64_t check_every, int64_t max_steps,
                                    int64_t *steps_to_steady, lbm_obs *out);
 

@@ -1438,12 +1438,31 @@ bool batch_layout(const lbm_params* p, int count, BatchLayout* L, const char** w
 // channel at height 32 gets two segments of 20 rows, not 32 + 8: a short
 // last segment pays the pipeline start and the 4 re-staged halo rows for
 // few rows). The segment count is unchanged.
+// Segment height of a domain of ny rows for a wanted height: the same
+// segment count with heights that differ by at most one row.
+int even_rows(int ny, int want)
+{
+    const int nseg = (ny + want - 1) / want;
+    const int even = (ny + nseg - 1) / nseg;
+    return even >= 4 ? even : want;
+}
+
 int domain_tile_rows(const lbm_batch* b, const lbm_ctx* c)
 {
-    const int want = b->tile_rows ? b->tile_rows : c->g.tile_rows;
-    const int nseg = (c->g.ny + want - 1) / want;
-    const int even = (c->g.ny + nseg - 1) / nseg;
-    return even >= 4 ? even : want;
+    return even_rows(c->g.ny, b->tile_rows ? b->tile_rows : c->g.tile_rows);
+}
+
+// Tiles of the active domains at the wanted tile height `rows`.
+long long active_tiles(const lbm_batch* b, int rows)
+{
+    long long n = 0;
+    for (int d = 0; d < b->count; ++d) {
+        if (!b->active[d]) continue;
+        const lbm_ctx* c = b->ctx[d];
+        const int r = even_rows(c->g.ny, rows);
+        n += (long long)ctas_x(c->g.nx, c->prm.storage) * ((c->g.ny + r - 1) / r);
+    }
+    return n;
 }
 
 // Tile list of the active domains (or of all domains), largest domains first
@@ -1788,6 +1807,22 @@ lbm_status lbm_batch_run_to_steady(lbm_batch* b, double rel_tol, int64_t check_e
     for (int d = 0; d < b->count; ++d) steps_to_steady[d] = -1;
     std::vector<lbm_obs> rec(b->count);
     int first_nan = -1;
+    // As domains converge and leave, the tile list shrinks and the persistent
+    // grid's SMs fall idle; a lower tile height gives the remaining domains
+    // more tiles. Keep at least two waves (the arithmetic does not depend on
+    // the tiling), down to 8-row segments; the caller's height is restored.
+    const int32_t rows_start = b->tile_rows;
+    const long long slots = (long long)b->ctas_per_sm * b->sm_count;
+    auto retile = [&]() {
+        if (b->tile_rows <= 0) return;  // each domain's own height (already sized for it alone)
+        int r = b->tile_rows;
+        while (r > 8 && active_tiles(b, r) < 2 * slots) r = r / 2 < 8 ? 8 : r / 2;
+        if (r != b->tile_rows) {
+            b->tile_rows = r;
+            b->tiles_dirty = true;
+        }
+    };
+    retile();
     for (int64_t done = 0; done < max_steps;) {
         bool any = false;
         for (int d = 0; d < b->count; ++d) any = any || b->active[d];
@@ -1818,10 +1853,14 @@ lbm_status lbm_batch_run_to_steady(lbm_batch* b, double rel_tol, int64_t check_e
             q_prev[d] = q;
             have_prev[d] = 1;
         }
-        if (changed) b->tiles_dirty = true;
+        if (changed) {
+            b->tiles_dirty = true;
+            retile();
+        }
     }
-    // restore the caller's active set
+    // restore the caller's active set and tile height
     b->active = start_active;
+    b->tile_rows = rows_start;
     b->tiles_dirty = true;
     if (first_nan >= 0) return bfail(b, LBM_ENAN, "domain %d became non-finite", first_nan);
     for (int d = 0; d < b->count; ++d)

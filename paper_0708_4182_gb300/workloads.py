@@ -229,16 +229,24 @@ def stepped_channel_mask(nx: int, width: int, a: int, b: int, pitch: int) -> np.
 
 
 def paper_channel(width: int, f_elec: float, nx: int = 256, a: int = 8, b: int = 8, pitch: int = 32,
-                  body_fx: float = 8e-6) -> Workload:
+                  body_fx: float = 8e-6, perturb: float = 1e-3, seed: int = 11) -> Workload:
     """The paper's electrowetting channel runs: rough-wall channel of width 160
     or 80 under a rightward body force 8e-6, electric force 0, 0.15 or 0.25.
     The paper gives neither the step sizes a, b, p nor the length; these are
     chosen (a = b = 8, p = 32, length 256). Liquid fills the channel up to the
-    step crests, vapor fills the grooves between steps."""
+    step crests, vapor fills the grooves between steps. The channel is mirror
+    symmetric, and a symmetric start stays symmetric in a deterministic
+    update; each node's density is therefore scaled by 1 + perturb * xi, xi
+    uniform on [-1, 1) from a SplitMix64 stream (seed), so that an unstable
+    symmetric state (the paper's narrow channel at strong f) can break."""
     mask = stepped_channel_mask(nx, width, a, b, pitch)
     ny = width + 2
     fill = 1.0 - 2.0 * (b + 1) / (ny - 2)
     rho = slab_field(nx, ny, fill, mask=mask)
+    if perturb:
+        rng = SplitMix64(seed)
+        xi = np.array([2.0 * rng.uniform() - 1.0 for _ in range(nx * ny)]).reshape(ny, nx)
+        rho = rho * (1.0 + perturb * xi)
     return Workload(f"paper_channel_w{width}", nx, ny, mask, rho,
                     dict(PAPER, tau=1.0, f_elec=f_elec, body_fx=body_fx, body_fy=0.0),
                     dict(width=width, a=a, b=b, pitch=pitch, fill=fill))

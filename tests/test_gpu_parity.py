@@ -468,10 +468,11 @@ def test_density_only_setup_equals_rest_equilibrium(lbm, storage):
 
 def test_unit_normal_reading_matches_oracle(lbm):
     """The electric force along the unit face normal (LBM_NORMAL_UNIT) on a
-    rough channel, whose step corners are where the two readings differ:
-    populations after 100 steps within the gates, and different from the
-    per-face reading's."""
-    w = wl.rough_channel(nx=300, ny=48, amp=6, level=15, seed=5, body_fx=1e-5)
+    rough channel full of liquid, so that conductive liquid fills the
+    concave step corners, where the two readings differ (with vapor in the
+    grooves no corner is conductive and they coincide): populations after
+    100 steps within the gates, and different from the per-face reading's."""
+    w = wl.rough_channel(nx=300, ny=48, amp=6, level=15, seed=5, body_fx=1e-5, fill=1.0)
     params = dict(w.params, normal=1)
     p = oracle.Params(w.nx, w.ny, **params)
     f_ref = oracle.step(p, w.mask, oracle.equilibrium(p, w.mask, w.rho, 0, 0), 100)
