@@ -72,8 +72,7 @@ enum Storage { kF32 = 0, kF32Dev = 1, kF16Dev = 2, kBF16Dev = 3 };
 // at. The 16-bit forms (288 threads): 6 and 3. The 32-bit forms (160
 // threads, a pair of nodes per thread): LBM_STAGES_F32 / LBM_CTAS_F32 and
 // LBM_STAGES_F32DEV / LBM_CTAS_F32DEV for the tau = 1 instances, whose
-// register needs are lower; the tau != 1 instances, and the persistent
-// batch kernel of the FP32 deviation form (which spills at 4), aim at 3.
+// register needs are lower; the tau != 1 instances aim at 3.
 // Shared memory and registers must allow that many CTAs. Measured at
 // 16384x4096 (GLUPS, FP32 / FP32 deviations / batch FP32 / batch FP32
 // deviations): 6 stages x 3 CTAs 89.4 / 85.9 / 80.5 / 72.8; FP32 4 x 5 and
@@ -98,7 +97,12 @@ __host__ __device__ constexpr int ctas_of(int st, bool t1 = true)
 {
     return st == kF32 ? (t1 ? LBM_CTAS_F32 : 3) : st == kF32Dev ? (t1 ? LBM_CTAS_F32DEV : 3) : 3;
 }
-__host__ __device__ constexpr int batch_ctas_of(int st, bool t1 = true) { return st == kF32Dev ? 3 : ctas_of(st, t1); }
+// the persistent batch kernel: as the single-domain step; its observing mode
+// aims at 3 (it spills at 4)
+__host__ __device__ constexpr int batch_ctas_of(int mode, int st, bool t1)
+{
+    return mode == 0 ? ctas_of(st, t1) : (ctas_of(st, t1) > 3 ? 3 : ctas_of(st, t1));
+}
 // the single-domain kernel of a mode: the observing modes keep their
 // reduction state too and aim at one CTA less (no spills)
 __host__ __device__ constexpr int step_ctas_of(int mode, int st, bool t1)
@@ -1447,18 +1451,26 @@ struct DomainDev {
 // one launch; buffers alternate with `parity`. Between tiles the CTA
 // invalidates and re-arms its mbarriers.
 template <int MODE, int ST = kF32, bool T1 = true>
-__global__ void __launch_bounds__(threads_of(ST), batch_ctas_of(ST, T1))
+__global__ void __launch_bounds__(threads_of(ST), batch_ctas_of(MODE, ST, T1))
     batch_step_kernel(const DomainDev* __restrict__ doms, const int4* __restrict__ tiles, int ntiles,
                       int parity, int* __restrict__ err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
+    // the tile's domain parameters live in shared memory, read where used, so
+    // that they hold no registers across the tile (the single-domain kernel
+    // reads them from its parameter space)
+    __shared__ Geom g;
+    __shared__ Phys p;
     for (int i = blockIdx.x; i < ntiles; i += gridDim.x) {
         const int4 tl = tiles[i];
         const DomainDev& d = doms[tl.x];
-        const Geom g = d.g;
-        const Phys p = d.p;
+        if (threadIdx.x == 0) {
+            g = d.g;
+            p = d.p;
+        }
+        __syncthreads();
         run_tile<MODE, ST, T1>(d.buf[parity], d.buf[parity ^ 1], g, p, d.partials, nullptr, err, tl.y, tl.z, tl.w,
-                           smem_raw);
+                               smem_raw);
         __syncthreads();
         if (threadIdx.x == 0) {
             uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + stages_of(ST) * stage_bytes<ST>() +
