@@ -45,3 +45,31 @@ def test_default_arm_needs_a_gpu():
     r = run_bench("--steps", "1", "--warmup", "1", "--no-cpu-baseline", "--no-e2e", "--no-batch", timeout=300)
     assert r.returncode != 0
     assert not [ln for ln in r.stdout.splitlines() if ln.startswith("{") and '"value"' in ln]
+
+
+@pytest.mark.gpu
+def test_default_arm_line_on_a_small_domain():
+    """The GPU arm's line on a small domain: the contract keys, the roofline
+    and e2e records (with the set-up split) and the storage form's
+    steady-flux gate."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    r = run_bench("--nx", "1024", "--ny", "512", "--steps", "6", "--warmup", "3", "--no-cpu-baseline",
+                  "--no-batch", timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "roofline", "clocks", "e2e",
+                "gpu_launches"):
+        assert key in d, key
+    assert d["value"] > 0 and d["steps"] == 6 and d["warmup"] == 3 and d["gpu_launches"] >= 6
+    assert d["config"]["storage"] == "fp32dev" and "meets" in d["config"]["storage_steady_flux_gate"]
+    roof = d["roofline"]
+    assert roof["bound"] == "hbm" and roof["unit"] == "GB/s" and 0 < roof["frac"] < 1.5
+    e = d["e2e"]
+    assert e["value"] > 0 and e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
+    parts = e["setup_parts_ms"]
+    assert parts["of which: density upload alone"] > 0 and parts["of which: field kernels alone"] > 0
