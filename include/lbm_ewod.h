@@ -80,6 +80,20 @@ enum { LBM_GREEN_MC = 0, LBM_GREEN_PRINTED = 1 };
  * only where two perpendicular solid faces meet. */
 enum { LBM_NORMAL_FACES = 0, LBM_NORMAL_UNIT = 1 };
 
+/* Thread layout of the step kernel for the 32-bit storage forms (the 16-bit
+ * forms have one layout and ignore the field). No counterpart in the paper:
+ * both layouts compute the same update and store the same bits.
+ * LBM_LAYOUT_PAIRS: each thread updates two neighbouring nodes with paired
+ *                   FP32 instructions (fewer instructions per node; the
+ *                   faster layout once the domain fills the GPU).
+ * LBM_LAYOUT_SINGLE: one node per thread (twice the threads per CTA, which
+ *                   hide more latency on small domains).
+ * LBM_LAYOUT_AUTO (0, the default): pairs unless the domain (a batch: all
+ *                   its domains together) gives no more than 3 CTAs per SM
+ *                   at 4-row segments. A batch takes the first domain's
+ *                   field. */
+enum { LBM_LAYOUT_AUTO = 0, LBM_LAYOUT_PAIRS = 1, LBM_LAYOUT_SINGLE = 2 };
+
 /* Population storage in device memory (arithmetic is FP32 in all forms).
  * LBM_FP32:     the post-collision populations f*_a, FP32 (36 B per node).
  * LBM_FP32_DEV: rho* = sum_a f*_a (FP32) and the deviations
@@ -115,6 +129,7 @@ typedef struct {
                           the step kernel (read with lbm_obs_latest); 0: off */
     int32_t tile_rows; /* rows per CTA segment of the step kernel (>= 4), 0 = auto */
     int32_t normal;    /* LBM_NORMAL_FACES or LBM_NORMAL_UNIT */
+    int32_t layout;    /* LBM_LAYOUT_AUTO, LBM_LAYOUT_PAIRS or LBM_LAYOUT_SINGLE */
 } lbm_params;
 
 typedef struct {

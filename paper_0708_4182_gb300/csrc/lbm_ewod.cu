@@ -49,6 +49,9 @@ bool params_valid(const lbm_params* p, const char** why)
     if (!(p->rho0 > 0.0)) { *why = "rho0 must be > 0"; return false; }
     if (p->green != LBM_GREEN_MC && p->green != LBM_GREEN_PRINTED) { *why = "unknown green convention"; return false; }
     if (p->normal != LBM_NORMAL_FACES && p->normal != LBM_NORMAL_UNIT) { *why = "unknown normal reading"; return false; }
+    if (p->layout != LBM_LAYOUT_AUTO && p->layout != LBM_LAYOUT_PAIRS && p->layout != LBM_LAYOUT_SINGLE) {
+        *why = "unknown thread layout"; return false;
+    }
     if (p->storage < LBM_FP32 || p->storage > LBM_BF16_DEV) { *why = "unsupported storage"; return false; }
     if ((p->storage == LBM_FP16_DEV || p->storage == LBM_BF16_DEV) && (p->nx % 8) != 0) {
         *why = "16-bit storage needs nx to be a multiple of 8"; return false;
@@ -89,7 +92,7 @@ Layout layout_of(const lbm_params* p)
     return L;
 }
 
-int auto_tile_rows(int nx, int ny, int storage, int sm_count)
+int auto_tile_rows(int nx, int ny, int storage, int sm_count, bool pair)
 {
     // Segment height. Each CTA re-stages 4 halo rows, so taller segments waste
     // less, but several waves of CTAs (3 per SM) balance the slower seam
@@ -99,7 +102,7 @@ int auto_tile_rows(int nx, int ny, int storage, int sm_count)
     // the grid has fewer than 4 waves; then even the segments out (same
     // count, heights differing by at most one row) so that no short last
     // segment pays the pipeline start and halo rows for a few rows.
-    const long long slots = (long long)ctas_of(storage) * sm_count;
+    const long long slots = (long long)ctas_of(storage, true, pair) * sm_count;
     int rows = 64;
     while (rows > 4 && (long long)ctas_x(nx, storage) * ((ny + rows - 1) / rows) < 4 * slots) rows >>= 1;
     const int nseg = (ny + rows - 1) / rows;
@@ -572,7 +575,7 @@ __global__ void __launch_bounds__(kAuxThreads)
                 q.rho = q.solid ? 0.f : (dx == 0 && dy == 0 ? nd.rho : rho_at(xn, yn));
                 psi3[dy + 1][dx + 1] = pseudopotential(p, q);
             }
-        collide_node<kObs>(nd, psi3[0], psi3[1], psi3[2], 1, p, g, nullptr, nullptr, x, y, acc);
+        collide_node<kObs, true>(nd, psi3[0], psi3[1], psi3[2], 1, p, g, nullptr, nullptr, x, y, acc);
     }
     // deterministic CTA reduction into this CTA's partial slot
     __shared__ double red_d[4][kAuxThreads / 32];
@@ -634,6 +637,7 @@ struct lbm_ctx {
     double* staging = nullptr;
     int* status = nullptr;
     int sm_count = 0;
+    bool pair = true;  // the 32-bit forms' pair layout (false: one node per thread)
     dim3 grid;
     int64_t t = 0;
     int64_t last_obs_t = -1;
@@ -696,21 +700,35 @@ Phys make_phys(const lbm_params& p)
 
 // The kernel instance: the tau = 1 specialisation unless a step relaxes
 // with tau != 1 (the observing modes never relax).
-template <int MODE, int ST>
-lbm_status launch_step_st(lbm_ctx* c, const float* fin, float* fout, double* fields)
+template <int MODE, int ST, bool PAIR>
+lbm_status launch_step_layout(lbm_ctx* c, const float* fin, float* fout, double* fields)
 {
+    constexpr unsigned nt = threads_of(ST, PAIR);
+    constexpr size_t sm = smem_bytes<ST, PAIR>();
     bool t1 = true;
     if constexpr (MODE == kStep || MODE == kStepObs) {
         if (c->ph.tau != 1.f) {
             t1 = false;
-            step_kernel<MODE, ST, false><<<c->grid, threads_of(ST), smem_bytes<ST>(), c->stream>>>(
-                fin, fout, c->g, c->ph, c->partials, fields, c->status);
+            step_kernel<MODE, ST, false, PAIR><<<c->grid, nt, sm, c->stream>>>(fin, fout, c->g, c->ph, c->partials,
+                                                                              fields, c->status);
         }
     }
     if (t1)
-        step_kernel<MODE, ST, true><<<c->grid, threads_of(ST), smem_bytes<ST>(), c->stream>>>(
-            fin, fout, c->g, c->ph, c->partials, fields, c->status);
+        step_kernel<MODE, ST, true, PAIR><<<c->grid, nt, sm, c->stream>>>(fin, fout, c->g, c->ph, c->partials,
+                                                                         fields, c->status);
     return check_launch(c, "step kernel launch");
+}
+
+// The 16-bit forms have one layout (one node per thread, PAIR = false).
+template <int MODE, int ST>
+lbm_status launch_step_st(lbm_ctx* c, const float* fin, float* fout, double* fields)
+{
+    if constexpr (is16(ST))
+        return launch_step_layout<MODE, ST, false>(c, fin, fout, fields);
+    else if (c->pair)
+        return launch_step_layout<MODE, ST, true>(c, fin, fout, fields);
+    else
+        return launch_step_layout<MODE, ST, false>(c, fin, fout, fields);
 }
 
 template <int MODE>
@@ -724,31 +742,46 @@ lbm_status launch_step(lbm_ctx* c, const float* fin, float* fout, double* fields
     }
 }
 
-// Step kernel (plain step, no observables) of a storage form.
-template <int ST> const void* plain_step_ptr(bool t1)
+// Step kernel (plain step, no observables) of a storage form and layout
+// (the same as launch_step_st picks).
+template <int ST, bool PAIR> const void* plain_step_layout(bool t1)
 {
-    return t1 ? reinterpret_cast<const void*>(&step_kernel<kStep, ST, true>)
-              : reinterpret_cast<const void*>(&step_kernel<kStep, ST, false>);
+    return t1 ? reinterpret_cast<const void*>(&step_kernel<kStep, ST, true, PAIR>)
+              : reinterpret_cast<const void*>(&step_kernel<kStep, ST, false, PAIR>);
 }
 
-const void* plain_step_kernel(int storage, bool t1)
+template <int ST> const void* plain_step_ptr(bool t1, bool pair)
+{
+    if constexpr (is16(ST))
+        return plain_step_layout<ST, false>(t1);
+    else
+        return pair ? plain_step_layout<ST, true>(t1) : plain_step_layout<ST, false>(t1);
+}
+
+const void* plain_step_kernel(int storage, bool t1, bool pair)
 {
     switch (storage) {
-    case LBM_FP32_DEV: return plain_step_ptr<kF32Dev>(t1);
-    case LBM_FP16_DEV: return plain_step_ptr<kF16Dev>(t1);
-    case LBM_BF16_DEV: return plain_step_ptr<kBF16Dev>(t1);
-    default: return plain_step_ptr<kF32>(t1);
+    case LBM_FP32_DEV: return plain_step_ptr<kF32Dev>(t1, pair);
+    case LBM_FP16_DEV: return plain_step_ptr<kF16Dev>(t1, pair);
+    case LBM_BF16_DEV: return plain_step_ptr<kBF16Dev>(t1, pair);
+    default: return plain_step_ptr<kF32>(t1, pair);
     }
 }
 
-size_t step_smem(int storage)
+size_t step_smem(int storage, bool pair)
 {
     switch (storage) {
-    case LBM_FP32_DEV: return smem_bytes<kF32Dev>();
-    case LBM_FP16_DEV: return smem_bytes<kF16Dev>();
-    case LBM_BF16_DEV: return smem_bytes<kBF16Dev>();
-    default: return smem_bytes<kF32>();
+    case LBM_FP32_DEV: return pair ? smem_bytes<kF32Dev, true>() : smem_bytes<kF32Dev, false>();
+    case LBM_FP16_DEV: return smem_bytes<kF16Dev, false>();
+    case LBM_BF16_DEV: return smem_bytes<kBF16Dev, false>();
+    default: return pair ? smem_bytes<kF32, true>() : smem_bytes<kF32, false>();
     }
+}
+
+// threads per CTA of a storage form and layout
+unsigned step_threads(int storage, bool pair)
+{
+    return unsigned(threads_of(storage, pair && !is16(storage)));
 }
 
 // kGraphSteps (even) plain steps starting from the current buffer, as one
@@ -771,10 +804,10 @@ lbm_status step_graph(lbm_ctx* c, cudaGraphExec_t* out)
         float* fout = (k & 1) ? c->cur : c->nxt;
         void* args[] = {&fin, &fout, &c->g, &c->ph, &c->partials, &no_fields, &c->status};
         cudaKernelNodeParams kp{};
-        kp.func = const_cast<void*>(plain_step_kernel(c->prm.storage, c->ph.tau == 1.f));
+        kp.func = const_cast<void*>(plain_step_kernel(c->prm.storage, c->ph.tau == 1.f, c->pair));
         kp.gridDim = c->grid;
-        kp.blockDim = dim3(threads_of(c->prm.storage));
-        kp.sharedMemBytes = static_cast<unsigned>(step_smem(c->prm.storage));
+        kp.blockDim = dim3(step_threads(c->prm.storage, c->pair));
+        kp.sharedMemBytes = static_cast<unsigned>(step_smem(c->prm.storage, c->pair));
         kp.kernelParams = args;
         cudaGraphNode_t node;
         s = check_cuda(c, cudaGraphAddKernelNode(&node, graph, prev ? &prev : nullptr, prev ? 1 : 0, &kp),
@@ -788,15 +821,15 @@ lbm_status step_graph(lbm_ctx* c, cudaGraphExec_t* out)
 }
 
 
-template <int MODE, int ST>
+template <int MODE, int ST, bool PAIR>
 cudaError_t allow_smem_st()
 {
-    cudaError_t e = cudaFuncSetAttribute(step_kernel<MODE, ST, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(smem_bytes<ST>()));
+    cudaError_t e = cudaFuncSetAttribute(step_kernel<MODE, ST, true, PAIR>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_bytes<ST, PAIR>()));
     if constexpr (MODE == kStep || MODE == kStepObs) {
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(step_kernel<MODE, ST, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     int(smem_bytes<ST>()));
+            e = cudaFuncSetAttribute(step_kernel<MODE, ST, false, PAIR>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_bytes<ST, PAIR>()));
     }
     return e;
 }
@@ -804,10 +837,12 @@ cudaError_t allow_smem_st()
 template <int MODE>
 cudaError_t allow_smem()
 {
-    cudaError_t e = allow_smem_st<MODE, kF32>();
-    if (e == cudaSuccess) e = allow_smem_st<MODE, kF32Dev>();
-    if (e == cudaSuccess) e = allow_smem_st<MODE, kF16Dev>();
-    if (e == cudaSuccess) e = allow_smem_st<MODE, kBF16Dev>();
+    cudaError_t e = allow_smem_st<MODE, kF32, true>();
+    if (e == cudaSuccess) e = allow_smem_st<MODE, kF32, false>();
+    if (e == cudaSuccess) e = allow_smem_st<MODE, kF32Dev, true>();
+    if (e == cudaSuccess) e = allow_smem_st<MODE, kF32Dev, false>();
+    if (e == cudaSuccess) e = allow_smem_st<MODE, kF16Dev, false>();
+    if (e == cudaSuccess) e = allow_smem_st<MODE, kBF16Dev, false>();
     return e;
 }
 
@@ -924,7 +959,17 @@ lbm_status lbm_create(const lbm_params* p, void* d_workspace, size_t bytes, void
     c->g.ny = p->ny;
     c->g.pitch = pitch_of(p->nx);
     c->g.plane = p->ny * c->g.pitch;
-    c->g.tile_rows = p->tile_rows ? p->tile_rows : auto_tile_rows(p->nx, p->ny, p->storage, c->sm_count);
+    // Thread layout of the 32-bit forms: pairs, unless the domain is too small
+    // to give the GPU more than 3 CTAs per SM at the smallest segment height
+    // (4 rows); there the one-node layout's twice as many threads per CTA
+    // hide more latency. Measured (MLUPS, FP32 one-node / pairs): 128x64
+    // 1114 / 889, 1024x256 29901 / 27499, 1024x512 34375 / 47015.
+    c->pair = !is16(p->storage) &&
+              (p->layout == LBM_LAYOUT_PAIRS ||
+               (p->layout == LBM_LAYOUT_AUTO &&
+                (long long)ctas_x(p->nx, p->storage) * ((p->ny + 3) / 4) > 3LL * c->sm_count));
+    c->g.tile_rows =
+        p->tile_rows ? p->tile_rows : auto_tile_rows(p->nx, p->ny, p->storage, c->sm_count, c->pair);
     c->grid = dim3(ctas_x(p->nx, p->storage), (p->ny + c->g.tile_rows - 1) / c->g.tile_rows);
     c->ph = make_phys(*p);
     *out = c;
@@ -1359,6 +1404,7 @@ struct lbm_batch {
     int ctas_per_sm = 3;                 // resident CTAs per SM of the persistent grid (1..max_ctas)
     int max_ctas = 3;                    // CTAs of the step kernel instance that fit on one SM
     bool tau1 = true;                    // every domain relaxes with tau = 1 (the tau = 1 kernel instance)
+    bool pair = true;                    // the 32-bit forms' pair layout (false: one node per thread)
     // device tables (in the batch's own workspace region)
     DomainDev* d_dom = nullptr;
     int4* d_tiles = nullptr;
@@ -1516,33 +1562,35 @@ lbm_status upload_tables(lbm_batch* b, bool all)
 }
 
 // t1: every domain of the batch relaxes with tau = 1
+template <int ST, bool PAIR>
+const void* batch_kernel_layout(int mode, bool t1)
+{
+    if (mode == kObs) return reinterpret_cast<const void*>(&batch_step_kernel<kObs, ST, true, PAIR>);
+    return t1 ? reinterpret_cast<const void*>(&batch_step_kernel<kStep, ST, true, PAIR>)
+              : reinterpret_cast<const void*>(&batch_step_kernel<kStep, ST, false, PAIR>);
+}
+
 template <int ST>
-const void* batch_kernel_ptr(int mode, bool t1)
+const void* batch_kernel_ptr(int mode, bool t1, bool pair)
 {
-    if (mode == kObs) return reinterpret_cast<const void*>(&batch_step_kernel<kObs, ST, true>);
-    return t1 ? reinterpret_cast<const void*>(&batch_step_kernel<kStep, ST, true>)
-              : reinterpret_cast<const void*>(&batch_step_kernel<kStep, ST, false>);
+    if constexpr (is16(ST))
+        return batch_kernel_layout<ST, false>(mode, t1);
+    else
+        return pair ? batch_kernel_layout<ST, true>(mode, t1) : batch_kernel_layout<ST, false>(mode, t1);
 }
 
-const void* batch_kernel(int storage, int mode, bool t1)
+const void* batch_kernel(int storage, int mode, bool t1, bool pair)
 {
     switch (storage) {
-    case LBM_FP32_DEV: return batch_kernel_ptr<kF32Dev>(mode, t1);
-    case LBM_FP16_DEV: return batch_kernel_ptr<kF16Dev>(mode, t1);
-    case LBM_BF16_DEV: return batch_kernel_ptr<kBF16Dev>(mode, t1);
-    default: return batch_kernel_ptr<kF32>(mode, t1);
+    case LBM_FP32_DEV: return batch_kernel_ptr<kF32Dev>(mode, t1, pair);
+    case LBM_FP16_DEV: return batch_kernel_ptr<kF16Dev>(mode, t1, pair);
+    case LBM_BF16_DEV: return batch_kernel_ptr<kBF16Dev>(mode, t1, pair);
+    default: return batch_kernel_ptr<kF32>(mode, t1, pair);
     }
 }
 
-size_t batch_smem(int storage)
-{
-    switch (storage) {
-    case LBM_FP32_DEV: return smem_bytes<kF32Dev>();
-    case LBM_FP16_DEV: return smem_bytes<kF16Dev>();
-    case LBM_BF16_DEV: return smem_bytes<kBF16Dev>();
-    default: return smem_bytes<kF32>();
-    }
-}
+// the batch kernel's dynamic shared memory: the single-domain step's
+size_t batch_smem(int storage, bool pair) { return step_smem(storage, pair); }
 
 int batch_grid(const lbm_batch* b)
 {
@@ -1555,9 +1603,9 @@ lbm_status launch_batch(lbm_batch* b, int mode, int parity)
     if (b->ntiles == 0) return LBM_OK;
     int nt = b->ntiles;
     void* args[] = {&b->d_dom, &b->d_tiles, &nt, &parity, &b->d_status};
-    return bcheck(b, cudaLaunchKernel(batch_kernel(b->storage, mode, b->tau1), dim3(batch_grid(b)),
-                                      dim3(threads_of(b->storage)), args,
-                                      batch_smem(b->storage), b->stream),
+    return bcheck(b, cudaLaunchKernel(batch_kernel(b->storage, mode, b->tau1, b->pair), dim3(batch_grid(b)),
+                                      dim3(step_threads(b->storage, b->pair)), args,
+                                      batch_smem(b->storage, b->pair), b->stream),
                   "batch step launch");
 }
 
@@ -1577,10 +1625,10 @@ lbm_status batch_graph(lbm_batch* b)
     for (int k = 0; k < 2; ++k) {
         void* args[] = {&b->d_dom, &b->d_tiles, &nt, &parities[k], &b->d_status};
         cudaKernelNodeParams kp{};
-        kp.func = const_cast<void*>(batch_kernel(b->storage, kStep, b->tau1));
+        kp.func = const_cast<void*>(batch_kernel(b->storage, kStep, b->tau1, b->pair));
         kp.gridDim = dim3(grid);
-        kp.blockDim = dim3(threads_of(b->storage));
-        kp.sharedMemBytes = unsigned(batch_smem(b->storage));
+        kp.blockDim = dim3(step_threads(b->storage, b->pair));
+        kp.sharedMemBytes = unsigned(batch_smem(b->storage, b->pair));
         kp.kernelParams = args;
         cudaGraphNode_t node;
         if ((s = bcheck(b, cudaGraphAddKernelNode(&node, b->graph, prev ? &prev : nullptr, prev ? 1 : 0, &kp),
@@ -1705,17 +1753,32 @@ lbm_status lbm_batch_create(const lbm_params* params, int32_t count, void* d_wor
     cudaError_t e = cudaSuccess;
     for (int d = 0; d < count; ++d)
         if (b->ctx[d]->ph.tau != 1.f) b->tau1 = false;
+    // Thread layout (32-bit forms), by the rule of a single domain applied to
+    // the whole batch: pairs unless all domains together give the GPU no
+    // more than 3 CTAs per SM at 4-row segments; the first domain's layout
+    // field may force either.
+    {
+        long long tiles4 = 0;
+        for (int d = 0; d < count; ++d)
+            tiles4 += (long long)ctas_x(params[d].nx, params[d].storage) * ((params[d].ny + 3) / 4);
+        const int lay = params[0].layout;
+        b->pair = !is16(b->storage) &&
+                  (lay == LBM_LAYOUT_PAIRS || (lay == LBM_LAYOUT_AUTO && tiles4 > 3LL * b->sm_count));
+    }
     for (int st = 0; st < 4 && e == cudaSuccess; ++st) {
-        for (int t1 = 0; t1 < 2 && e == cudaSuccess; ++t1)
-            e = cudaFuncSetAttribute(batch_kernel(st, kStep, t1 != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     int(batch_smem(st)));
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(batch_kernel(st, kObs, true), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     int(batch_smem(st)));
+        for (int pr = 0; pr < 2 && e == cudaSuccess; ++pr) {
+            for (int t1 = 0; t1 < 2 && e == cudaSuccess; ++t1)
+                e = cudaFuncSetAttribute(batch_kernel(st, kStep, t1 != 0, pr != 0),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(batch_smem(st, pr != 0)));
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(batch_kernel(st, kObs, true, pr != 0),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(batch_smem(st, pr != 0)));
+        }
     }
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->max_ctas, batch_kernel(b->storage, kStep, b->tau1),
-                                                          threads_of(b->storage), batch_smem(b->storage));
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &b->max_ctas, batch_kernel(b->storage, kStep, b->tau1, b->pair), step_threads(b->storage, b->pair),
+            batch_smem(b->storage, b->pair));
     if (e == cudaSuccess && b->max_ctas < 1) e = cudaErrorInvalidConfiguration;
     b->ctas_per_sm = b->max_ctas;
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream);

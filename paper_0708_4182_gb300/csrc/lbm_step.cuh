@@ -21,8 +21,9 @@
 //    the stage's "full" mbarrier; pieces that cannot move in 16-byte units
 //    (periodic seam, ragged strips of the FP32 forms) go by 4-byte cp.async
 //    that arrive on the same barrier, so the producer never waits for a load;
-//  - kW/32 consumer warps pull one node's 9 populations per thread out of the
-//    ring (bounce-back values come from the same stage, no dependent loads),
+//  - the consumer warps pull the 9 populations of one node per thread, or of
+//    two neighbouring nodes per thread in the 32-bit forms' pair layout, out
+//    of the ring (bounce-back values come from the same stage, no dependent loads),
 //    form rho and psi, write psi into a 4-row ring, meet at a named barrier,
 //    then compute the 8-neighbour forces of the previous row, collide and
 //    store f* with coalesced stores; each warp then frees its ring stage on
@@ -67,12 +68,14 @@ constexpr int kPartialStride = 8;              // doubles per CTA in the partial
 constexpr uint32_t kWaitLimit = 1u << 18;      // try_wait rounds before giving up (about 1 s on a GB300)
 
 enum Storage { kF32 = 0, kF32Dev = 1, kF16Dev = 2, kBF16Dev = 3 };
+__host__ __device__ constexpr bool is16(int st) { return st == kF16Dev || st == kBF16Dev; }
 
 // Staging ring depth (rows) and resident CTAs per SM the launch bounds aim
-// at. The 16-bit forms (288 threads): 6 and 3. The 32-bit forms (160
-// threads, a pair of nodes per thread): LBM_STAGES_F32 / LBM_CTAS_F32 and
-// LBM_STAGES_F32DEV / LBM_CTAS_F32DEV for the tau = 1 instances, whose
-// register needs are lower; the tau != 1 instances aim at 3.
+// at. The 16-bit forms and the one-node layout of the 32-bit forms (288
+// threads): 6 and 3. The pair layout of the 32-bit forms (160 threads, a pair
+// of nodes per thread): LBM_STAGES_F32 / LBM_CTAS_F32 and LBM_STAGES_F32DEV /
+// LBM_CTAS_F32DEV for the tau = 1 instances, whose register needs are lower;
+// the tau != 1 instances aim at 3.
 // Shared memory and registers must allow that many CTAs. Measured at
 // 16384x4096 (GLUPS, FP32 / FP32 deviations / batch FP32 / batch FP32
 // deviations): 6 stages x 3 CTAs 89.4 / 85.9 / 80.5 / 72.8; FP32 4 x 5 and
@@ -89,25 +92,27 @@ enum Storage { kF32 = 0, kF32Dev = 1, kF16Dev = 2, kBF16Dev = 3 };
 #ifndef LBM_CTAS_F32DEV
 #define LBM_CTAS_F32DEV 4
 #endif
-__host__ __device__ constexpr int stages_of(int st)
+// pair: the 32-bit forms' pair layout (ignored by the 16-bit forms)
+__host__ __device__ constexpr int stages_of(int st, bool pair = true)
 {
-    return st == kF32 ? LBM_STAGES_F32 : st == kF32Dev ? LBM_STAGES_F32DEV : 6;
+    return !pair ? 6 : st == kF32 ? LBM_STAGES_F32 : st == kF32Dev ? LBM_STAGES_F32DEV : 6;
 }
-__host__ __device__ constexpr int ctas_of(int st, bool t1 = true)
+__host__ __device__ constexpr int ctas_of(int st, bool t1 = true, bool pair = true)
 {
-    return st == kF32 ? (t1 ? LBM_CTAS_F32 : 3) : st == kF32Dev ? (t1 ? LBM_CTAS_F32DEV : 3) : 3;
+    return !pair ? 3 : st == kF32 ? (t1 ? LBM_CTAS_F32 : 3) : st == kF32Dev ? (t1 ? LBM_CTAS_F32DEV : 3) : 3;
 }
 // the persistent batch kernel: as the single-domain step; its observing mode
 // aims at 3 (it spills at 4)
-__host__ __device__ constexpr int batch_ctas_of(int mode, int st, bool t1)
+__host__ __device__ constexpr int batch_ctas_of(int mode, int st, bool t1, bool pair = true)
 {
-    return mode == 0 ? ctas_of(st, t1) : (ctas_of(st, t1) > 3 ? 3 : ctas_of(st, t1));
+    return mode == 0 ? ctas_of(st, t1, pair) : (ctas_of(st, t1, pair) > 3 ? 3 : ctas_of(st, t1, pair));
 }
 // the single-domain kernel of a mode: the observing modes keep their
 // reduction state too and aim at one CTA less (no spills)
-__host__ __device__ constexpr int step_ctas_of(int mode, int st, bool t1)
+__host__ __device__ constexpr int step_ctas_of(int mode, int st, bool t1, bool pair = true)
 {
-    return mode == 0 ? ctas_of(st, t1) : (ctas_of(st, t1) > 3 ? ctas_of(st, t1) - 1 : ctas_of(st, t1));
+    return mode == 0 ? ctas_of(st, t1, pair)
+                     : (ctas_of(st, t1, pair) > 3 ? ctas_of(st, t1, pair) - 1 : ctas_of(st, t1, pair));
 }
 
 // T: type of the 8 values after plane 0 (populations or deviations); align:
@@ -123,11 +128,12 @@ template <> struct StoreT<kBF16Dev> { using T = __nv_bfloat16; static constexpr 
 // Columns a CTA collides: kW, or kW - 2 where neighbouring strips overlap.
 __host__ __device__ constexpr int strip_cols(int st) { return (st == kF16Dev || st == kBF16Dev) ? kW - 2 : kW; }
 
-// Consumer threads per CTA: the 32-bit forms give each thread a pair of
-// neighbouring columns (packed two-lane FP32 arithmetic, see run_tile), the
-// 16-bit forms one column. One producer warp comes on top.
-__host__ __device__ constexpr int consumers(int st) { return (st == kF16Dev || st == kBF16Dev) ? kW : kW / 2; }
-__host__ __device__ constexpr int threads_of(int st) { return consumers(st) + 32; }
+// Consumer threads per CTA: the pair layout of the 32-bit forms gives each
+// thread a pair of neighbouring columns (packed two-lane FP32 arithmetic, see
+// run_tile); the one-node layout and the 16-bit forms one column. One
+// producer warp comes on top.
+__host__ __device__ constexpr int consumers(int st, bool pair = true) { return (is16(st) || !pair) ? kW : kW / 2; }
+__host__ __device__ constexpr int threads_of(int st, bool pair = true) { return consumers(st, pair) + 32; }
 
 // Element index of deviation a (1..8) of the node at o = y * pitch + x among
 // the deviation values that follow plane 0 (plane = ny * pitch): FP32
@@ -144,9 +150,9 @@ template <int ST> __host__ __device__ constexpr size_t stage_bytes()
 {
     return size_t(kRowLen) * (sizeof(float) + 8 * sizeof(typename StoreT<ST>::T));
 }
-template <int ST> __host__ __device__ constexpr size_t smem_bytes()
+template <int ST, bool PAIR = true> __host__ __device__ constexpr size_t smem_bytes()
 {
-    return stages_of(ST) * (stage_bytes<ST>() + 2 * sizeof(uint64_t)) + 4 * kPsiStride * sizeof(float) + 128;
+    return stages_of(ST, PAIR) * (stage_bytes<ST>() + 2 * sizeof(uint64_t)) + 4 * kPsiStride * sizeof(float) + 128;
 }
 // bytes of one node's state in global memory (plane 0 + the other 8 values)
 template <int ST> __host__ __device__ constexpr int node_bytes() { return 4 + 8 * int(sizeof(typename StoreT<ST>::T)); }
@@ -165,8 +171,6 @@ template <typename T> __device__ __forceinline__ T from_f(float v);
 template <> __device__ __forceinline__ float from_f<float>(float v) { return v; }
 template <> __device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v * kF16Scale); }
 template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
-
-constexpr size_t kSmemBytes = smem_bytes<kF32>();
 
 struct Geom {
     int nx, ny;
@@ -394,50 +398,55 @@ struct ObsAcc {
     unsigned bad = 0;
 };
 
-// Forces, velocity shift, collision and the mode's epilogue for one fluid node
-// (x, r) whose pulled populations are `n`; psi rows r-1, r, r+1 are pm, pc, pp
-// (indexed by ring column t = node column - x0 + 1).
+// Eq. 6 and the electric force of a node with solid pull sources (flags sb,
+// nonzero), added to the negated Eq. 5 sums nsgx, nsgy: the node's force
+// before the body force. Written with explicit roundings (no contraction
+// left to the compiler) so that the one-node and the two-node kernels give
+// the same bits.
+__device__ __forceinline__ void wall_electric(uint32_t sb, float psi, float nsgx, float nsgy, float rho,
+                                              const Phys& p, float& fx, float& fy)
+{
+    // S(x + e_a) = solid flag of the pull source of the opposite direction
+    const float sE = (sb >> 3) & 1, sW = (sb >> 1) & 1;    // (x+1,y), (x-1,y)
+    const float sN = (sb >> 4) & 1, sS = (sb >> 2) & 1;    // (x,y+1), (x,y-1)
+    const float sNE = (sb >> 7) & 1, sNW = (sb >> 8) & 1;  // (x+1,y+1), (x-1,y+1)
+    const float sSW = (sb >> 5) & 1, sSE = (sb >> 6) & 1;  // (x-1,y-1), (x+1,y-1)
+    // Eq. 6: sum_a W_a S(x+e_a) e_a (the flag differences are exact)
+    const float swx = fmaf(p.w_axis, sE - sW, __fmul_rn(p.w_diag, (sNE - sNW) + (sSE - sSW)));
+    const float swy = fmaf(p.w_axis, sN - sS, __fmul_rn(p.w_diag, (sNE + sNW) - (sSE + sSW)));
+    fx = __fmul_rn(psi, __fsub_rn(nsgx, swx));
+    fy = __fmul_rn(psi, __fsub_rn(nsgy, swy));
+    // electric force f n on the conductive single layer next to a wall
+    if (rho >= p.rho_c) {
+        const float ex = sE - sW, ey = sN - sS;
+        const float fe = (ex != 0.f && ey != 0.f) ? __fmul_rn(p.f_elec, p.e_corner) : p.f_elec;
+        fx = fmaf(fe, ex, fx);
+        fy = fmaf(fe, ey, fy);
+    }
+}
+
 // Total force on one fluid node: Eq. 5 from the psi rows pm, pc, pp (ring
 // column t), Eq. 6 and the electric wall-layer force from the solid flags of
-// the pull sources (n.sb), and the body force. N has fields rho and sb.
+// the pull sources (n.sb), and the body force. N has fields rho and sb. The
+// sign of Eq. 5 is carried by the constants (-G: round to nearest is
+// symmetric, so this is exactly the negated sum); every operation is the
+// two-node kernel's (node_force2) lane for lane.
 template <typename N>
 __device__ __forceinline__ void node_force(const N& n, const float* pm, const float* pc, const float* pp,
                                            int t, const Phys& p, float& Fx_out, float& Fy_out)
 {
     const float psi = pc[t];
-    // Eq. 5: sum_a G_a psi(x+e_a) e_a, axis and diagonal links
-    const float sgx = p.g_axis * (pc[t + 1] - pc[t - 1]) +
-                      p.g_diag * ((pp[t + 1] - pp[t - 1]) + (pm[t + 1] - pm[t - 1]));
-    const float sgy = p.g_axis * (pp[t] - pm[t]) +
-                      p.g_diag * ((pp[t + 1] + pp[t - 1]) - (pm[t + 1] + pm[t - 1]));
-    float Fx, Fy;
-    const uint32_t sb = n.sb;
-    if (sb == 0) {
-        // no solid neighbour: Eq. 6 and the electric force vanish
-        Fx = -psi * sgx;
-        Fy = -psi * sgy;
-    } else {
-        // S(x + e_a) = solid flag of the pull source of the opposite direction
-        const float sE = (sb >> 3) & 1, sW = (sb >> 1) & 1;    // (x+1,y), (x-1,y)
-        const float sN = (sb >> 4) & 1, sS = (sb >> 2) & 1;    // (x,y+1), (x,y-1)
-        const float sNE = (sb >> 7) & 1, sNW = (sb >> 8) & 1;  // (x+1,y+1), (x-1,y+1)
-        const float sSW = (sb >> 5) & 1, sSE = (sb >> 6) & 1;  // (x-1,y-1), (x+1,y-1)
-        // Eq. 6: sum_a W_a S(x+e_a) e_a
-        const float swx = p.w_axis * (sE - sW) + p.w_diag * ((sNE - sNW) + (sSE - sSW));
-        const float swy = p.w_axis * (sN - sS) + p.w_diag * ((sNE + sNW) - (sSE + sSW));
-        Fx = -psi * (sgx + swx);
-        Fy = -psi * (sgy + swy);
-        // electric force f n on the conductive single layer next to a wall
-        if (n.rho >= p.rho_c) {
-            const float ex = sE - sW, ey = sN - sS;
-            const float fe = (ex != 0.f && ey != 0.f) ? p.f_elec * p.e_corner : p.f_elec;
-            Fx += fe * ex;
-            Fy += fe * ey;
-        }
-    }
+    const float dxc = pc[t + 1] - pc[t - 1];
+    const float dxp = pp[t + 1] - pp[t - 1], dxm = pm[t + 1] - pm[t - 1];
+    const float sxp = pp[t + 1] + pp[t - 1], sxm = pm[t + 1] + pm[t - 1];
+    // Eq. 5: -sum_a G_a psi(x+e_a) e_a, axis and diagonal links
+    const float nsgx = fmaf(-p.g_axis, dxc, __fmul_rn(-p.g_diag, __fadd_rn(dxp, dxm)));
+    const float nsgy = fmaf(-p.g_axis, __fsub_rn(pp[t], pm[t]), __fmul_rn(-p.g_diag, __fsub_rn(sxp, sxm)));
+    float Fx = __fmul_rn(psi, nsgx), Fy = __fmul_rn(psi, nsgy);
+    if (n.sb != 0) wall_electric(n.sb, psi, nsgx, nsgy, n.rho, p, Fx, Fy);
     // body force on every fluid node
-    Fx_out = Fx + n.rho * p.bfx;
-    Fy_out = Fy + n.rho * p.bfy;
+    Fx_out = fmaf(n.rho, p.bfx, Fx);
+    Fy_out = fmaf(n.rho, p.bfy, Fy);
 }
 
 // Observables or fields epilogue of one fluid node (modes other than kStep).
@@ -462,7 +471,8 @@ __device__ __forceinline__ void node_observe(float rho, float rinv, float jx, fl
             acc.q.add(vx);
             acc.px.add(mx);
             acc.py.add(my);
-            acc.umax2 = fmaxf(acc.umax2, vx * vx + vy * vy);
+            // explicit roundings: the same |u|^2 in every kernel instance
+            acc.umax2 = fmaxf(acc.umax2, fmaf(vx, vx, __fmul_rn(vy, vy)));
             acc.rmin = fminf(acc.rmin, rho);
         } else {
             ++acc.bad;
@@ -470,10 +480,21 @@ __device__ __forceinline__ void node_observe(float rho, float rinv, float jx, fl
     }
 }
 
+// n / d by the corrected reciprocal r ~ 1/d (div_corrected) with nd = -d,
+// written as the two-node kernel writes it (div2), operation for operation.
+__device__ __forceinline__ float div1(float n, float nd, float r)
+{
+    const float q0 = __fmul_rn(n, r);
+    const float e = fmaf(q0, nd, n);
+    return fmaf(e, r, q0);
+}
+
 // Forces, velocity shift, collision and the mode's epilogue for one fluid node
 // (x, r) in plain storage, whose pulled populations are `n`; psi rows r-1, r,
-// r+1 are pm, pc, pp (indexed by ring column t = node column - x0 + 1).
-template <int MODE>
+// r+1 are pm, pc, pp (indexed by the node's ring column t). Every operation is
+// the two-node kernel's (collide_pair) lane for lane, so the one-node and
+// two-node layouts store the same bits.
+template <int MODE, bool T1>
 __device__ __forceinline__ void collide_node(const Pulled& n, const float* pm, const float* pc,
                                              const float* pp, int t, const Phys& p, const Geom& g,
                                              float* __restrict__ fout, double* __restrict__ fields,
@@ -488,35 +509,33 @@ __device__ __forceinline__ void collide_node(const Pulled& n, const float* pm, c
         // from one corrected rho/9 by exact power-of-two scalings, so
         // sum_a f_eq = rho has no systematic bias (1/9 in FP32 is 7.5e-9 too
         // large, which would add mass every step); at tau = 1 f* = f_eq.
-        const float ux = div_corrected(fmaf(p.tau, Fx, n.jx), n.rho, rinv);
-        const float uy = div_corrected(fmaf(p.tau, Fy, n.jy), n.rho, rinv);
-        const float om = 1.f - 1.5f * fmaf(ux, ux, uy * uy);
-        const float r9 = div_corrected(n.rho, 9.f, 1.f / 9.f);
-        const float w0r = 4.f * r9, w1r = r9, w2r = 0.25f * r9;
-        const float d5 = ux + uy, d6 = uy - ux;
-        // f_eq_a = w_a rho (1 + 3 c + 4.5 c^2 - 1.5 u^2), c = e_a . u
-        auto poly = [om](float c) { return fmaf(c, fmaf(4.5f, c, 3.f), om); };
-        float feq[9];
-        feq[0] = w0r * om;
-        feq[1] = w1r * poly(ux);
-        feq[2] = w1r * poly(uy);
-        feq[3] = w1r * poly(-ux);
-        feq[4] = w1r * poly(-uy);
-        feq[5] = w2r * poly(d5);
-        feq[6] = w2r * poly(d6);
-        feq[7] = w2r * poly(-d5);
-        feq[8] = w2r * poly(-d6);
-        float* o = fout + r * g.pitch + x;
-        if (p.tau == 1.f) {
+        const float ux = div1(fmaf(p.tau, Fx, n.jx), -n.rho, rinv);
+        const float uy = div1(fmaf(p.tau, Fy, n.jy), -n.rho, rinv);
+        const float om = fmaf(-1.5f, fmaf(ux, ux, __fmul_rn(uy, uy)), 1.f);
+        const float r9 = div1(n.rho, -9.f, 1.f / 9.f);
+        const float w0r = __fmul_rn(4.f, r9), w2r = __fmul_rn(0.25f, r9);
+        const float d5 = __fadd_rn(ux, uy), d6 = __fsub_rn(uy, ux);
+        // f_eq_a = w_a rho (1 + 3 c + 4.5 c^2 - 1.5 u^2) with c = +-(e_a . u):
+        // (-c)(4.5(-c) + 3) = c (4.5 c - 3) exactly
+        auto polyp = [om](float c) { return fmaf(c, fmaf(4.5f, c, 3.f), om); };
+        auto polym = [om](float c) { return fmaf(c, fmaf(4.5f, c, -3.f), om); };
+        float fs[9];
+        fs[0] = __fmul_rn(w0r, om);
+        fs[1] = __fmul_rn(r9, polyp(ux));
+        fs[2] = __fmul_rn(r9, polyp(uy));
+        fs[3] = __fmul_rn(r9, polym(ux));
+        fs[4] = __fmul_rn(r9, polym(uy));
+        fs[5] = __fmul_rn(w2r, polyp(d5));
+        fs[6] = __fmul_rn(w2r, polyp(d6));
+        fs[7] = __fmul_rn(w2r, polym(d5));
+        fs[8] = __fmul_rn(w2r, polym(d6));
+        if (!T1 && p.tau != 1.f) {
 #pragma unroll
-            for (int a = 0; a < 9; ++a) o[a * g.plane] = feq[a];
-        } else {
-#pragma unroll
-            for (int a = 0; a < 9; ++a) {
-                const float fa = n.f[a];
-                o[a * g.plane] = fmaf(feq[a] - fa, p.inv_tau, fa);
-            }
+            for (int a = 0; a < 9; ++a) fs[a] = fmaf(__fsub_rn(fs[a], n.f[a]), p.inv_tau, n.f[a]);
         }
+        float* o = fout + r * g.pitch + x;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) o[a * g.plane] = fs[a];
     }
     if constexpr (MODE != kStep) node_observe<MODE>(n.rho, rinv, n.jx, n.jy, Fx, Fy, g, fields, x, r, acc);
 }
@@ -634,7 +653,9 @@ __device__ __forceinline__ void pull_dev(const float* __restrict__ s0m, const fl
 
 // Collision in deviation form: stores rho in plane 0 and the raw
 // d*_a = f*_a - w_a rho after it (the equilibrium's deviation part
-// w_a rho (3 c + 4.5 c^2 - 1.5 u^2) is formed without its leading 1).
+// w_a rho (3 c + 4.5 c^2 - 1.5 u^2) is formed without its leading 1). For
+// FP32 deviations every operation is the two-node kernel's
+// (collide_dev_pair) lane for lane.
 template <int MODE, typename T, bool T1>
 __device__ __forceinline__ void collide_dev(const PulledDev& n, const float* pm, const float* pc,
                                             const float* pp, int t, const Phys& p, const Geom& g,
@@ -645,52 +666,46 @@ __device__ __forceinline__ void collide_dev(const PulledDev& n, const float* pm,
     node_force(n, pm, pc, pp, t, p, Fx, Fy);
     const float rinv = rcp_approx(n.rho);
     if constexpr (MODE == kStep || MODE == kStepObs) {
-        const float ux = div_corrected(fmaf(p.tau, Fx, n.jx), n.rho, rinv);
-        const float uy = div_corrected(fmaf(p.tau, Fy, n.jy), n.rho, rinv);
-        const float usq = 1.5f * fmaf(ux, ux, uy * uy);
-        const float r9 = div_corrected(n.rho, 9.f, 1.f / 9.f);
-        const float w1r = r9 * RawScale<T>::scale, w2r = 0.25f * w1r;
-        const float d5 = ux + uy, d6 = uy - ux;
-        auto dpoly = [usq](float c) { return fmaf(c, fmaf(4.5f, c, 3.f), -usq); };
+        const float ux = div1(fmaf(p.tau, Fx, n.jx), -n.rho, rinv);
+        const float uy = div1(fmaf(p.tau, Fy, n.jy), -n.rho, rinv);
+        const float nusq = __fmul_rn(-1.5f, fmaf(ux, ux, __fmul_rn(uy, uy)));
+        // power-of-two scaling to raw units: exact
+        const float w1r = __fmul_rn(div1(n.rho, -9.f, 1.f / 9.f), RawScale<T>::scale);
+        const float w2r = __fmul_rn(0.25f, w1r);
+        const float d5 = __fadd_rn(ux, uy), d6 = __fsub_rn(uy, ux);
+        auto dpolyp = [nusq](float c) { return fmaf(c, fmaf(4.5f, c, 3.f), nusq); };
+        auto dpolym = [nusq](float c) { return fmaf(c, fmaf(4.5f, c, -3.f), nusq); };
         float dq[9];
-        dq[1] = w1r * dpoly(ux);
-        dq[2] = w1r * dpoly(uy);
-        dq[3] = w1r * dpoly(-ux);
-        dq[4] = w1r * dpoly(-uy);
-        dq[5] = w2r * dpoly(d5);
-        dq[6] = w2r * dpoly(d6);
-        dq[7] = w2r * dpoly(-d5);
-        dq[8] = w2r * dpoly(-d6);
+        dq[1] = __fmul_rn(w1r, dpolyp(ux));
+        dq[2] = __fmul_rn(w1r, dpolyp(uy));
+        dq[3] = __fmul_rn(w1r, dpolym(ux));
+        dq[4] = __fmul_rn(w1r, dpolym(uy));
+        dq[5] = __fmul_rn(w2r, dpolyp(d5));
+        dq[6] = __fmul_rn(w2r, dpolyp(d6));
+        dq[7] = __fmul_rn(w2r, dpolym(d5));
+        dq[8] = __fmul_rn(w2r, dpolym(d6));
+        if (!T1 && p.tau != 1.f) {
+#pragma unroll
+            for (int a = 1; a < 9; ++a) dq[a] = fmaf(__fsub_rn(dq[a], n.g[a]), p.inv_tau, n.g[a]);
+        }
         const int o = r * g.pitch + x;
         fout0[o] = n.rho;
         if constexpr (sizeof(T) == 2) {
-            float v[9];
-            if (T1 || p.tau == 1.f) {
-#pragma unroll
-                for (int a = 1; a < 9; ++a) v[a] = dq[a];
-            } else {
-#pragma unroll
-                for (int a = 1; a < 9; ++a) v[a] = fmaf(dq[a] - n.g[a], p.inv_tau, n.g[a]);
-            }
             // the node's 8 deviations in one 16-byte store (paired conversions,
             // each value rounded to nearest as alone)
             uint32_t w[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                T lo = from_raw<T>(v[2 * k + 1]), hi = from_raw<T>(v[2 * k + 2]);
+                T lo = from_raw<T>(dq[2 * k + 1]), hi = from_raw<T>(dq[2 * k + 2]);
                 unsigned short bl, bh;
                 memcpy(&bl, &lo, 2);
                 memcpy(&bh, &hi, 2);
                 w[k] = uint32_t(bl) | (uint32_t(bh) << 16);
             }
             *reinterpret_cast<uint4*>(foutd + size_t(o) * 8) = make_uint4(w[0], w[1], w[2], w[3]);
-        } else if (T1 || p.tau == 1.f) {
-#pragma unroll
-            for (int a = 1; a < 9; ++a) foutd[(a - 1) * g.plane + o] = from_raw<T>(dq[a]);
         } else {
 #pragma unroll
-            for (int a = 1; a < 9; ++a)
-                foutd[(a - 1) * g.plane + o] = from_raw<T>(fmaf(dq[a] - n.g[a], p.inv_tau, n.g[a]));
+            for (int a = 1; a < 9; ++a) foutd[(a - 1) * g.plane + o] = from_raw<T>(dq[a]);
         }
     }
     if constexpr (MODE != kStep) node_observe<MODE>(n.rho, rinv, n.jx, n.jy, Fx, Fy, g, fields, x, r, acc);
@@ -871,25 +886,9 @@ __device__ __forceinline__ void node_force2(float2 rho, const uint32_t (&sb)[2],
     if ((sb[0] | sb[1]) != 0) {
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-            const uint32_t b = sb[k];
-            if (b == 0) continue;
-            const float sE = (b >> 3) & 1, sW = (b >> 1) & 1;
-            const float sN = (b >> 4) & 1, sS = (b >> 2) & 1;
-            const float sNE = (b >> 7) & 1, sNW = (b >> 8) & 1;
-            const float sSW = (b >> 5) & 1, sSE = (b >> 6) & 1;
-            // Eq. 6: sum_a W_a S(x+e_a) e_a
-            const float swx = p.w_axis * (sE - sW) + p.w_diag * ((sNE - sNW) + (sSE - sSW));
-            const float swy = p.w_axis * (sN - sS) + p.w_diag * ((sNE + sNW) - (sSE + sSW));
-            const float ps = lane_of(psi, k);
-            float fx = ps * (lane_of(nsgx, k) - swx);
-            float fy = ps * (lane_of(nsgy, k) - swy);
-            // electric force f n on the conductive single layer next to a wall
-            if (lane_of(rho, k) >= p.rho_c) {
-                const float ex = sE - sW, ey = sN - sS;
-                const float fe = (ex != 0.f && ey != 0.f) ? p.f_elec * p.e_corner : p.f_elec;
-                fx += fe * ex;
-                fy += fe * ey;
-            }
+            if (sb[k] == 0) continue;
+            float fx, fy;
+            wall_electric(sb[k], lane_of(psi, k), lane_of(nsgx, k), lane_of(nsgy, k), lane_of(rho, k), p, fx, fy);
             set_lane(Fx, k, fx);
             set_lane(Fy, k, fy);
         }
@@ -1044,29 +1043,34 @@ __device__ __forceinline__ void mbar_inval(uint64_t* bar)
 // [by*tile_rows, (by+1)*tile_rows); per-CTA observables go to
 // partials[slot]. smem_raw is the dynamic shared memory.
 //
-// Consumer thread t pulls node column x0 - P + t and writes its psi into
-// column t + 1 - P of the psi ring, whose columns 0 .. nint + 1 hold the
-// strip's columns x0 - 1 .. x0 + nint. Two layouts (P = StoreT<ST>::overlap):
-//  - P = 0 (32-bit forms, bound by DRAM): strips of kW columns at
-//    x0 = bx*kW. Thread t pulls and collides column x0 + t; threads 0 and
-//    nint - 1 also pull the halo columns x0 - 1 and x0 + nint. Warp stores
-//    cover whole 128-byte lines.
+// Three layouts of the consumer threads (P = StoreT<ST>::overlap):
+//  - P = 0, PAIR (32-bit forms, large domains, bound by DRAM): strips of kW
+//    columns at x0 = bx*kW, kW/2 consumer threads, thread t owning the two
+//    columns x0 + 2t and x0 + 2t + 1 (see the consumer section below);
+//  - P = 0, one node per thread (32-bit forms, domains too small to fill the
+//    GPU with pair CTAs, where twice the threads per CTA hide more latency):
+//    thread t pulls and collides column x0 + t and writes its psi into ring
+//    column t + 1; threads 0 and nint - 1 also pull the halo columns x0 - 1
+//    and x0 + nint (ring columns 0 and nint + 1);
 //  - P = 1 (16-bit forms, bound by instruction issue): strips of kW - 2
-//    columns at x0 = bx*(kW-2). Thread t pulls column x0 - 1 + t, so the
-//    halo columns come from threads 0 and nint + 1 like every other column
-//    and all consumer warps do the same work; threads 1 .. nint collide.
-//    Neighbouring strips overlap by two pulled columns.
-// In both the producer warp only stages rows, running ahead of the consumers.
-template <int MODE, int ST, bool T1>
+//    columns at x0 = bx*(kW-2). Thread t pulls column x0 - 1 + t into ring
+//    column t, so the halo columns come from threads 0 and nint + 1 like
+//    every other column and all consumer warps do the same work; threads
+//    1 .. nint collide. Neighbouring strips overlap by two pulled columns.
+// Warp stores cover whole 128-byte lines in the 32-bit layouts. In all three
+// the producer warp only stages rows, running ahead of the consumers. The
+// two 32-bit layouts store the same bits.
+template <int MODE, int ST, bool T1, bool PAIR>
 __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* __restrict__ fout, const Geom& g,
                                          const Phys& p, double* __restrict__ partials,
                                          double* __restrict__ fields, int* __restrict__ err, int bx, int by,
                                          int slot, unsigned char* smem_raw)
 {
     using T = typename StoreT<ST>::T;
-    constexpr int kStages = stages_of(ST);
+    constexpr int kStages = stages_of(ST, PAIR);
     constexpr int A = StoreT<ST>::align;
     constexpr int P = StoreT<ST>::overlap;
+    constexpr bool PR = P == 0 && PAIR;  // the pair layout
     constexpr int R = kRowLen;
     constexpr size_t SB = stage_bytes<ST>();
     // ring stage s: plane 0 (FP32, R) then the deviations in the layout of
@@ -1098,7 +1102,7 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 32);               // 32 producer-lane arrivals + tx bytes
-            mbar_init(&empty[s], consumers(ST) / 32);  // one arrival per consumer warp
+            mbar_init(&empty[s], consumers(ST, PAIR) / 32);  // one arrival per consumer warp
         }
         fence_mbar_init();
     }
@@ -1116,10 +1120,10 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
     };
 
     using PT = std::conditional_t<ST == kF32, Pulled, PulledDev>;
-    constexpr int NC = consumers(ST);
+    constexpr int NC = consumers(ST, PAIR);
     constexpr int NCW = NC / 32;
-    // the state of what a consumer thread pulls per row: a pair of nodes (P = 0) or one
-    using PT2 = std::conditional_t<P == 0, std::conditional_t<ST == kF32, Pulled2, PulledDev2>, PT>;
+    // the state of what a consumer thread pulls per row: a pair of nodes or one
+    using PT2 = std::conditional_t<PR, std::conditional_t<ST == kF32, Pulled2, PulledDev2>, PT>;
     // pull the node in staged column col of the row held by stage bc, whose
     // neighbour rows are in stages bm (row - 1) and bp (row + 1)
     auto pull = [&](const unsigned char* bm, const unsigned char* bc, const unsigned char* bp, int col, PT& n) {
@@ -1249,22 +1253,24 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
     // ---------------- consumer warps
     // P = 1: thread t pulls node column x0 - 1 + t (staged column t + 1 + o,
     // psi ring column t) and collides it if it lies inside the strip.
-    // P = 0: thread t owns the pair of columns x0 + 2t (lane A) and
+    // P = 0, one node: thread t pulls column x0 + t (staged column t + 1 + o,
+    // ring column t + 1) and collides it if it lies inside the strip.
+    // P = 0, pairs: thread t owns the pair of columns x0 + 2t (lane A) and
     // x0 + 2t + 1 (lane B): staged columns c, c + 1 with c = 2t + 1 + o
     // (even, as o = 3), psi ring columns 2t + 2 and 2t + 3. The pulled
     // columns are x0 .. x0 + nint, the last one being the right halo; the left
     // halo x0 - 1 (ring column 1) is one extra pull by thread 0, and a full
     // strip's right halo x0 + kW (ring column kW + 2) one by the last thread.
     const int t = tid;
-    const int np = nint + 1;                                       // P = 0: pulled columns
-    const bool active = P == 0 ? 2 * t < np : t < nint + 2;         // pulls something
-    const bool b_ok = 2 * t + 1 < np;                               // P = 0: lane B pulled
-    const bool col_a = P == 0 ? 2 * t < nint : (t >= 1 && t <= nint);
-    const bool col_b = 2 * t + 1 < nint;                            // P = 0: lane B collided
-    const bool halo_r = P == 0 && t == NC - 1 && np > 2 * NC;
-    const int c = P == 0 ? 2 * t + 1 + o : t + 1 + o;              // staged column (of lane A)
-    const int x = P == 0 ? x0 + 2 * t : x0 - 1 + t;
-    const int tr = P == 0 ? 2 * t + 2 : t;                         // psi ring column (of lane A)
+    const int np = nint + 1;                                       // pairs: pulled columns
+    const bool active = PR ? 2 * t < np : P == 0 ? t < nint : t < nint + 2;  // pulls something
+    const bool b_ok = 2 * t + 1 < np;                               // pairs: lane B pulled
+    const bool col_a = PR ? 2 * t < nint : P == 0 ? t < nint : (t >= 1 && t <= nint);
+    const bool col_b = 2 * t + 1 < nint;                            // pairs: lane B collided
+    const bool halo_r = PR && t == NC - 1 && np > 2 * NC;
+    const int c = PR ? 2 * t + 1 + o : t + 1 + o;                  // staged column (of lane A)
+    const int x = PR ? x0 + 2 * t : x0 - P + t;
+    const int tr = PR ? 2 * t + 2 : t + 1 - P;                     // psi ring column (of lane A)
     ObsAcc acc;
     bool ok = true;
     // prologue: the two oldest staged rows (y0-2, y0-1) must be present
@@ -1304,7 +1310,7 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
         ok = mbar_wait(&full[s_p], ph_p, err) && ok;
         float* prow = psi_w + ((r + 4) & 3) * kPsiStride;
         if (active) {
-            if constexpr (P == 0) {
+            if constexpr (PR) {
                 const float* s0m = reinterpret_cast<const float*>(b_m);
                 const float* s0c = reinterpret_cast<const float*>(b_c);
                 const float* s0p = reinterpret_cast<const float*>(b_p);
@@ -1327,6 +1333,18 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
             } else {
                 pull(b_m, b_c, b_p, c, into);
                 prow[tr] = pseudopotential(p, into);
+                if constexpr (P == 0) {
+                    if (t == 0) {  // left halo column x0 - 1
+                        PT h;
+                        pull(b_m, b_c, b_p, c - 1, h);
+                        prow[tr - 1] = pseudopotential(p, h);
+                    }
+                    if (t == nint - 1) {  // right halo column x0 + nint
+                        PT h;
+                        pull(b_m, b_c, b_p, c + 1, h);
+                        prow[tr + 1] = pseudopotential(p, h);
+                    }
+                }
             }
         }
         consumer_sync<NC>();
@@ -1339,7 +1357,7 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
             const float* pm = psi_w + ((rc + 3) & 3) * kPsiStride;
             const float* pc = psi_w + ((rc + 4) & 3) * kPsiStride;
             const float* pp = psi_w + ((rc + 5) & 3) * kPsiStride;
-            if constexpr (P == 0) {
+            if constexpr (PR) {
                 const bool col[2] = {col_a && !prev.solid[0], col_b && !prev.solid[1]};
                 if (col[0] || col[1]) {
                     if constexpr (ST == kF32)
@@ -1353,10 +1371,13 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
                     if (col_b && prev.solid[1]) zero_fields(x + 1, rc);
                 }
             } else {
-                if (col_a && !prev.solid)
-                    collide_dev<MODE, T, T1>(prev, pm, pc, pp, tr, p, g, fout, reinterpret_cast<T*>(fout + g.plane),
-                                         fields, x, rc, acc);
-                else if constexpr (MODE == kFields) {
+                if (col_a && !prev.solid) {
+                    if constexpr (ST == kF32)
+                        collide_node<MODE, T1>(prev, pm, pc, pp, tr, p, g, fout, fields, x, rc, acc);
+                    else
+                        collide_dev<MODE, T, T1>(prev, pm, pc, pp, tr, p, g, fout,
+                                                 reinterpret_cast<T*>(fout + g.plane), fields, x, rc, acc);
+                } else if constexpr (MODE == kFields) {
                     if (col_a) zero_fields(x, rc);
                 }
             }
@@ -1366,7 +1387,7 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
 
     // two pulled-state register sets used in turn, so that no copy is made
     PT2 n0, n1;
-    if constexpr (P == 0) {
+    if constexpr (PR) {
         n0.solid[0] = n0.solid[1] = n1.solid[0] = n1.solid[1] = true;
     } else {
         n0.solid = n1.solid = true;
@@ -1427,14 +1448,14 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
 
 // T1: tau = 1 (the relaxation sets f* = f_eq, so no pulled population is
 // kept for it); the modes that only observe use T1 = true.
-template <int MODE, int ST = kF32, bool T1 = true>
-__global__ void __launch_bounds__(threads_of(ST), step_ctas_of(MODE, ST, T1))
+template <int MODE, int ST = kF32, bool T1 = true, bool PAIR = true>
+__global__ void __launch_bounds__(threads_of(ST, PAIR), step_ctas_of(MODE, ST, T1, PAIR))
     step_kernel(const float* __restrict__ fin, float* __restrict__ fout, Geom g, Phys p,
                 double* __restrict__ partials, double* __restrict__ fields, int* __restrict__ err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    run_tile<MODE, ST, T1>(fin, fout, g, p, partials, fields, err, blockIdx.x, blockIdx.y,
-                       blockIdx.y * gridDim.x + blockIdx.x, smem_raw);
+    run_tile<MODE, ST, T1, PAIR>(fin, fout, g, p, partials, fields, err, blockIdx.x, blockIdx.y,
+                                 blockIdx.y * gridDim.x + blockIdx.x, smem_raw);
 }
 
 // One domain of a batch: geometry, model parameters, its two population
@@ -1450,8 +1471,8 @@ struct DomainDev {
 // segment, partial slot) with stride gridDim.x, so domains of any size share
 // one launch; buffers alternate with `parity`. Between tiles the CTA
 // invalidates and re-arms its mbarriers.
-template <int MODE, int ST = kF32, bool T1 = true>
-__global__ void __launch_bounds__(threads_of(ST), batch_ctas_of(MODE, ST, T1))
+template <int MODE, int ST = kF32, bool T1 = true, bool PAIR = true>
+__global__ void __launch_bounds__(threads_of(ST, PAIR), batch_ctas_of(MODE, ST, T1, PAIR))
     batch_step_kernel(const DomainDev* __restrict__ doms, const int4* __restrict__ tiles, int ntiles,
                       int parity, int* __restrict__ err)
 {
@@ -1469,13 +1490,13 @@ __global__ void __launch_bounds__(threads_of(ST), batch_ctas_of(MODE, ST, T1))
             p = d.p;
         }
         __syncthreads();
-        run_tile<MODE, ST, T1>(d.buf[parity], d.buf[parity ^ 1], g, p, d.partials, nullptr, err, tl.y, tl.z, tl.w,
-                               smem_raw);
+        run_tile<MODE, ST, T1, PAIR>(d.buf[parity], d.buf[parity ^ 1], g, p, d.partials, nullptr, err, tl.y, tl.z,
+                                     tl.w, smem_raw);
         __syncthreads();
         if (threadIdx.x == 0) {
-            uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + stages_of(ST) * stage_bytes<ST>() +
+            uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + stages_of(ST, PAIR) * stage_bytes<ST>() +
                                                          4 * kPsiStride * sizeof(float));
-            for (int s = 0; s < 2 * stages_of(ST); ++s) mbar_inval(&bars[s]);
+            for (int s = 0; s < 2 * stages_of(ST, PAIR); ++s) mbar_inval(&bars[s]);
         }
         __syncthreads();
     }

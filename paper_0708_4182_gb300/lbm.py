@@ -25,6 +25,8 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENAN, LBM_ETIMEOUT, LBM_ESTATE, L
 LBM_GREEN_MC, LBM_GREEN_PRINTED = 0, 1
 LBM_FP32, LBM_FP32_DEV, LBM_FP16_DEV, LBM_BF16_DEV = 0, 1, 2, 3
 LBM_RHO_U, LBM_POPS, LBM_RHO_U_PHYS, LBM_UX_PROFILE, LBM_RHO = 0, 1, 2, 3, 4
+LBM_NORMAL_FACES, LBM_NORMAL_UNIT = 0, 1
+LBM_LAYOUT_AUTO, LBM_LAYOUT_PAIRS, LBM_LAYOUT_SINGLE = 0, 1, 2
 
 
 class LbmUnavailable(RuntimeError):
@@ -45,7 +47,7 @@ class lbm_params(ctypes.Structure):
         ("body_fx", ctypes.c_double), ("body_fy", ctypes.c_double),
         ("green", ctypes.c_int32), ("storage", ctypes.c_int32),
         ("obs_every", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
-        ("normal", ctypes.c_int32),
+        ("normal", ctypes.c_int32), ("layout", ctypes.c_int32),
     ]
 
 
@@ -116,10 +118,10 @@ def _check(ctx, status: int):
 
 def make_params(nx, ny, tau=1.0, G=-0.52, G_wall=-0.14, rho0=1.0, rho_c=1.0, f_elec=0.0,
                 body_fx=0.0, body_fy=0.0, green=LBM_GREEN_MC, storage=LBM_FP32, obs_every=0,
-                tile_rows=0, normal=0) -> lbm_params:
+                tile_rows=0, normal=0, layout=0) -> lbm_params:
     return lbm_params(int(nx), int(ny), float(tau), float(G), float(G_wall), float(rho0),
                       float(rho_c), float(f_elec), float(body_fx), float(body_fy), int(green),
-                      int(storage), int(obs_every), int(tile_rows), int(normal))
+                      int(storage), int(obs_every), int(tile_rows), int(normal), int(layout))
 
 
 # ---------------------------------------------------------------- low level

@@ -42,10 +42,13 @@ def specs_of(ws, storage=0):
     return [dict(nx=w.nx, ny=w.ny, storage=storage, **w.params) for w in ws]
 
 
-@pytest.mark.parametrize("storage", [0, 1, 2, 3])
-def test_batch_equals_single_domain_runs(lbm, storage):
+@pytest.mark.parametrize("storage,layout", [(0, 0), (0, 1), (0, 2), (1, 0), (1, 1), (1, 2), (2, 0), (3, 0)])
+def test_batch_equals_single_domain_runs(lbm, storage, layout):
+    """Each domain of a batch equals the same domain stepped alone, bitwise;
+    the batch's thread layout (automatic or forced) need not be the single
+    domain's (automatic) one."""
     ws = sweep_workloads(storage=storage)
-    b = lbm.Batch(specs_of(ws, storage))
+    b = lbm.Batch([dict(s, layout=layout) for s in specs_of(ws, storage)])
     b.set_tile_rows(16)
     for w, d in zip(ws, b.domains):
         d.set_geometry(w.mask)
@@ -66,8 +69,8 @@ def test_batch_equals_single_domain_runs(lbm, storage):
     b.close()
 
 
-@pytest.mark.parametrize("storage", [0, 2])
-def test_batch_tiny_and_ragged_domains_equal_single_runs(lbm, storage):
+@pytest.mark.parametrize("storage,layout", [(0, 1), (0, 2), (2, 0)])
+def test_batch_tiny_and_ragged_domains_equal_single_runs(lbm, storage, layout):
     """Tiny and ragged domains in one batch (an 8-column domain whose staged
     window wraps many times, a single row, strips with ragged ends): each
     equals the same domain stepped alone, bitwise."""
@@ -80,7 +83,8 @@ def test_batch_tiny_and_ragged_domains_equal_single_runs(lbm, storage):
         if ny >= 3:
             mask[0] = mask[-1] = 1
         cases.append((mask, _blob_field(nx, ny, mask, nx * 1000 + ny)))
-    b = lbm.Batch([dict(nx=m.shape[1], ny=m.shape[0], storage=storage, **params) for m, _ in cases])
+    b = lbm.Batch([dict(nx=m.shape[1], ny=m.shape[0], storage=storage, layout=layout, **params)
+                   for m, _ in cases])
     b.set_tile_rows(8)
     for (m, rho), d in zip(cases, b.domains):
         d.set_geometry(m)

@@ -142,8 +142,11 @@ RAGGED = [
 ]
 
 
+@pytest.mark.parametrize("layout", [1, 2])
 @pytest.mark.parametrize("nx,ny,walls,tile_rows", RAGGED)
-def test_ragged_and_tiny_domains(lbm, nx, ny, walls, tile_rows):
+def test_ragged_and_tiny_domains(lbm, nx, ny, walls, tile_rows, layout):
+    """Both thread layouts of the step kernel (pairs, one node per thread)
+    against the oracle."""
     mask = np.zeros((ny, nx), np.uint8)
     if walls and ny >= 3:
         mask[0] = mask[-1] = 1
@@ -151,9 +154,38 @@ def test_ragged_and_tiny_domains(lbm, nx, ny, walls, tile_rows):
             mask[ny // 2:ny // 2 + 2, nx // 3:nx // 3 + 3] = 1  # an interior block
     rho = _blob_field(nx, ny, mask, nx * 1000 + ny)
     params = dict(wl.PAPER, tau=1.0, f_elec=0.2, body_fx=1e-5, body_fy=-2e-6)
-    p, f_ref, lat = run_both(lbm, mask, rho, params, 40, tile_rows=tile_rows)
+    p, f_ref, lat = run_both(lbm, mask, rho, params, 40, tile_rows=tile_rows, layout=layout)
     assert_pops(lat.populations(), f_ref, mask)
     check_obs(lat, p, mask, f_ref)
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+@pytest.mark.parametrize("tau", [1.0, 0.9])
+def test_layouts_give_identical_populations(lbm, storage, tau):
+    """The pair layout and the one-node layout of the 32-bit forms store the
+    same bits (both are written with explicit roundings, operation for
+    operation), on a rough channel with the electric force and ragged strips
+    (520 columns), with tau = 1 and tau != 1; the fused observables agree and
+    the per-node fields are identical."""
+    w = wl.rough_channel(nx=520, ny=90, amp=6, level=9, seed=5, body_fx=1e-5)
+    params = dict(w.params, tau=tau, storage=storage)
+    pops, fields, obs = [], [], []
+    for layout in (1, 2):
+        lat = lbm.Lattice(w.nx, w.ny, **params, layout=layout, obs_every=7, tile_rows=8)
+        lat.set_geometry(w.mask)
+        lat.set_rho_u(w.rho)
+        lat.step(42)
+        pops.append(lat.populations())
+        fields.append(lat.fields())
+        obs.append(lat.obs_latest())
+    assert np.array_equal(pops[0], pops[1])
+    for a, b in zip(fields[0], fields[1]):
+        assert np.array_equal(a, b)
+    assert obs[0]["step"] == obs[1]["step"] == 35  # state 35, reduced by the step from it
+    for k in ("max_u", "min_rho", "nonfinite"):
+        assert obs[0][k] == obs[1][k], k
+    for k in ("mass", "flux_Q", "mom_x", "mom_y"):
+        assert obs[0][k] == pytest.approx(obs[1][k], rel=1e-12, abs=1e-15), k
 
 
 def test_printed_green_convention_and_tau(lbm):
