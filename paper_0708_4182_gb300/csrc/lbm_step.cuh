@@ -54,6 +54,7 @@
 
 #include <cstdint>
 #include <type_traits>
+#include <utility>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -92,14 +93,21 @@ __host__ __device__ constexpr bool is16(int st) { return st == kF16Dev || st == 
 #ifndef LBM_CTAS_F32DEV
 #define LBM_CTAS_F32DEV 4
 #endif
+#ifndef LBM_STAGES_16
+#define LBM_STAGES_16 6
+#endif
+#ifndef LBM_CTAS_16
+#define LBM_CTAS_16 3
+#endif
 // pair: the 32-bit forms' pair layout (ignored by the 16-bit forms)
 __host__ __device__ constexpr int stages_of(int st, bool pair = true)
 {
-    return !pair ? 6 : st == kF32 ? LBM_STAGES_F32 : st == kF32Dev ? LBM_STAGES_F32DEV : 6;
+    return is16(st) ? LBM_STAGES_16 : !pair ? 6 : st == kF32 ? LBM_STAGES_F32 : LBM_STAGES_F32DEV;
 }
 __host__ __device__ constexpr int ctas_of(int st, bool t1 = true, bool pair = true)
 {
-    return !pair ? 3 : st == kF32 ? (t1 ? LBM_CTAS_F32 : 3) : st == kF32Dev ? (t1 ? LBM_CTAS_F32DEV : 3) : 3;
+    return is16(st) ? (t1 ? LBM_CTAS_16 : 3)
+                    : !pair ? 3 : st == kF32 ? (t1 ? LBM_CTAS_F32 : 3) : (t1 ? LBM_CTAS_F32DEV : 3);
 }
 // the persistent batch kernel: as the single-domain step; its observing mode
 // aims at 3 (it spills at 4)
@@ -108,10 +116,12 @@ __host__ __device__ constexpr int batch_ctas_of(int mode, int st, bool t1, bool 
     return mode == 0 ? ctas_of(st, t1, pair) : (ctas_of(st, t1, pair) > 3 ? 3 : ctas_of(st, t1, pair));
 }
 // the single-domain kernel of a mode: the observing modes keep their
-// reduction state too and aim at one CTA less (no spills)
+// reduction state too and aim at one CTA less (no spills); the step with
+// fused observables and tau != 1 (once per observation interval) at 2
 __host__ __device__ constexpr int step_ctas_of(int mode, int st, bool t1, bool pair = true)
 {
     return mode == 0 ? ctas_of(st, t1, pair)
+           : !t1     ? 2
                      : (ctas_of(st, t1, pair) > 3 ? ctas_of(st, t1, pair) - 1 : ctas_of(st, t1, pair));
 }
 
@@ -152,7 +162,8 @@ template <int ST> __host__ __device__ constexpr size_t stage_bytes()
 }
 template <int ST, bool PAIR = true> __host__ __device__ constexpr size_t smem_bytes()
 {
-    return stages_of(ST, PAIR) * (stage_bytes<ST>() + 2 * sizeof(uint64_t)) + 4 * kPsiStride * sizeof(float) + 128;
+    // ring stages, their two mbarriers each, the psi ring (one row per stage) and alignment slack
+    return stages_of(ST, PAIR) * (stage_bytes<ST>() + 2 * sizeof(uint64_t) + kPsiStride * sizeof(float)) + 128;
 }
 // bytes of one node's state in global memory (plane 0 + the other 8 values)
 template <int ST> __host__ __device__ constexpr int node_bytes() { return 4 + 8 * int(sizeof(typename StoreT<ST>::T)); }
@@ -300,10 +311,13 @@ template <int NC> __device__ __forceinline__ void consumer_sync()
 }
 
 // ------------------------------------------------------------------ two-lane FP32
-// A float2 holds one value of each of two neighbouring nodes (lane x: the
-// left node A, lane y: the right node B). These map to Blackwell's paired
-// FP32 instructions (add/mul/fma .rn on f32x2): each lane is rounded exactly
-// as the scalar operation would be, and one instruction serves both nodes.
+// In the pair layout a float2 holds one value of each of two neighbouring
+// nodes (lane x: the left node A, lane y: the right node B); in the one-node
+// functions it holds two values of the same node that go through the same
+// operation (the x and y components of a vector, or the two halves of a sum).
+// These map to Blackwell's paired FP32 instructions (add/mul/fma .rn on
+// f32x2): each lane is rounded exactly as the scalar operation would be, and
+// one instruction does both lanes' operation.
 __device__ __forceinline__ float2 splat(float v) { return make_float2(v, v); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
@@ -430,23 +444,25 @@ __device__ __forceinline__ void wall_electric(uint32_t sb, float psi, float nsgx
 // the pull sources (n.sb), and the body force. N has fields rho and sb. The
 // sign of Eq. 5 is carried by the constants (-G: round to nearest is
 // symmetric, so this is exactly the negated sum); every operation is the
-// two-node kernel's (node_force2) lane for lane.
+// two-node kernel's (node_force2) lane for lane. The x and y components go
+// through the paired instructions together (lane x: the x component).
 template <typename N>
-__device__ __forceinline__ void node_force(const N& n, const float* pm, const float* pc, const float* pp,
-                                           int t, const Phys& p, float& Fx_out, float& Fy_out)
+__device__ __forceinline__ float2 node_force(const N& n, const float* pm, const float* pc, const float* pp,
+                                             int t, const Phys& p)
 {
     const float psi = pc[t];
-    const float dxc = pc[t + 1] - pc[t - 1];
-    const float dxp = pp[t + 1] - pp[t - 1], dxm = pm[t + 1] - pm[t - 1];
-    const float sxp = pp[t + 1] + pp[t - 1], sxm = pm[t + 1] + pm[t - 1];
+    // (psi(x+1) - psi(x-1), psi(y+1) - psi(y-1)) on the node's row and column
+    const float2 dc = sub2(make_float2(pc[t + 1], pp[t]), make_float2(pc[t - 1], pm[t]));
+    // rows y+1 and y-1: right minus left, right plus left
+    const float2 pr = make_float2(pp[t + 1], pm[t + 1]), pl = make_float2(pp[t - 1], pm[t - 1]);
+    const float2 dd = sub2(pr, pl), ss = add2(pr, pl);
     // Eq. 5: -sum_a G_a psi(x+e_a) e_a, axis and diagonal links
-    const float nsgx = fmaf(-p.g_axis, dxc, __fmul_rn(-p.g_diag, __fadd_rn(dxp, dxm)));
-    const float nsgy = fmaf(-p.g_axis, __fsub_rn(pp[t], pm[t]), __fmul_rn(-p.g_diag, __fsub_rn(sxp, sxm)));
-    float Fx = __fmul_rn(psi, nsgx), Fy = __fmul_rn(psi, nsgy);
-    if (n.sb != 0) wall_electric(n.sb, psi, nsgx, nsgy, n.rho, p, Fx, Fy);
+    const float2 nsg = fma2(splat(-p.g_axis), dc,
+                            mul2(splat(-p.g_diag), make_float2(__fadd_rn(dd.x, dd.y), __fsub_rn(ss.x, ss.y))));
+    float2 F = mul2(splat(psi), nsg);
+    if (n.sb != 0) wall_electric(n.sb, psi, nsg.x, nsg.y, n.rho, p, F.x, F.y);
     // body force on every fluid node
-    Fx_out = fmaf(n.rho, p.bfx, Fx);
-    Fy_out = fmaf(n.rho, p.bfy, Fy);
+    return fma2(splat(n.rho), make_float2(p.bfx, p.bfy), F);
 }
 
 // Observables or fields epilogue of one fluid node (modes other than kStep).
@@ -489,6 +505,14 @@ __device__ __forceinline__ float div1(float n, float nd, float r)
     return fmaf(e, r, q0);
 }
 
+// The same in both lanes.
+__device__ __forceinline__ float2 div2(float2 n, float2 nd, float2 r)
+{
+    const float2 q0 = mul2(n, r);
+    const float2 e = fma2(q0, nd, n);
+    return fma2(e, r, q0);
+}
+
 // Forces, velocity shift, collision and the mode's epilogue for one fluid node
 // (x, r) in plain storage, whose pulled populations are `n`; psi rows r-1, r,
 // r+1 are pm, pc, pp (indexed by the node's ring column t). Every operation is
@@ -500,8 +524,7 @@ __device__ __forceinline__ void collide_node(const Pulled& n, const float* pm, c
                                              float* __restrict__ fout, double* __restrict__ fields,
                                              int x, int r, ObsAcc& acc)
 {
-    float Fx, Fy;
-    node_force(n, pm, pc, pp, t, p, Fx, Fy);
+    const float2 F = node_force(n, pm, pc, pp, t, p);
     const float rinv = rcp_approx(n.rho);
     if constexpr (MODE == kStep || MODE == kStepObs) {
         // Eq. 10 velocity shift, Eq. 3 equilibrium, Eq. 1 relaxation.
@@ -509,26 +532,24 @@ __device__ __forceinline__ void collide_node(const Pulled& n, const float* pm, c
         // from one corrected rho/9 by exact power-of-two scalings, so
         // sum_a f_eq = rho has no systematic bias (1/9 in FP32 is 7.5e-9 too
         // large, which would add mass every step); at tau = 1 f* = f_eq.
-        const float ux = div1(fmaf(p.tau, Fx, n.jx), -n.rho, rinv);
-        const float uy = div1(fmaf(p.tau, Fy, n.jy), -n.rho, rinv);
-        const float om = fmaf(-1.5f, fmaf(ux, ux, __fmul_rn(uy, uy)), 1.f);
+        // Lane pairs: (x, y) components, then the directions (1, 2), (3, 4),
+        // (5, 6), (7, 8).
+        const float2 u = div2(fma2(splat(p.tau), F, make_float2(n.jx, n.jy)), splat(-n.rho), splat(rinv));
+        const float om = fmaf(-1.5f, fmaf(u.x, u.x, __fmul_rn(u.y, u.y)), 1.f);
         const float r9 = div1(n.rho, -9.f, 1.f / 9.f);
         const float w0r = __fmul_rn(4.f, r9), w2r = __fmul_rn(0.25f, r9);
-        const float d5 = __fadd_rn(ux, uy), d6 = __fsub_rn(uy, ux);
+        const float2 dg = make_float2(__fadd_rn(u.x, u.y), __fsub_rn(u.y, u.x));  // e5.u, e6.u
         // f_eq_a = w_a rho (1 + 3 c + 4.5 c^2 - 1.5 u^2) with c = +-(e_a . u):
         // (-c)(4.5(-c) + 3) = c (4.5 c - 3) exactly
-        auto polyp = [om](float c) { return fmaf(c, fmaf(4.5f, c, 3.f), om); };
-        auto polym = [om](float c) { return fmaf(c, fmaf(4.5f, c, -3.f), om); };
+        const float2 oms = splat(om);
+        auto polyp = [oms](float2 c) { return fma2(c, fma2(splat(4.5f), c, splat(3.f)), oms); };
+        auto polym = [oms](float2 c) { return fma2(c, fma2(splat(4.5f), c, splat(-3.f)), oms); };
         float fs[9];
         fs[0] = __fmul_rn(w0r, om);
-        fs[1] = __fmul_rn(r9, polyp(ux));
-        fs[2] = __fmul_rn(r9, polyp(uy));
-        fs[3] = __fmul_rn(r9, polym(ux));
-        fs[4] = __fmul_rn(r9, polym(uy));
-        fs[5] = __fmul_rn(w2r, polyp(d5));
-        fs[6] = __fmul_rn(w2r, polyp(d6));
-        fs[7] = __fmul_rn(w2r, polym(d5));
-        fs[8] = __fmul_rn(w2r, polym(d6));
+        const float2 f12 = mul2(splat(r9), polyp(u)), f34 = mul2(splat(r9), polym(u));
+        const float2 f56 = mul2(splat(w2r), polyp(dg)), f78 = mul2(splat(w2r), polym(dg));
+        fs[1] = f12.x; fs[2] = f12.y; fs[3] = f34.x; fs[4] = f34.y;
+        fs[5] = f56.x; fs[6] = f56.y; fs[7] = f78.x; fs[8] = f78.y;
         if (!T1 && p.tau != 1.f) {
 #pragma unroll
             for (int a = 0; a < 9; ++a) fs[a] = fmaf(__fsub_rn(fs[a], n.f[a]), p.inv_tau, n.f[a]);
@@ -537,7 +558,7 @@ __device__ __forceinline__ void collide_node(const Pulled& n, const float* pm, c
 #pragma unroll
         for (int a = 0; a < 9; ++a) o[a * g.plane] = fs[a];
     }
-    if constexpr (MODE != kStep) node_observe<MODE>(n.rho, rinv, n.jx, n.jy, Fx, Fy, g, fields, x, r, acc);
+    if constexpr (MODE != kStep) node_observe<MODE>(n.rho, rinv, n.jx, n.jy, F.x, F.y, g, fields, x, r, acc);
 }
 
 // ------------------------------------------------------------------ deviation storage
@@ -564,6 +585,28 @@ template <> __device__ __forceinline__ __half from_raw<__half>(float v) { return
 template <> __device__ __forceinline__ __nv_bfloat16 from_raw<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 template <typename T> struct RawScale { static constexpr float scale = 1.f, unscale = 1.f; };
 template <> struct RawScale<__half> { static constexpr float scale = kF16Scale, unscale = kF16Unscale; };
+// Two raw 16-bit values in one 32-bit word (lane x in the low half), to and
+// from FP32 with one paired conversion each way.
+template <typename T> __device__ __forceinline__ uint32_t pack_raw2(float2 v);
+template <> __device__ __forceinline__ uint32_t pack_raw2<__half>(float2 v)
+{
+    const __half2 h = __floats2half2_rn(v.x, v.y);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+template <> __device__ __forceinline__ uint32_t pack_raw2<__nv_bfloat16>(float2 v)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+template <typename T> __device__ __forceinline__ float2 unpack_raw2(uint32_t w);
+template <> __device__ __forceinline__ float2 unpack_raw2<__half>(uint32_t w)
+{
+    return __half22float2(*reinterpret_cast<const __half2*>(&w));
+}
+template <> __device__ __forceinline__ float2 unpack_raw2<__nv_bfloat16>(uint32_t w)
+{
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
 
 // Pull in deviation form: s0* are plane-0 rows (rho*) r-1, r, r+1; sd* the
 // same rows' deviations (laid out by dev_index with plane R); c the node column.
@@ -584,42 +627,44 @@ __device__ __forceinline__ void pull_dev(const float* __restrict__ s0m, const fl
         n.sb = 0;
         return;
     }
-    float rs[9], d[9], own[9];
     auto dv = [](const T* sd, int col, int a) { return to_raw(sd[dev_index<T>(size_t(col), a, size_t(R))]); };
-    rs[1] = s0c[c - 1];  d[1] = dv(sdc, c - 1, 1);  // e1: source (x-1, y)
-    rs[2] = s0m[c];      d[2] = dv(sdm, c, 2);      // e2: source (x, y-1)
-    rs[3] = s0c[c + 1];  d[3] = dv(sdc, c + 1, 3);  // e3: source (x+1, y)
-    rs[4] = s0p[c];      d[4] = dv(sdp, c, 4);      // e4: source (x, y+1)
-    rs[5] = s0m[c - 1];  d[5] = dv(sdm, c - 1, 5);  // e5: source (x-1, y-1)
-    rs[6] = s0m[c + 1];  d[6] = dv(sdm, c + 1, 6);  // e6: source (x+1, y-1)
-    rs[7] = s0p[c + 1];  d[7] = dv(sdp, c + 1, 7);  // e7: source (x+1, y+1)
-    rs[8] = s0p[c - 1];  d[8] = dv(sdp, c - 1, 8);  // e8: source (x-1, y+1)
+    // The 8 sources in four lane pairs (lane x an axis direction, lane y a
+    // diagonal one): (1, 5), (3, 7), (2, 6), (4, 8), so that each sum below
+    // runs its two halves in the two lanes.
+    float2 rA = make_float2(s0c[c - 1], s0m[c - 1]);  // rho* at the sources of e1: (x-1, y), e5: (x-1, y-1)
+    float2 rB = make_float2(s0c[c + 1], s0p[c + 1]);  // e3: (x+1, y), e7: (x+1, y+1)
+    float2 rC = make_float2(s0m[c], s0m[c + 1]);      // e2: (x, y-1), e6: (x+1, y-1)
+    float2 rD = make_float2(s0p[c], s0p[c - 1]);      // e4: (x, y+1), e8: (x-1, y+1)
+    float2 dA = make_float2(dv(sdc, c - 1, 1), dv(sdm, c - 1, 5));
+    float2 dB = make_float2(dv(sdc, c + 1, 3), dv(sdp, c + 1, 7));
+    float2 dC = make_float2(dv(sdm, c, 2), dv(sdm, c + 1, 6));
+    float2 dD = make_float2(dv(sdp, c, 4), dv(sdp, c - 1, 8));
+    float own[9];
     if constexpr (sizeof(T) == 2) {
-        // the node's own 8 deviations: one 16-byte load
-        const uint4 q = *reinterpret_cast<const uint4*>(sdc + size_t(c) * 8);
-        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+        // the node's own 8 deviations: one 16-byte load, paired conversions
+        const uint4 qv = *reinterpret_cast<const uint4*>(sdc + size_t(c) * 8);
+        const uint32_t w[4] = {qv.x, qv.y, qv.z, qv.w};
 #pragma unroll
-        for (int b = 1; b < 9; ++b) {
-            const unsigned short bits = (unsigned short)(w[(b - 1) >> 1] >> (16 * ((b - 1) & 1)));
-            T v;
-            memcpy(&v, &bits, sizeof(T));
-            own[b] = to_raw(v);
+        for (int k = 0; k < 4; ++k) {
+            const float2 v = unpack_raw2<T>(w[k]);
+            own[2 * k + 1] = v.x;
+            own[2 * k + 2] = v.y;
         }
     } else {
 #pragma unroll
         for (int b = 1; b < 9; ++b) own[b] = dv(sdc, c, b);
     }
-    constexpr int opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
-    auto qsum = [&rs, r0](float& q1, float& q2) {
-        q1 = ((rs[1] - r0) + (rs[3] - r0)) + ((rs[2] - r0) + (rs[4] - r0));
-        q2 = ((rs[5] - r0) + (rs[7] - r0)) + ((rs[6] - r0) + (rs[8] - r0));
-    };
+    const float2 r0s = splat(r0);
+    float2 qa = sub2(rA, r0s), qb = sub2(rB, r0s), qc = sub2(rC, r0s), qd = sub2(rD, r0s);
+    // (q1, q2) = sums of rho*_src - rho*(x) over the axis and the diagonal links
+    float2 q = add2(add2(qa, qb), add2(qc, qd));
     uint32_t sb = 0;
-    float q1, q2;
-    qsum(q1, q2);
     // a solid source holds a NaN sentinel in plane 0: only a NaN sum (a
     // wall nearby, or a state gone non-finite) takes the per-direction checks
-    if (isnan(q1 + q2)) {
+    if (isnan(q.x + q.y)) {
+        constexpr int opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+        float rs[9] = {0.f, rA.x, rC.x, rB.x, rD.x, rA.y, rC.y, rB.y, rD.y};
+        float d[9] = {0.f, dA.x, dC.x, dB.x, dD.x, dA.y, dC.y, dB.y, dD.y};
 #pragma unroll
         for (int a = 1; a < 9; ++a) {
             if (is_solid(rs[a])) {  // half-way bounce-back: the node's own f*_opp(a)
@@ -628,24 +673,38 @@ __device__ __forceinline__ void pull_dev(const float* __restrict__ s0m, const fl
                 d[a] = own[opp[a]];
             }
         }
-        qsum(q1, q2);
+        rA = make_float2(rs[1], rs[5]); rB = make_float2(rs[3], rs[7]);
+        rC = make_float2(rs[2], rs[6]); rD = make_float2(rs[4], rs[8]);
+        dA = make_float2(d[1], d[5]); dB = make_float2(d[3], d[7]);
+        dC = make_float2(d[2], d[6]); dD = make_float2(d[4], d[8]);
+        qa = sub2(rA, r0s); qb = sub2(rB, r0s); qc = sub2(rC, r0s); qd = sub2(rD, r0s);
+        q = add2(add2(qa, qb), add2(qc, qd));
     }
     constexpr float w1 = 1.f / 9.f, w2 = 1.f / 36.f;
     // rho - rho*(x) = sum_a w_a (rho*_src - rho*(x)) + sum_a d_a(src) - sum_b d_b(x)
-    const float dsrc = ((d[1] + d[3]) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8]));
-    const float down = ((own[1] + own[3]) + (own[2] + own[4])) + ((own[5] + own[7]) + (own[6] + own[8]));
-    const float drho = fmaf(w1, q1, fmaf(w2, q2, (dsrc - down) * U));
-    const float rho = r0 + drho;
-    n.rho = rho;
-    n.jx = fmaf(w1, rs[1] - rs[3], fmaf(w2, (rs[5] - rs[7]) + (rs[8] - rs[6]),
-                                        ((d[1] - d[3]) + (d[5] - d[7]) + (d[8] - d[6])) * U));
-    n.jy = fmaf(w1, rs[2] - rs[4], fmaf(w2, (rs[5] - rs[7]) + (rs[6] - rs[8]),
-                                        ((d[2] - d[4]) + (d[5] - d[7]) + (d[6] - d[8])) * U));
+    const float2 ds = add2(add2(dA, dB), add2(dC, dD));
+    const float2 dn = add2(add2(make_float2(own[1], own[5]), make_float2(own[3], own[7])),
+                           add2(make_float2(own[2], own[6]), make_float2(own[4], own[8])));
+    const float dsrc = ds.x + ds.y, down = dn.x + dn.y;
+    const float drho = fmaf(w1, q.x, fmaf(w2, q.y, (dsrc - down) * U));
+    n.rho = r0 + drho;
+    // rho u: (jx, jy) in the two lanes; e_r = (rho*_1 - rho*_3, rho*_5 - rho*_7),
+    // f_r = (rho*_2 - rho*_4, rho*_6 - rho*_8), the same for the deviations
+    const float2 er = sub2(rA, rB), fr = sub2(rC, rD), ed = sub2(dA, dB), fd = sub2(dC, dD);
+    float2 jd = make_float2((ed.x + ed.y) - fd.y, (fd.x + ed.y) + fd.y);
+    if constexpr (U != 1.f) jd = mul2(jd, splat(U));
+    const float2 j = fma2(splat(w1), make_float2(er.x, fr.x),
+                          fma2(splat(w2), make_float2(er.y - fr.y, er.y + fr.y), jd));
+    n.jx = j.x;
+    n.jy = j.y;
     // g_a = f_a - w_a rho = w_a ((rho*_src - rho*(x)) - drho) + d_a(src), in
     // raw units; only the relaxation with tau != 1 reads it
     if (need_g) {
-#pragma unroll
-        for (int a = 1; a < 9; ++a) n.g[a] = fmaf((a <= 4 ? w1 : w2) * S, (rs[a] - r0) - drho, d[a]);
+        const float2 wS = make_float2(w1 * S, w2 * S), dr = splat(drho);
+        const float2 gA = fma2(wS, sub2(qa, dr), dA), gB = fma2(wS, sub2(qb, dr), dB);
+        const float2 gC = fma2(wS, sub2(qc, dr), dC), gD = fma2(wS, sub2(qd, dr), dD);
+        n.g[1] = gA.x; n.g[5] = gA.y; n.g[3] = gB.x; n.g[7] = gB.y;
+        n.g[2] = gC.x; n.g[6] = gC.y; n.g[4] = gD.x; n.g[8] = gD.y;
     }
     n.g[0] = 0.f;
     n.sb = sb;
@@ -662,53 +721,49 @@ __device__ __forceinline__ void collide_dev(const PulledDev& n, const float* pm,
                                             float* __restrict__ fout0, T* __restrict__ foutd,
                                             double* __restrict__ fields, int x, int r, ObsAcc& acc)
 {
-    float Fx, Fy;
-    node_force(n, pm, pc, pp, t, p, Fx, Fy);
+    const float2 F = node_force(n, pm, pc, pp, t, p);
     const float rinv = rcp_approx(n.rho);
     if constexpr (MODE == kStep || MODE == kStepObs) {
-        const float ux = div1(fmaf(p.tau, Fx, n.jx), -n.rho, rinv);
-        const float uy = div1(fmaf(p.tau, Fy, n.jy), -n.rho, rinv);
-        const float nusq = __fmul_rn(-1.5f, fmaf(ux, ux, __fmul_rn(uy, uy)));
+        // lane pairs as in collide_node; q[k] holds d*_(2k+1) and d*_(2k+2)
+        const float2 u = div2(fma2(splat(p.tau), F, make_float2(n.jx, n.jy)), splat(-n.rho), splat(rinv));
+        const float nusq = __fmul_rn(-1.5f, fmaf(u.x, u.x, __fmul_rn(u.y, u.y)));
         // power-of-two scaling to raw units: exact
         const float w1r = __fmul_rn(div1(n.rho, -9.f, 1.f / 9.f), RawScale<T>::scale);
         const float w2r = __fmul_rn(0.25f, w1r);
-        const float d5 = __fadd_rn(ux, uy), d6 = __fsub_rn(uy, ux);
-        auto dpolyp = [nusq](float c) { return fmaf(c, fmaf(4.5f, c, 3.f), nusq); };
-        auto dpolym = [nusq](float c) { return fmaf(c, fmaf(4.5f, c, -3.f), nusq); };
-        float dq[9];
-        dq[1] = __fmul_rn(w1r, dpolyp(ux));
-        dq[2] = __fmul_rn(w1r, dpolyp(uy));
-        dq[3] = __fmul_rn(w1r, dpolym(ux));
-        dq[4] = __fmul_rn(w1r, dpolym(uy));
-        dq[5] = __fmul_rn(w2r, dpolyp(d5));
-        dq[6] = __fmul_rn(w2r, dpolyp(d6));
-        dq[7] = __fmul_rn(w2r, dpolym(d5));
-        dq[8] = __fmul_rn(w2r, dpolym(d6));
+        const float2 dg = make_float2(__fadd_rn(u.x, u.y), __fsub_rn(u.y, u.x));  // e5.u, e6.u
+        const float2 nus = splat(nusq);
+        auto dpolyp = [nus](float2 c) { return fma2(c, fma2(splat(4.5f), c, splat(3.f)), nus); };
+        auto dpolym = [nus](float2 c) { return fma2(c, fma2(splat(4.5f), c, splat(-3.f)), nus); };
+        float2 q[4];
+        q[0] = mul2(splat(w1r), dpolyp(u));
+        q[1] = mul2(splat(w1r), dpolym(u));
+        q[2] = mul2(splat(w2r), dpolyp(dg));
+        q[3] = mul2(splat(w2r), dpolym(dg));
         if (!T1 && p.tau != 1.f) {
 #pragma unroll
-            for (int a = 1; a < 9; ++a) dq[a] = fmaf(__fsub_rn(dq[a], n.g[a]), p.inv_tau, n.g[a]);
+            for (int k = 0; k < 4; ++k) {
+                const float ga = n.g[2 * k + 1], gb = n.g[2 * k + 2];
+                q[k] = make_float2(fmaf(__fsub_rn(q[k].x, ga), p.inv_tau, ga), fmaf(__fsub_rn(q[k].y, gb), p.inv_tau, gb));
+            }
         }
         const int o = r * g.pitch + x;
         fout0[o] = n.rho;
         if constexpr (sizeof(T) == 2) {
-            // the node's 8 deviations in one 16-byte store (paired conversions,
-            // each value rounded to nearest as alone)
+            // the node's 8 deviations in one 16-byte store; each paired
+            // conversion rounds both values to nearest, each as alone
             uint32_t w[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                T lo = from_raw<T>(dq[2 * k + 1]), hi = from_raw<T>(dq[2 * k + 2]);
-                unsigned short bl, bh;
-                memcpy(&bl, &lo, 2);
-                memcpy(&bh, &hi, 2);
-                w[k] = uint32_t(bl) | (uint32_t(bh) << 16);
-            }
+            for (int k = 0; k < 4; ++k) w[k] = pack_raw2<T>(q[k]);
             *reinterpret_cast<uint4*>(foutd + size_t(o) * 8) = make_uint4(w[0], w[1], w[2], w[3]);
         } else {
 #pragma unroll
-            for (int a = 1; a < 9; ++a) foutd[(a - 1) * g.plane + o] = from_raw<T>(dq[a]);
+            for (int k = 0; k < 4; ++k) {
+                foutd[(2 * k) * g.plane + o] = q[k].x;
+                foutd[(2 * k + 1) * g.plane + o] = q[k].y;
+            }
         }
     }
-    if constexpr (MODE != kStep) node_observe<MODE>(n.rho, rinv, n.jx, n.jy, Fx, Fy, g, fields, x, r, acc);
+    if constexpr (MODE != kStep) node_observe<MODE>(n.rho, rinv, n.jx, n.jy, F.x, F.y, g, fields, x, r, acc);
 }
 
 // ------------------------------------------------------------------ node pairs (32-bit forms)
@@ -898,14 +953,6 @@ __device__ __forceinline__ void node_force2(float2 rho, const uint32_t (&sb)[2],
     Fy_out = fma2(rho, splat(p.bfy), Fy);
 }
 
-// n / d by the corrected reciprocal (div_corrected) in both lanes; nd = -d.
-__device__ __forceinline__ float2 div2(float2 n, float2 nd, float2 r)
-{
-    const float2 q0 = mul2(n, r);
-    const float2 e = fma2(q0, nd, n);
-    return fma2(e, r, q0);
-}
-
 // Observables / fields epilogue of the lanes that are collided fluid nodes.
 template <int MODE>
 __device__ __forceinline__ void observe_pair(const float2& rho, const float2& rinv, const float2& jx,
@@ -1034,6 +1081,13 @@ __device__ __forceinline__ void collide_dev_pair(const PulledDev2& n, const bool
 
 // ------------------------------------------------------------------ kernel
 
+// f(std::integral_constant<int, J>) for J = 0, 1, ..., in order
+template <typename F, int... J>
+__device__ __forceinline__ void unroll_seq(std::integer_sequence<int, J...>, F&& f)
+{
+    (f(std::integral_constant<int, J>{}), ...);
+}
+
 __device__ __forceinline__ void mbar_inval(uint64_t* bar)
 {
     asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -1075,8 +1129,8 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
     constexpr size_t SB = stage_bytes<ST>();
     // ring stage s: plane 0 (FP32, R) then the deviations in the layout of
     // dev_index with plane = R (8 planes of R for FP32, 8 per node for 16 bits)
-    float* psi_ring = reinterpret_cast<float*>(smem_raw + kStages * SB);      // [4][kPsiStride]
-    uint64_t* full = reinterpret_cast<uint64_t*>(psi_ring + 4 * kPsiStride);  // [kStages]
+    float* psi_ring = reinterpret_cast<float*>(smem_raw + kStages * SB);            // [kStages][kPsiStride]
+    uint64_t* full = reinterpret_cast<uint64_t*>(psi_ring + kStages * kPsiStride);  // [kStages]
     uint64_t* empty = full + kStages;                                         // [kStages]
     auto stage_ptr = [&](int s) { return smem_raw + size_t(s) * SB; };
 
@@ -1278,14 +1332,6 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
     ok = mbar_wait(&full[0], 0, err) && ok;
     ok = mbar_wait(&full[1], 0, err) && ok;
 
-    // ring position of staged rows k-1, k, k+1 (stage indices and bases) and
-    // the fill parity of row k+1; advanced by one row per body() call
-    int s_m = 0, s_p = 2;
-    uint32_t ph_p = 0;
-    const unsigned char* b_m = stage_ptr(0);
-    const unsigned char* b_c = stage_ptr(1);
-    const unsigned char* b_p = stage_ptr(2);
-
     auto psi_of = [&](bool solid, float rho) { return solid ? 0.f : -p.rho0 * expm1f(-rho * p.inv_rho0); };
     // all-zero fields of the collided solid lanes (kFields)
     auto zero_fields = [&](int xs, int rs) {
@@ -1294,21 +1340,18 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
         fields[nn + i] = 0.0;
         fields[2 * nn + i] = 0.0;
     };
-    auto advance = [&]() {
-        s_m = (s_m == kStages - 1) ? 0 : s_m + 1;
-        s_p = (s_p == kStages - 1) ? 0 : s_p + 1;
-        ph_p ^= (s_p == 0) ? 1u : 0u;
-        b_m = b_c;
-        b_c = b_p;
-        b_p = stage_ptr(s_p);
-    };
 
-    // Row k: pull row r = y0 - 2 + k (staged rows k-1, k, k+1) into `into`,
-    // then collide row r - 1, pulled at row k - 1 into `prev`.
-    auto body = [&](int k, PT2& into, const PT2& prev) {
+    // Row k: pull row r = y0 - 2 + k (staged rows k-1, k, k+1, in stages
+    // s_m, s_c, s_p; row k+1 filled in phase ph_p) into `into`, then collide
+    // row r - 1, pulled at row k - 1 into `prev`. Staged row k sits in stage
+    // k % kStages and its psi in the psi ring row of the same index.
+    auto body = [&](int k, PT2& into, const PT2& prev, int s_m, int s_c, int s_p, uint32_t ph_p) {
         const int r = y0 - 2 + k;
+        const unsigned char* b_m = stage_ptr(s_m);
+        const unsigned char* b_c = stage_ptr(s_c);
+        const unsigned char* b_p = stage_ptr(s_p);
         ok = mbar_wait(&full[s_p], ph_p, err) && ok;
-        float* prow = psi_w + ((r + 4) & 3) * kPsiStride;
+        float* prow = psi_w + s_c * kPsiStride;
         if (active) {
             if constexpr (PR) {
                 const float* s0m = reinterpret_cast<const float*>(b_m);
@@ -1354,9 +1397,9 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
         if (k >= 3) {
             // collide row r-1 with psi rows r-2, r-1, r
             const int rc = r - 1;
-            const float* pm = psi_w + ((rc + 3) & 3) * kPsiStride;
-            const float* pc = psi_w + ((rc + 4) & 3) * kPsiStride;
-            const float* pp = psi_w + ((rc + 5) & 3) * kPsiStride;
+            const float* pm = psi_w + (s_m == 0 ? kStages - 1 : s_m - 1) * kPsiStride;
+            const float* pc = psi_w + s_m * kPsiStride;
+            const float* pp = psi_w + s_c * kPsiStride;
             if constexpr (PR) {
                 const bool col[2] = {col_a && !prev.solid[0], col_b && !prev.solid[1]};
                 if (col[0] || col[1]) {
@@ -1382,7 +1425,6 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
                 }
             }
         }
-        advance();
     };
 
     // two pulled-state register sets used in turn, so that no copy is made
@@ -1392,9 +1434,49 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
     } else {
         n0.solid = n1.solid = true;
     }
-    for (int k = 1; k <= nrows - 2; k += 2) {
-        body(k, n0, n1);
-        if (k + 1 <= nrows - 2) body(k + 1, n1, n0);
+    const int kmax = nrows - 2;
+    if constexpr (is16(ST) && MODE == kStep) {
+    // The plain step of the 16-bit forms (bound by instruction issue) unrolls the row loop by
+    // U rows, a multiple of the ring depth and even: every stage index,
+    // mbarrier address, psi ring row and register set is a compile-time
+    // constant; the fill phase of row k+1 is that of the iteration
+    // (U = kStages) or a constant (U = 2 kStages). Measured at 16384x4096:
+    // 110.7 / 112.0 GLUPS (FP16 / BF16) against 102.9 / 104.5 rolled. The
+    // 32-bit forms keep the rolled loop: unrolled, the pair kernels lost
+    // 2-3% (FP32, 4 rows) and 60% (FP32 deviations, 10 rows of code).
+    constexpr int U = (kStages % 2 == 0) ? kStages : 2 * kStages;
+    uint32_t it = 0;
+    for (int k0 = 1; k0 <= kmax; k0 += U) {
+        unroll_seq(std::make_integer_sequence<int, U>{}, [&](auto jc) {
+            constexpr int J = decltype(jc)::value;
+            constexpr int sm = J % kStages, sc = (J + 1) % kStages, sp = (J + 2) % kStages;
+            const uint32_t ph = (U == kStages ? it : 0u) ^ uint32_t(((J + 2) / kStages) & 1);
+            if (k0 + J <= kmax) {
+                if constexpr (J % 2 == 0)
+                    body(k0 + J, n0, n1, sm, sc, sp, ph);
+                else
+                    body(k0 + J, n1, n0, sm, sc, sp, ph);
+            }
+        });
+        it ^= 1u;
+    }
+    } else {
+        int s_m = 0, s_c = 1, s_p = 2;
+        uint32_t ph_p = 0;
+        auto advance = [&]() {
+            s_m = s_c;
+            s_c = s_p;
+            s_p = (s_p == kStages - 1) ? 0 : s_p + 1;
+            ph_p ^= (s_p == 0) ? 1u : 0u;
+        };
+        for (int k = 1; k <= kmax; k += 2) {
+            body(k, n0, n1, s_m, s_c, s_p, ph_p);
+            advance();
+            if (k + 1 <= kmax) {
+                body(k + 1, n1, n0, s_m, s_c, s_p, ph_p);
+                advance();
+            }
+        }
     }
     (void)ok;
 
@@ -1494,8 +1576,8 @@ __global__ void __launch_bounds__(threads_of(ST, PAIR), batch_ctas_of(MODE, ST, 
                                      tl.w, smem_raw);
         __syncthreads();
         if (threadIdx.x == 0) {
-            uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + stages_of(ST, PAIR) * stage_bytes<ST>() +
-                                                         4 * kPsiStride * sizeof(float));
+            uint64_t* bars = reinterpret_cast<uint64_t*>(
+                smem_raw + stages_of(ST, PAIR) * (stage_bytes<ST>() + kPsiStride * sizeof(float)));
             for (int s = 0; s < 2 * stages_of(ST, PAIR); ++s) mbar_inval(&bars[s]);
         }
         __syncthreads();
