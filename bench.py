@@ -371,7 +371,7 @@ def run_ours(args, rank, world, local_rank):
     return line
 
 
-KERNEL_VERSION = "step-v8"
+KERNEL_VERSION = "step-v9"
 # whether a storage form's steady flux meets the 1e-4 gate against the FP64
 # oracle (tests/test_gpu_steady.py): plain FP32 storage stalls short of it
 STEADY_FLUX_GATE = {"fp32": "misses: stalls about 0.5% short of the steady flux",
