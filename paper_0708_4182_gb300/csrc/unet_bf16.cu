@@ -39,7 +39,6 @@ using bf16 = __nv_bfloat16;
 constexpr int kT = 256;                      // threads of the SIMT kernels
 constexpr int kTcThreads = 128;              // threads of the tensor-core kernels (4 warps = 128 TMEM lanes)
 constexpr int kStages = 4;                   // operand ring depth of the tensor-core kernels
-constexpr int kWgradStep = 64;               // pixels per K-step of the weight gradient where the row allows
 constexpr uint32_t kWaitLimit = 1u << 18;    // try_wait rounds before giving up (about 1 s on a GB300)
 constexpr int kTileRows = 4, kTileCols = 32; // output pixels of one conv CTA (M = 128)
 constexpr int kSmemPerSm = 233472;           // shared memory of one SM (bytes)
@@ -73,6 +72,32 @@ __device__ __forceinline__ void mbar_wait(uint64_t* bar, uint32_t parity, int* e
         if (ok) return;
     }
     atomicOr(err, 1);
+}
+
+// The same for a thread that waits many times: after its first timeout
+// (alive = false) it waits no more, so a kernel that lost a phase ends after
+// one time limit per thread rather than one per wait.
+__device__ __forceinline__ void mbar_wait_alive(uint64_t* bar, uint32_t parity, int* err, bool& alive)
+{
+    if (!alive) return;
+    for (uint32_t i = 0; i < kWaitLimit; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return;
+    }
+    atomicOr(err, 1);
+    alive = false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+                 : "memory");
 }
 
 // 16-byte global -> shared copy; src_bytes = 0 fills zeros (src is not read)
@@ -426,117 +451,153 @@ __global__ void conv_pack_kernel(const float* __restrict__ w, int co, int ci, in
 }
 
 // ------------------------------------------------------------------ tensor-core weight gradient
-// Weight gradient, one CTA per tap row: per K-step of P pixels of one image
-// row (P = 16, 32 or 64, dividing the row), dy (A, 128 output channels x P
-// pixels, MN-major: 8 channels of a pixel in 16 bytes, pixels at a 16-byte
-// pitch, so LBO = 8 pixels and SBO = P pixels) is staged once, and x as a
-// halo row of P + 2 pixels x NT channels (B, MN-major likewise: SBO = P + 2
-// pixels). Each 16-pixel piece j of the step gives three MMAs, one per tap
-// (dy, dx = -1, 0, 1) of the row: A starts 16 j pixels in, B 16 j + dx pixels
-// in, into three accumulators of NT columns (3 NT <= 128 tensor-memory
-// columns). Wider steps stage more bytes per ring slot and wait less often.
+// dw[co][ci][tap] += sum over pixels p of dy[p][co] x[p + off(tap)][ci]: per
+// tap a GEMM with M = 128 output channels, N = NT input channels and K = the
+// pixels. One CTA takes one tap row (dy = -1, 0, 1 of the 3x3 stencil) and a
+// range of npix pixels. Per K-step of P pixels of one image row (P = 16, 32
+// or 64, dividing the row), dy (A, 128 output channels x P pixels, MN-major:
+// 8 channels of a pixel in 16 bytes, pixels at a 16-byte pitch, so LBO = 8
+// pixels and SBO = P pixels) is staged once, and x as a halo row of P + 2
+// pixels x NT channels (B, MN-major likewise: SBO = P + 2 pixels). Each
+// 16-pixel piece j of the step gives three MMAs, one per tap (dx = -1, 0, 1)
+// of the row: A starts 16 j pixels in, B 16 j + dx pixels in, into three
+// accumulators of NT columns (3 NT <= 512 tensor-memory columns).
+//
+// Warp roles: warps 1-3 stage the operands with 16-byte cp.async into a ring
+// of kWgStages slots; each producer thread waits for its own copies of a slot
+// two steps later, fences them for the tensor core's (async) proxy and
+// arrives on the slot's "full" mbarrier (96 arrivals). One thread of warp 0
+// waits on "full", issues the MMAs and commits them to the slot's "empty"
+// mbarrier, which the producers wait on before refilling the slot. No
+// CTA-wide barrier runs inside the K loop. The epilogue adds the three
+// accumulators into dw (FP32 atomics; the grid splits the pixels).
+constexpr int kWgStages = 4;   // operand ring depth of the weight gradient
+constexpr int kWgLag = 2;      // K-steps between a producer's copies and its "full" arrival
+constexpr int kWgProducers = kTcThreads - 32;
 template <int P> __host__ __device__ constexpr int wgrad_halo_pix() { return P + 2; }
+template <int NT, int P> __host__ __device__ constexpr int wgrad_smem_needed()
+{
+    return kWgStages * (128 * P * 2 + (NT / 8) * wgrad_halo_pix<P>() * 16) + 2 * kWgStages * 8 + 16;
+}
 
 template <int NT, int P>
-__global__ void __launch_bounds__(kTcThreads) wgrad_tc_taps_kernel(const bf16* __restrict__ x, int ct_x, int ci,
-                                                                   const bf16* __restrict__ dy, int ct_dy, int co,
-                                                                   float* __restrict__ dw, int H, int W, int npix,
-                                                                   int* __restrict__ err)
+__global__ void __launch_bounds__(kTcThreads) wgrad_tc_kernel(const bf16* __restrict__ x, int ct_x, int ci,
+                                                              const bf16* __restrict__ dy, int ct_dy, int co,
+                                                              float* __restrict__ dw, int H, int W, int npix,
+                                                              int* __restrict__ err)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    static_assert(3 * NT <= int(tmem_cols(3 * NT)), "three accumulators must fit the allocation");
+    static_assert(3 * NT <= 512, "three accumulators must fit the tensor memory");
     static_assert(P == 16 || P == 32 || P == 64, "K-step of 16, 32 or 64 pixels");
+    static_assert(kWgLag < kWgStages, "a producer arrives on a slot before it needs it again");
     constexpr int G = NT / 8;                              // 8-channel groups of B
     constexpr int HP = wgrad_halo_pix<P>();                // halo row pixels
     constexpr int kABytes = 128 * P * 2;                   // 128 output channels x P pixels
     constexpr int kBBytes = G * HP * 16;                   // one halo row of B
     constexpr uint32_t kCols = tmem_cols(3 * NT);
     unsigned char* sa = smem;
-    unsigned char* sb = smem + kStages * kABytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sb + kStages * kBBytes);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + kStages);
+    unsigned char* sb = smem + kWgStages * kABytes;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sb + kWgStages * kBBytes);
+    uint64_t* empty = full + kWgStages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(empty + kWgStages);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int co0 = blockIdx.x * 128, ci0 = blockIdx.y * NT;
     const int trow = blockIdx.z % 3;                       // taps 3 trow .. 3 trow + 2 (row offset trow - 1)
     const int co_here = co - co0 < 128 ? co - co0 : 128;
     const int ci_here = ci - ci0 < NT ? ci - ci0 : NT;
-    const long long p_begin = (long long)(blockIdx.z / 3) * npix;
     const int KT = npix / P;
 
     // rows of A beyond co_here and channel groups of B beyond ci_here are never loaded: zero them once
-    for (int i = tid; i < kStages * (kABytes + kBBytes) / 16; i += kTcThreads)
+    for (int i = tid; i < kWgStages * (kABytes + kBBytes) / 16; i += kTcThreads)
         reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < kWgStages; ++s) {
+            mbar_init(&full[s], kWgProducers);
+            mbar_init(&empty[s], 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) tmem_alloc(tmem_slot, kCols);
+    fence_proxy_async();  // the zeroed slots, before the tensor core reads them
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    bool alive = true;
 
-    const int ga = co_here / 8, gb = (ci_here + 7) / 8;
-    auto load = [&](int it) {
-        const int s = it % kStages;
-        const long long p0 = p_begin + (long long)it * P;
-        const int bimg = int(p0 / ((long long)H * W));
-        const int rem = int(p0 % ((long long)H * W));
-        const int yy = rem / W, x0 = rem % W;
-        unsigned char* da = sa + s * kABytes;
-        unsigned char* db = sb + s * kBBytes;
-        for (int q = tid; q < P * ga; q += kTcThreads) {
-            const int k = q % P, g = q / P;
-            const bf16* src = dy + (size_t(bimg * H + yy) * W + x0 + k) * ct_dy + co0 + g * 8;
-            cp_async16_cg(da + g * (P * 16) + k * 16, src, 16u);
-        }
-        const int ys = yy + trow - 1;
-        const bool ok = ys >= 0 && ys < H;
-        for (int q = tid; q < HP * gb; q += kTcThreads) {
-            const int pix = q % HP, g = q / HP;
-            const int xs = wrapx(x0 + pix - 1, W);
-            const bf16* src = ok ? x + (size_t(bimg * H + ys) * W + xs) * ct_x + ci0 + g * 8 : x;
-            cp_async16_ca(db + g * (HP * 16) + pix * 16, src, ok ? 16u : 0u);
-        }
-    };
-
-    constexpr uint32_t idesc = idesc_bf16(NT, true, true);
+    if (warp == 0) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(NT, true, true);
 #pragma unroll 1
-    for (int it = 0; it < kStages - 1; ++it) {
-        if (it < KT) load(it);
-        cp_async_commit();
-    }
+            for (int k = 0; k < KT; ++k) {
+                const int s = k % kWgStages;
+                mbar_wait_alive(&full[s], uint32_t(k / kWgStages) & 1u, err, alive);
+                tc_fence_after();
+                const uint32_t a0 = smem_u32(sa + s * kABytes);
+                const uint32_t b0 = smem_u32(sb + s * kBBytes);
+#pragma unroll
+                for (int j = 0; j < P / 16; ++j) {
+                    const uint64_t da = smem_desc(a0 + j * 256, 128, P * 16);
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx) {
+                        const uint64_t db = smem_desc(b0 + (16 * j + dx) * 16, 128, HP * 16);
+                        mma_bf16(tmem + dx * NT, da, db, idesc, (k > 0 || j > 0) ? 1u : 0u);
+                    }
+                }
+                mma_commit(&empty[s]);
+            }
+        }
+        __syncwarp();
+    } else {
+        const int pt = tid - 32;                           // producer thread 0 .. 95
+        const int ga = (co_here + 7) / 8, gb = (ci_here + 7) / 8;
+        // position of K-step k: image bimg, row yy, first column x0 (each step
+        // lies inside one image row), advanced incrementally
+        const long long p_begin = (long long)(blockIdx.z / 3) * npix;
+        int bimg = int(p_begin / ((long long)H * W));
+        const int rem = int(p_begin - (long long)bimg * H * W);
+        int yy = rem / W, x0 = rem % W;
 #pragma unroll 1
-    for (int it = 0; it < KT; ++it) {
-        const int s = it % kStages;
-        cp_async_wait<kStages - 2>();
-        fence_proxy_async();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            const uint32_t a0 = smem_u32(sa + s * kABytes);
-            const uint32_t b0 = smem_u32(sb + s * kBBytes);
-#pragma unroll
-            for (int j = 0; j < P / 16; ++j) {
-                const uint64_t da = smem_desc(a0 + j * 256, 128, P * 16);
-#pragma unroll
-                for (int dx = 0; dx < 3; ++dx) {
-                    const uint64_t db = smem_desc(b0 + (16 * j + dx) * 16, 128, HP * 16);
-                    mma_bf16(tmem + dx * NT, da, db, idesc, (it > 0 || j > 0) ? 1u : 0u);
+        for (int k = 0; k < KT; ++k) {
+            const int s = k % kWgStages;
+            if (k >= kWgStages) mbar_wait_alive(&empty[s], uint32_t((k / kWgStages) - 1) & 1u, err, alive);
+            unsigned char* da = sa + s * kABytes;
+            unsigned char* db = sb + s * kBBytes;
+            const bf16* arow = dy + (size_t(bimg * H + yy) * W + x0) * ct_dy + co0;
+            for (int q = pt; q < P * ga; q += kWgProducers) {
+                const int kk = q % P, g = q / P;
+                cp_async16_cg(da + g * (P * 16) + kk * 16, arow + size_t(kk) * ct_dy + g * 8, 16u);
+            }
+            const int ys = yy + trow - 1;
+            const bool ok = ys >= 0 && ys < H;
+            const bf16* brow = x + size_t(bimg * H + (ok ? ys : 0)) * W * ct_x + ci0;
+            for (int q = pt; q < HP * gb; q += kWgProducers) {
+                const int pix = q % HP, g = q / HP;
+                const int xs = wrapx(x0 + pix - 1, W);
+                cp_async16_ca(db + g * (HP * 16) + pix * 16, ok ? brow + size_t(xs) * ct_x + g * 8 : x, ok ? 16u : 0u);
+            }
+            cp_async_commit();
+            if (k >= kWgLag) {
+                cp_async_wait<kWgLag>();
+                fence_proxy_async();
+                mbar_arrive(&full[(k - kWgLag) % kWgStages]);
+            }
+            x0 += P;
+            if (x0 == W) {
+                x0 = 0;
+                if (++yy == H) {
+                    yy = 0;
+                    ++bimg;
                 }
             }
-            mma_commit(&bars[s]);
         }
-        const int nxt = it + kStages - 1;
-        if (nxt < KT) {
-            if (nxt >= kStages) mbar_wait(&bars[nxt % kStages], uint32_t((nxt / kStages) - 1) & 1u, err);
-            load(nxt);
-        }
-        cp_async_commit();
+        cp_async_wait<0>();
+        fence_proxy_async();
+        for (int k = KT > kWgLag ? KT - kWgLag : 0; k < KT; ++k) mbar_arrive(&full[k % kWgStages]);
     }
-    cp_async_wait<0>();
-    mbar_wait(&bars[(KT - 1) % kStages], uint32_t((KT - 1) / kStages) & 1u, err);
+    // every warp: the last commit completes when all MMAs have
+    mbar_wait_alive(&empty[(KT - 1) % kWgStages], uint32_t((KT - 1) / kWgStages) & 1u, err, alive);
     tc_fence_after();
 
     const int m = warp * 32 + lane;  // output channel co0 + m
@@ -893,12 +954,11 @@ int launch_conv(const void* x, int ct_in, int kc, const void* wt, const float* b
 }
 
 template <int NT, int P>
-int launch_wgrad_taps_p(const void* x, int ct_x, int ci, const void* dy, int ct_dy, int co, float* dw, int h, int wd,
-                        int npix, long long total, cudaStream_t st)
+int launch_wgrad_p(const void* x, int ct_x, int ci, const void* dy, int ct_dy, int co, float* dw, int h, int wd,
+                   int npix, long long total, cudaStream_t st)
 {
-    constexpr int needed = kStages * (128 * P * 2 + (NT / 8) * wgrad_halo_pix<P>() * 16) + kStages * 8 + 16;
-    const int smem = smem_for_tmem(int(tmem_cols(3 * NT)), needed);
-    auto k = wgrad_tc_taps_kernel<NT, P>;
+    const int smem = smem_for_tmem(int(tmem_cols(3 * NT)), wgrad_smem_needed<NT, P>());
+    auto k = wgrad_tc_kernel<NT, P>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return int(e);
     dim3 grid((co + 127) / 128, (ci + NT - 1) / NT, int(3 * (total / npix)));
@@ -907,25 +967,42 @@ int launch_wgrad_taps_p(const void* x, int ct_x, int ci, const void* dy, int ct_
     return status(cudaGetLastError());
 }
 
-template <int NT>
-int launch_wgrad_taps(const void* x, int ct_x, int ci, const void* dy, int ct_dy, int co, float* dw, int n, int h,
-                      int wd, cudaStream_t st)
+// CTAs of the weight gradient that fit on one SM (shared and tensor memory)
+template <int NT, int P> int wgrad_ctas_per_sm()
 {
-    // pixels per CTA: a power of two (whole 16-pixel row pieces) dividing the
-    // total, at most 2048, halved while the grid has fewer than four CTAs per
-    // SM (at least 64 pixels per CTA)
+    const int smem = smem_for_tmem(int(tmem_cols(3 * NT)), wgrad_smem_needed<NT, P>());
+    const int by_smem = kSmemPerSm / (smem + 1024), by_tmem = 512 / int(tmem_cols(3 * NT));
+    return by_smem < by_tmem ? (by_smem > 0 ? by_smem : 1) : by_tmem;
+}
+
+template <int NT, int P>
+int launch_wgrad_np(const void* x, int ct_x, int ci, const void* dy, int ct_dy, int co, float* dw, int n, int h,
+                    int wd, cudaStream_t st)
+{
+    // pixels per CTA: a power of two dividing the total, at most 4096 (long
+    // K loops: the tensor time of one layer is a few microseconds, and each
+    // split adds its co x ci x 3 partial sums into dw with atomics), halved
+    // while the grid fills less than half of the CTA slots, down to 8 K-steps
     const long long total = (long long)n * h * wd;
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+    const long long slots = (long long)(sms > 0 ? sms : 148) * wgrad_ctas_per_sm<NT, P>();
     const long long tiles = 3LL * ((co + 127) / 128) * ((ci + NT - 1) / NT);
-    int npix = 2048;
-    while (npix > 16 && total % npix) npix >>= 1;
-    while (npix > 64 && tiles * (total / npix) < 4LL * (sms > 0 ? sms : 148) && total % (npix / 2) == 0) npix >>= 1;
-    // K-step: kWgradStep pixels if that divides both the row and
-    // the CTA's pixel range (every step stays inside one image row), else 16
-    if (wd % kWgradStep == 0 && npix % kWgradStep == 0)
-        return launch_wgrad_taps_p<NT, kWgradStep>(x, ct_x, ci, dy, ct_dy, co, dw, h, wd, npix, total, st);
-    return launch_wgrad_taps_p<NT, 16>(x, ct_x, ci, dy, ct_dy, co, dw, h, wd, npix, total, st);
+    int npix = 4096;
+    while (npix > P && total % npix) npix >>= 1;
+    while (npix > 8 * P && tiles * (total / npix) < slots / 2 && total % (npix / 2) == 0) npix >>= 1;
+    return launch_wgrad_p<NT, P>(x, ct_x, ci, dy, ct_dy, co, dw, h, wd, npix, total, st);
+}
+
+template <int NT>
+int launch_wgrad(const void* x, int ct_x, int ci, const void* dy, int ct_dy, int co, float* dw, int n, int h,
+                 int wd, cudaStream_t st)
+{
+    // K-step: the widest of 64, 32, 16 pixels that divides the row (every
+    // step stays inside one image row)
+    if (wd % 64 == 0) return launch_wgrad_np<NT, 64>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
+    if (wd % 32 == 0) return launch_wgrad_np<NT, 32>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
+    return launch_wgrad_np<NT, 16>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
 }
 
 }  // namespace
@@ -980,11 +1057,16 @@ int unet_conv3x3_bwd_weight(const void* x, int ct_x, int ci, const void* dy, int
         (reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(dy)) & 15)
         return -1;
     cudaStream_t st = (cudaStream_t)stream;
+    // input-channel tile: 128, 64, 32 or 16 (at most ci rounded up to 16)
     int rc;
-    if (ci <= 16)
-        rc = launch_wgrad_taps<16>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
+    if (ci > 64)
+        rc = launch_wgrad<128>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
+    else if (ci > 32)
+        rc = launch_wgrad<64>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
+    else if (ci > 16)
+        rc = launch_wgrad<32>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
     else
-        rc = launch_wgrad_taps<32>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
+        rc = launch_wgrad<16>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
     if (rc || !db) return rc;
     const long long npix = (long long)n * h * wd;
     const int per = 1024;
