@@ -40,6 +40,14 @@ size_t unet_conv_pack_elems(int co, int ci, int transpose);
  * elements. */
 int unet_conv_pack(const float *w, int co, int ci, int transpose, void *out, void *stream);
 
+/* Several unet_conv_pack calls in one launch. jobs (device memory, int64)
+ * holds njobs records of 5 values: the address of w, co, ci, transpose and
+ * the address of out (each as for unet_conv_pack, co or ci a multiple of 32
+ * as the packing needs); max_elems bounds the largest record's
+ * unet_conv_pack_elems (it sizes the grid). Returns -1 for a NULL table,
+ * njobs outside 1 .. 65535 or max_elems < 1. */
+int unet_conv_pack_many(const long long *jobs, int njobs, long max_elems, void *stream);
+
 /* 3x3 convolution on the tensor cores (tcgen05.mma, FP32 accumulation in
  * tensor memory): y[b, p, o] = act(bias[o] + sum_{tap, i} W[o][i](tap)
  * x[b, p + off(tap), i]) with W the packed operand `wt`; bias may be NULL,
@@ -106,6 +114,21 @@ int unet_mse(const float *pred, const float *target, const float *wc, int c, int
  * w_bf16 (may be NULL) receives the BF16 compute copy. */
 int unet_adam(float *w_master, void *w_bf16, const float *grad, float *m, float *v, long count, float lr,
               float beta1, float beta2, float eps, int step, float weight_decay, void *stream);
+
+/* The same with the step's scalars read from device memory: hyper[0] = lr,
+ * hyper[1] = 1 - beta1^t, hyper[2] = 1 - beta2^t (written by
+ * unet_adam_hyper), so that a captured CUDA graph of training steps replays
+ * with each step's values. Returns -1 if hyper is NULL. */
+int unet_adam_dev(float *w_master, void *w_bf16, const float *grad, float *m, float *v, long count,
+                  const float *hyper, float beta1, float beta2, float eps, float weight_decay, void *stream);
+
+/* Advance a device-side Adam step: state (6 floats, device) holds [0] the
+ * step t (start 0), [1] beta1^t and [2] beta2^t (start 1, multiplied in
+ * FP32 as unet_adam does); the call increments t and writes [3] the learning
+ * rate lr_schedule[t - 1] (device, n >= 1 entries, the last one beyond the
+ * end), [4] 1 - beta1^t and [5] 1 - beta2^t: the hyper argument of
+ * unet_adam_dev is state + 3. Returns -1 for NULL pointers or n < 1. */
+int unet_adam_hyper(float *state, const float *lr_schedule, int n, float beta1, float beta2, void *stream);
 
 /* Warm-start fields of n domains (n <= 65535) from the network output y
  * [n][3][hw] (FP32, normalised): on fluid nodes (mask [n][hw] == 0)

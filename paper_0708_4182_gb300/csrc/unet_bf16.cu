@@ -429,25 +429,46 @@ __global__ void __launch_bounds__(kTcThreads) conv3x3_tc_row_kernel(const bf16* 
 // blocks [n tile][k chunk of 16][tap] of NT x 16 BF16 in core-matrix order
 // (row group i at 256 B, k half j at 128 B, row r at 16 B); k beyond the real
 // channels is 0.
+__device__ __forceinline__ void pack_one(const float* __restrict__ w, int co, int ci, int transpose, int nt, int kc,
+                                         long long i, bf16* __restrict__ out)
+{
+    const int kreal = transpose ? co : ci;
+    const int k = int(i % (kc * 16));
+    const long long r1 = i / (kc * 16);
+    const int t = int(r1 % 9);
+    const int n = int(r1 / 9);
+    float v = 0.f;
+    if (k < kreal) v = transpose ? w[(size_t(k) * ci + n) * 9 + (8 - t)] : w[(size_t(n) * ci + k) * 9 + t];
+    const int nbk = n / nt, nn = n % nt, c = k / 16, kk = k % 16;
+    const size_t blk = (size_t(nbk) * kc + c) * 9 + t;
+    const size_t off = blk * nt * 16 + ((nn >> 3) * 2 + (kk >> 3)) * 64 + (nn & 7) * 8 + (kk & 7);
+    out[off] = __float2bfloat16_rn(v);
+}
+
 __global__ void conv_pack_kernel(const float* __restrict__ w, int co, int ci, int transpose, int nt, int kc,
                                  bf16* __restrict__ out)
 {
     const int nrows = transpose ? ci : co;
-    const int kreal = transpose ? co : ci;
     const long long total = (long long)nrows * kc * 16 * 9;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int k = int(i % (kc * 16));
-        const long long r1 = i / (kc * 16);
-        const int t = int(r1 % 9);
-        const int n = int(r1 / 9);
-        float v = 0.f;
-        if (k < kreal) v = transpose ? w[(size_t(k) * ci + n) * 9 + (8 - t)] : w[(size_t(n) * ci + k) * 9 + t];
-        const int nbk = n / nt, nn = n % nt, c = k / 16, kk = k % 16;
-        const size_t blk = (size_t(nbk) * kc + c) * 9 + t;
-        const size_t off = blk * nt * 16 + ((nn >> 3) * 2 + (kk >> 3)) * 64 + (nn & 7) * 8 + (kk & 7);
-        out[off] = __float2bfloat16_rn(v);
-    }
+         i += (long long)gridDim.x * blockDim.x)
+        pack_one(w, co, ci, transpose, nt, kc, i, out);
+}
+
+// Several packings in one launch: job blockIdx.y is the record
+// jobs[5 y .. 5 y + 4] = (address of w, co, ci, transpose, address of out).
+__global__ void conv_pack_many_kernel(const long long* __restrict__ jobs)
+{
+    const long long* j = jobs + 5 * blockIdx.y;
+    const float* w = reinterpret_cast<const float*>(j[0]);
+    const int co = int(j[1]), ci = int(j[2]), transpose = int(j[3]);
+    bf16* out = reinterpret_cast<bf16*>(j[4]);
+    const int nrows = transpose ? ci : co, kreal = transpose ? co : ci;
+    const int kc = (kreal + 15) / 16, nt = conv_ntile(nrows);
+    const long long total = (long long)nrows * kc * 16 * 9;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x)
+        pack_one(w, co, ci, transpose, nt, kc, i, out);
 }
 
 // ------------------------------------------------------------------ tensor-core weight gradient
@@ -847,10 +868,17 @@ __global__ void mse_kernel(const float* __restrict__ p, const float* __restrict_
 }
 
 // Adam on FP32 master weights; writes the BF16 compute copy if wb != NULL
+// hyper (may be NULL): lr, c1 = 1 - b1^t, c2 = 1 - b2^t read from device
+// memory instead of the arguments (a replayable graph of training steps)
 __global__ void adam_kernel(float* __restrict__ wm, bf16* __restrict__ wb, const float* __restrict__ g,
                             float* __restrict__ m, float* __restrict__ v, long long n, float lr, float b1, float b2,
-                            float eps, float c1, float c2, float wd)
+                            float eps, float c1, float c2, float wd, const float* __restrict__ hyper)
 {
+    if (hyper) {
+        lr = hyper[0];
+        c1 = hyper[1];
+        c2 = hyper[2];
+    }
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const float gi = g[i] + wd * wm[i];
         const float mi = b1 * m[i] + (1.f - b1) * gi;
@@ -861,6 +889,24 @@ __global__ void adam_kernel(float* __restrict__ wm, bf16* __restrict__ wb, const
         wm[i] = w;
         if (wb) wb[i] = __float2bfloat16_rn(w);
     }
+}
+
+// One training step's Adam scalars on the device. state: [0] t, [1] b1^t,
+// [2] b2^t (running products, multiplied in FP32 as the host entry does),
+// then the step's [3] lr = lr_sched[t - 1] (the last entry beyond the end),
+// [4] 1 - b1^t, [5] 1 - b2^t.
+__global__ void adam_hyper_kernel(float* __restrict__ state, const float* __restrict__ lr_sched, int n, float b1,
+                                  float b2)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int t = int(state[0]) + 1;
+    const float p1 = state[1] * b1, p2 = state[2] * b2;
+    state[0] = float(t);
+    state[1] = p1;
+    state[2] = p2;
+    state[3] = lr_sched[t - 1 < n ? t - 1 : n - 1];
+    state[4] = 1.f - p1;
+    state[5] = 1.f - p2;
 }
 
 __global__ void f32_to_bf16_kernel(const float* __restrict__ x, bf16* __restrict__ y, long long n)
@@ -1032,6 +1078,13 @@ int unet_conv_pack(const float* w, int co, int ci, int transpose, void* out, voi
     return status(cudaGetLastError());
 }
 
+int unet_conv_pack_many(const long long* jobs, int njobs, long max_elems, void* stream)
+{
+    if (!jobs || njobs < 1 || njobs > 65535 || max_elems < 1) return -1;
+    conv_pack_many_kernel<<<dim3(blocks_for(max_elems), njobs), kT, 0, (cudaStream_t)stream>>>(jobs);
+    return status(cudaGetLastError());
+}
+
 int unet_conv3x3(const void* x, int ct_in, int cin, const void* wt, const float* bias, void* y, int ct_out, int cout,
                  int n, int h, int wd, int relu, void* stream)
 {
@@ -1174,7 +1227,23 @@ int unet_adam(float* w_master, void* w_bf16, const float* grad, float* m, float*
     }
     adam_kernel<<<blocks_for(count), kT, 0, (cudaStream_t)stream>>>(w_master, (bf16*)w_bf16, grad, m, v, count, lr,
                                                                     beta1, beta2, eps, 1.f - c1, 1.f - c2,
-                                                                    weight_decay);
+                                                                    weight_decay, nullptr);
+    return status(cudaGetLastError());
+}
+
+int unet_adam_dev(float* w_master, void* w_bf16, const float* grad, float* m, float* v, long count,
+                  const float* hyper, float beta1, float beta2, float eps, float weight_decay, void* stream)
+{
+    if (!hyper) return -1;
+    adam_kernel<<<blocks_for(count), kT, 0, (cudaStream_t)stream>>>(w_master, (bf16*)w_bf16, grad, m, v, count, 0.f,
+                                                                    beta1, beta2, eps, 1.f, 1.f, weight_decay, hyper);
+    return status(cudaGetLastError());
+}
+
+int unet_adam_hyper(float* state, const float* lr_schedule, int n, float beta1, float beta2, void* stream)
+{
+    if (!state || !lr_schedule || n < 1) return -1;
+    adam_hyper_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(state, lr_schedule, n, beta1, beta2);
     return status(cudaGetLastError());
 }
 

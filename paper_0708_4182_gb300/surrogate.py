@@ -46,6 +46,7 @@ def load_unet():
         "unet_conv_ntile": ([I], I),
         "unet_conv_pack_elems": ([I, I, I], ctypes.c_size_t),
         "unet_conv_pack": ([vp, I, I, I, vp, vp], I),
+        "unet_conv_pack_many": ([vp, I, L, vp], I),
         "unet_conv3x3": ([vp, I, I, vp, vp, vp, I, I, I, I, I, I, vp], I),
         "unet_conv3x3_bwd_weight": ([vp, I, I, vp, I, I, vp, vp, I, I, I, vp], I),
         "unet_tc_error": ([vp, I], I),
@@ -59,6 +60,8 @@ def load_unet():
         "unet_input_nhwc": ([vp, I, I, I, vp, I, vp], I),
         "unet_mse": ([vp, vp, vp, I, I, L, vp, vp, vp], I),
         "unet_adam": ([vp, vp, vp, vp, vp, L, F, F, F, F, I, F, vp], I),
+        "unet_adam_dev": ([vp, vp, vp, vp, vp, L, vp, F, F, F, F, vp], I),
+        "unet_adam_hyper": ([vp, vp, I, F, F, vp], I),
         "unet_f32_to_bf16": ([vp, vp, L, vp], I),
         "unet_warm_fields": ([vp, I, I, vp, vp, F, F, F, ctypes.c_double, ctypes.c_double, vp, vp, vp], I),
     }
@@ -122,21 +125,41 @@ class UNet:
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.s = ctypes.c_void_p(self.stream.cuda_stream)
         g = torch.Generator().manual_seed(seed)
+        # All weights, then all biases, in flat FP32 buffers (master values,
+        # gradients, Adam moments) and one BF16 copy: the optimizer step, the
+        # gradient reset and the BF16 copy are one launch each.
+        self.n_w = sum(co * ci * k * k for co, ci, k in self.shapes.values())
+        n_all = self.n_w + sum(co for co, _, _ in self.shapes.values())
+        self.flat = {key: torch.zeros(n_all, device=self.dev) for key in ("w", "g", "m", "v")}
+        self.flat["wb"] = torch.zeros(n_all, dtype=torch.bfloat16, device=self.dev)
         self.params = {}
+        self._offsets = {}
+        wo, bo = 0, self.n_w
         for name, (co, ci, k) in self.shapes.items():
             std = (2.0 / (ci * k * k)) ** 0.5
             wm = (torch.randn((co, ci, k, k), generator=g, dtype=torch.float64) * std).float().to(self.dev)
+            self._offsets[name] = (wo, bo)
             self.params[name] = self._param(name, wm, torch.zeros(co, device=self.dev))
+            wo += co * ci * k * k
+            bo += co
+        self._pack_jobs()
         self.step_count = 0
         self.norm = dict(rho_mean=1.5, rho_std=1.0, u_scale=1e-3)
+        self._wc_cache = {}
+        self.train_graph = None
         self._alloc(batch)
 
     def _param(self, name, wm, bm):
         t = self.torch
-        p = dict(w=wm.contiguous(), b=bm.contiguous(), wb=t.empty_like(wm, dtype=t.bfloat16), gw=t.zeros_like(wm),
-                 gb=t.zeros_like(bm), mw=t.zeros_like(wm), vw=t.zeros_like(wm), mb=t.zeros_like(bm),
-                 vb=t.zeros_like(bm))
         co, ci, k = self.shapes[name]
+        wo, bo = self._offsets[name]
+        nw = co * ci * k * k
+        fw = lambda key: self.flat[key][wo:wo + nw].view(co, ci, k, k)  # noqa: E731
+        fb = lambda key: self.flat[key][bo:bo + co]  # noqa: E731
+        p = dict(w=fw("w"), b=fb("w"), wb=fw("wb"), gw=fw("g"), gb=fb("g"), mw=fw("m"), vw=fw("v"), mb=fb("m"),
+                 vb=fb("v"))
+        p["w"].copy_(wm)
+        p["b"].copy_(bm)
         if k == 3:
             p["wt"] = t.empty(int(self.lib.unet_conv_pack_elems(co, ci, 0)), dtype=t.bfloat16, device=self.dev)
             if ci % 32 == 0:  # the input gradient of the first layer is not needed
@@ -155,6 +178,24 @@ class UNet:
             if "wtT" in p:
                 _call(self.lib.unet_conv_pack, ctypes.c_void_p(p["w"].data_ptr()), co, ci, 1,
                       ctypes.c_void_p(p["wtT"].data_ptr()), self.s)
+
+    def _pack_jobs(self):
+        """Device table of every layer's packings (unet_conv_pack_many)."""
+        jobs, most = [], 1
+        for name, p in self.params.items():
+            co, ci, k = self.shapes[name]
+            for tr, key in ((0, "wt"), (1, "wtT")):
+                if key in p:
+                    jobs.append([p["w"].data_ptr(), co, ci, tr, p[key].data_ptr()])
+                    most = max(most, int(self.lib.unet_conv_pack_elems(co, ci, tr)))
+        self.pack_table = self.torch.tensor(jobs, dtype=self.torch.int64, device=self.dev)
+        self.pack_most = most
+
+    def _refresh_packs(self):
+        """Packed tensor-core operands of every layer from the FP32 master
+        weights (one launch; the optimizer writes the BF16 copies itself)."""
+        _call(self.lib.unet_conv_pack_many, ctypes.c_void_p(self.pack_table.data_ptr()),
+              int(self.pack_table.shape[0]), self.pack_most, self.s)
 
     def set_weights(self, weights: dict):
         """Load FP32 weights/biases {name: (w, b)} (e.g. to match a reference)."""
@@ -251,12 +292,10 @@ class UNet:
         (a float, or with sync=False the FP64 device scalar)."""
         t, lib, n, s = self.torch, self.lib, self.batch, self.s
         H, W = self.H, self.W
-        for p in self.params.values():
-            p["gw"].zero_()
-            p["gb"].zero_()
+        self.flat["g"].zero_()
         self.loss_acc.zero_()
         tg = target.contiguous().float()
-        wct = t.as_tensor(wc, dtype=t.float32, device=self.dev)
+        wct = self._wc_dev(wc)
         _call(lib.unet_mse, ctypes.c_void_p(self.out.data_ptr()), ctypes.c_void_p(tg.data_ptr()),
               ctypes.c_void_p(wct.data_ptr()), OUT_CH, H * W, self.out.numel(),
               ctypes.c_void_p(self.gout.data_ptr()), ctypes.c_void_p(self.loss_acc.data_ptr()), s)
@@ -296,18 +335,86 @@ class UNet:
                            None if l == 0 else View(self.gP[l - 1], 0, C[l - 1]), hh, ww)
         return float(self.loss_acc.item()) if sync else self.loss_acc.clone()
 
-    def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0):
+    def _wc_dev(self, wc):
+        """Channel weights of the loss as a device tensor (made once per value,
+        so that a captured training step copies nothing from the host)."""
+        key = tuple(float(v) for v in wc)
+        d = self._wc_cache.get(key)
+        if d is None:
+            d = self.torch.tensor(key, dtype=self.torch.float32, device=self.dev)
+            self._wc_cache[key] = d
+        return d
+
+    def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, hyper=None):
+        """One Adam step. hyper (device address of lr, 1 - beta1^t, 1 - beta2^t,
+        written by unet_adam_hyper) replaces lr and the host step count."""
+        if hyper is None:
+            self.step_count += 1
+        f = self.flat
+        n_all = f["w"].numel()
+        # weight decay on the weights only: one launch over everything without it
+        ranges = [(0, n_all, weight_decay)] if weight_decay == 0.0 else \
+            [(0, self.n_w, weight_decay), (self.n_w, n_all, 0.0)]
+        for a, b, wd in ranges:
+            args = tuple(ctypes.c_void_p(f[key].data_ptr() + a * f[key].element_size())
+                         for key in ("w", "wb", "g", "m", "v")) + (b - a,)
+            if hyper is None:
+                _call(self.lib.unet_adam, *args, lr, beta1, beta2, eps, self.step_count, wd, self.s)
+            else:
+                _call(self.lib.unet_adam_dev, *args, ctypes.c_void_p(hyper), beta1, beta2, eps, wd, self.s)
+        self._refresh_packs()
+
+    def make_train_graph(self, wc, lr_schedule, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0):
+        """Capture one training step (forward, loss and backward, Adam) as a
+        CUDA graph reading its input planes from self.g_in and its targets
+        from self.g_tg; replay k uses learning rate lr_schedule[k] (the last
+        entry beyond the end) and continues the Adam step count on the
+        device (self.adam_state, see unet_adam_hyper)."""
+        import numpy as np
+        t = self.torch
+        self.g_in = t.zeros((self.B, self.in_ch, self.H, self.W), device=self.dev)
+        self.g_tg = t.zeros((self.B, OUT_CH, self.H, self.W), device=self.dev)
+        p1, p2 = np.float32(1.0), np.float32(1.0)
+        for _ in range(self.step_count):  # the running products of the host path, in FP32
+            p1, p2 = np.float32(p1 * np.float32(beta1)), np.float32(p2 * np.float32(beta2))
+        self.adam_state = t.tensor([float(self.step_count), float(p1), float(p2), 0.0, 0.0, 0.0],
+                                   dtype=t.float32, device=self.dev)
+        self.lr_sched = t.tensor([float(v) for v in lr_schedule], dtype=t.float32, device=self.dev)
+        self._wc_dev(wc)
+        side = t.cuda.Stream()
+        side.wait_stream(self.stream)
+        old = (self.stream, self.s)
+        self.stream, self.s = side, ctypes.c_void_p(side.cuda_stream)
+        try:
+            with t.cuda.stream(side):
+                # one pass without the optimizer step before capture (lazy set-up)
+                self.forward(self.g_in)
+                self.loss_backward(self.g_tg, wc, sync=False)
+            side.synchronize()
+            g = t.cuda.CUDAGraph()
+            with t.cuda.graph(g, stream=side):
+                _call(self.lib.unet_adam_hyper, ctypes.c_void_p(self.adam_state.data_ptr()),
+                      ctypes.c_void_p(self.lr_sched.data_ptr()), int(self.lr_sched.numel()), beta1, beta2, self.s)
+                self.forward(self.g_in)
+                self.loss_backward(self.g_tg, wc, sync=False)
+                self.adam(beta1=beta1, beta2=beta2, eps=eps, weight_decay=weight_decay,
+                          hyper=self.adam_state.data_ptr() + 3 * 4)
+        finally:
+            self.stream, self.s = old
+        self.stream.wait_stream(side)
+        self.train_graph = g
+        return g
+
+    def replay_train_step(self, planes, targets):
+        """One captured training step on the given batch (copied into the
+        graph's input and target buffers on the network's stream); the loss
+        lands in self.loss_acc."""
+        t = self.torch
+        with t.cuda.stream(self.stream):
+            self.g_in.copy_(planes)
+            self.g_tg.copy_(targets)
+            self.train_graph.replay()
         self.step_count += 1
-        for name, p in self.params.items():
-            _call(self.lib.unet_adam, ctypes.c_void_p(p["w"].data_ptr()), ctypes.c_void_p(p["wb"].data_ptr()),
-                  ctypes.c_void_p(p["gw"].data_ptr()), ctypes.c_void_p(p["mw"].data_ptr()),
-                  ctypes.c_void_p(p["vw"].data_ptr()), p["w"].numel(), lr, beta1, beta2, eps, self.step_count,
-                  weight_decay, self.s)
-            _call(self.lib.unet_adam, ctypes.c_void_p(p["b"].data_ptr()), None, ctypes.c_void_p(p["gb"].data_ptr()),
-                  ctypes.c_void_p(p["mb"].data_ptr()), ctypes.c_void_p(p["vb"].data_ptr()), p["b"].numel(), lr,
-                  beta1, beta2, eps, self.step_count, 0.0, self.s)
-            if "wt" in p:
-                self._refresh(name, p)
 
     def check_tensor_cores(self):
         """Raise if a tensor-core kernel's bounded wait timed out (flag cleared)."""
@@ -426,16 +533,22 @@ def fit_normalisation(net, fields, mask):
     return net.norm
 
 
-def train(net, planes, targets, epochs=20, lr=2e-3, wc=(1.0, 1.0, 0.25), seed=0, lr_final=1e-4):
+def train(net, planes, targets, epochs=20, lr=2e-3, wc=(1.0, 1.0, 0.25), seed=0, lr_final=1e-4, graph=True):
     """Adam over shuffled mini-batches (the network's batch size) with a
     cosine learning-rate decay from lr to lr_final; returns the mean loss of
-    every epoch."""
+    every epoch. graph: replay one captured CUDA graph per step (the same
+    kernels and values as the step-by-step launches, without the host cost
+    of about 200 launches per step)."""
     import math
     t = net.torch
     g = t.Generator().manual_seed(seed)
     n = planes.shape[0]
     per_epoch = n // net.batch
     total = epochs * per_epoch
+    rates = [lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * k / max(1, total - 1)))
+             for k in range(total)]
+    if graph:
+        net.make_train_graph(wc, rates)
     history = []
     k = 0
     for _ in range(epochs):
@@ -443,10 +556,14 @@ def train(net, planes, targets, epochs=20, lr=2e-3, wc=(1.0, 1.0, 0.25), seed=0,
         acc = t.zeros(1, dtype=t.float64, device=planes.device)
         for j in range(per_epoch):
             idx = perm[j * net.batch:(j + 1) * net.batch]
-            net.forward(planes[idx])
-            acc += net.loss_backward(targets[idx], wc, sync=False)
-            rate = lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * k / max(1, total - 1)))
-            net.adam(lr=rate)
+            if graph:
+                net.replay_train_step(planes[idx], targets[idx])
+                with t.cuda.stream(net.stream):
+                    acc += net.loss_acc
+            else:
+                net.forward(planes[idx])
+                acc += net.loss_backward(targets[idx], wc, sync=False)
+                net.adam(lr=rates[k])
             k += 1
         history.append(float(acc.item()) / per_epoch)
     return history
@@ -561,16 +678,23 @@ def _time_training_step(argv=None):
     ap.add_argument("--width", type=int, default=256)
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--eager", action="store_true", help="launch step by step instead of one CUDA graph per step")
     a = ap.parse_args(argv)
     net = UNet(batch=a.batch, height=a.height, width=a.width, seed=0)
     g = torch.Generator().manual_seed(0)
     planes = torch.rand((a.batch, IN_CH, a.height, a.width), generator=g).cuda()
     target = torch.randn((a.batch, OUT_CH, a.height, a.width), generator=g).cuda()
 
-    def step():
-        net.forward(planes)
-        net.loss_backward(target, [1.0, 1.0, 1.0], sync=False)
-        net.adam(1e-3)
+    if a.eager:
+        def step():
+            net.forward(planes)
+            net.loss_backward(target, [1.0, 1.0, 1.0], sync=False)
+            net.adam(1e-3)
+    else:
+        net.make_train_graph([1.0, 1.0, 1.0], [1e-3])
+
+        def step():
+            net.replay_train_step(planes, target)
 
     for _ in range(a.warmup):
         step()
@@ -582,7 +706,8 @@ def _time_training_step(argv=None):
     e1.record()
     torch.cuda.synchronize()
     net.check_tensor_cores()
-    print(f"U-Net training step, batch {a.batch} of {a.height}x{a.width}: "
+    print(f"U-Net training step, batch {a.batch} of {a.height}x{a.width} "
+          f"({'step-by-step launches' if a.eager else 'one CUDA graph per step'}): "
           f"{e0.elapsed_time(e1) / max(1, a.steps):.3f} ms")
 
 

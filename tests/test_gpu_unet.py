@@ -209,6 +209,32 @@ def test_training_reduces_loss(env):
     assert losses[-1] < 0.2 * losses[0], (losses[0], losses[-1])
 
 
+def test_graph_training_equals_step_by_step(env):
+    """surrogate.train with one captured CUDA graph per step against the same
+    steps launched one by one (Adam's step count and learning rate read from
+    device memory in the graph). The weight and bias gradients sum over
+    pixels with FP32 atomics in no fixed order, so two runs of either kind
+    differ in the last bits, which Adam's division by sqrt(v) enlarges where
+    a gradient is near zero (biases): losses agree to 1e-5, weights to 1e-3
+    and biases to 5e-3 (relative L2)."""
+    t, surrogate, lib = env
+    g = t.Generator().manual_seed(5)
+    planes = t.rand((8, surrogate.IN_CH, 32, 256), generator=g).cuda()
+    targets = t.randn((8, surrogate.OUT_CH, 32, 256), generator=g).cuda()
+    nets, hist = [], []
+    for graph in (False, True):
+        net = surrogate.UNet(batch=4, height=32, width=256, seed=3)
+        hist.append(surrogate.train(net, planes, targets, epochs=3, lr=2e-3, seed=11, graph=graph))
+        net.check_tensor_cores()
+        nets.append(net)
+    assert hist[0][0] == pytest.approx(hist[1][0], rel=1e-6)  # the first step's loss precedes any update
+    assert hist[0] == pytest.approx(hist[1], rel=1e-5)
+    assert nets[0].step_count == nets[1].step_count == 6
+    for name in nets[0].params:
+        for k, bound in (("w", 1e-3), ("b", 5e-3)):
+            assert rel(nets[1].params[name][k].cpu(), nets[0].params[name][k].cpu()) < bound, (name, k)
+
+
 def test_warm_fields_kernel(env):
     """Decode, clamp, mask and per-domain mass rescale of the warm-start
     fields against the same steps in FP64 on the host."""
