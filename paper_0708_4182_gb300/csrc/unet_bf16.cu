@@ -198,8 +198,25 @@ __host__ __device__ constexpr int conv_ntile(int n) { return n % 128 == 0 ? 128 
 // y[b, p, co] = act(bias[co] + sum_{tap, k} B[co][k](tap) x[b, p + off(tap), k])
 // x: NHWC view (channels per pixel ct_in, K = 16 kc channels used), y: NHWC
 // view (ct_out per pixel), wt: packed weights (conv_pack_kernel), one CTA =
-// 128 pixels x NT channels of one image.
-template <int NT>
+// 128 pixels (4 rows x 32 columns) x NT channels of one image.
+//
+// K runs over (chunk group, tap): a ring slot holds CK chunks of 16 input
+// channels of one tap (A: 128 pixels x 16 channels per chunk, K-major; B:
+// NT x 16 weights per chunk) and gets CK MMAs. Warp roles as in the weight
+// gradient (wgrad_tc_kernel): warps 1-3 stage the slots with cp.async and
+// arrive on the slot's "full" mbarrier kConvLag steps later (after their own
+// copies landed and were fenced for the async proxy); one thread issues the
+// MMAs and commits them to the slot's "empty" mbarrier; no CTA-wide barrier
+// runs inside the K loop.
+constexpr int kConvStages = 4;   // operand ring depth
+constexpr int kConvLag = 2;      // K-steps between a producer's copies and its "full" arrival
+constexpr int kConvProducers = kTcThreads - 32;
+template <int NT, int CK> __host__ __device__ constexpr int conv_smem_needed()
+{
+    return kConvStages * CK * (128 * 16 * 2 + NT * 16 * 2) + 2 * kConvStages * 8 + 16;
+}
+
+template <int NT, int CK>
 __global__ void __launch_bounds__(kTcThreads) conv3x3_tc_kernel(const bf16* __restrict__ x, int ct_in, int kc,
                                                                 const bf16* __restrict__ wt,
                                                                 const float* __restrict__ bias,
@@ -208,22 +225,28 @@ __global__ void __launch_bounds__(kTcThreads) conv3x3_tc_kernel(const bf16* __re
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     static_assert(NT <= int(tmem_cols(NT)), "the accumulator must fit the allocation");
-    constexpr int kABytes = 128 * 16 * 2;  // 128 pixels x 16 channels
-    constexpr int kBBytes = NT * 16 * 2;   // NT channels x 16 channels
+    static_assert(kConvLag < kConvStages, "a producer arrives on a slot before it needs it again");
+    constexpr int kAChunk = 128 * 16 * 2;  // 128 pixels x 16 channels
+    constexpr int kBChunk = NT * 16 * 2;   // NT channels x 16 channels
+    constexpr int kABytes = CK * kAChunk, kBBytes = CK * kBChunk;
     unsigned char* sa = smem;
-    unsigned char* sb = smem + kStages * kABytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sb + kStages * kBBytes);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + kStages);
+    unsigned char* sb = smem + kConvStages * kABytes;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sb + kConvStages * kBBytes);
+    uint64_t* empty = full + kConvStages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(empty + kConvStages);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tiles_x = W / kTileCols;
     const int ty0 = (blockIdx.x / tiles_x) * kTileRows, tx0 = (blockIdx.x % tiles_x) * kTileCols;
     const int nb = blockIdx.y, b = blockIdx.z;
-    const int KT = kc * 9;
+    const int KT = (kc / CK) * 9;
     const bf16* wblk = wt + size_t(nb) * kc * 9 * NT * 16;
 
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < kConvStages; ++s) {
+            mbar_init(&full[s], kConvProducers);
+            mbar_init(&empty[s], 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) tmem_alloc(tmem_slot, tmem_cols(NT));
@@ -231,55 +254,62 @@ __global__ void __launch_bounds__(kTcThreads) conv3x3_tc_kernel(const bf16* __re
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    bool alive = true;
 
-    auto load = [&](int it) {
-        const int s = it % kStages;
-        const int c = it / 9, t = it % 9;
-        const int dy = t / 3 - 1, dx = t % 3 - 1;
-        unsigned char* da = sa + s * kABytes;
+    if (warp == 0) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(NT, false, false);
+#pragma unroll 1
+            for (int it = 0; it < KT; ++it) {
+                const int s = it % kConvStages;
+                mbar_wait_alive(&full[s], uint32_t(it / kConvStages) & 1u, err, alive);
+                tc_fence_after();
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int q = tid + j * kTcThreads;  // 256 chunks of 16 B: pixel q/2, channel half q%2
-            const int p = q >> 1, h = q & 1;
-            const int yy = ty0 + (p >> 5) + dy, xx = wrapx(tx0 + (p & 31) + dx, W);
-            const bool ok = yy >= 0 && yy < H;
-            const bf16* src = ok ? x + (size_t(b * H + yy) * W + xx) * ct_in + c * 16 + h * 8 : x;
-            cp_async16_ca(da + (p >> 3) * 256 + h * 128 + (p & 7) * 16, src, ok ? 16u : 0u);
+                for (int j = 0; j < CK; ++j) {
+                    const uint64_t da = smem_desc(smem_u32(sa + s * kABytes + j * kAChunk), 128, 256);
+                    const uint64_t db = smem_desc(smem_u32(sb + s * kBBytes + j * kBChunk), 128, 256);
+                    mma_bf16(tmem, da, db, idesc, (it > 0 || j > 0) ? 1u : 0u);
+                }
+                mma_commit(&empty[s]);
+            }
         }
-        const bf16* wsrc = wblk + size_t(c * 9 + t) * NT * 16;
-        unsigned char* db = sb + s * kBBytes;
-        for (int q = tid; q < NT * 2; q += kTcThreads) cp_async16_cg(db + q * 16, wsrc + q * 8, 16u);
-    };
-
-    constexpr uint32_t idesc = idesc_bf16(NT, false, false);
+        __syncwarp();
+    } else {
+        const int pt = tid - 32;
 #pragma unroll 1
-    for (int it = 0; it < kStages - 1; ++it) {
-        if (it < KT) load(it);
-        cp_async_commit();
-    }
-#pragma unroll 1
-    for (int it = 0; it < KT; ++it) {
-        const int s = it % kStages;
-        cp_async_wait<kStages - 2>();
+        for (int it = 0; it < KT; ++it) {
+            const int s = it % kConvStages;
+            if (it >= kConvStages) mbar_wait_alive(&empty[s], uint32_t((it / kConvStages) - 1) & 1u, err, alive);
+            const int t = it % 9, cg = it / 9;
+            const int dy = t / 3 - 1, dx = t % 3 - 1;
+            unsigned char* da = sa + s * kABytes;
+            unsigned char* db = sb + s * kBBytes;
+            // A: CK chunks x 256 pieces of 16 B (pixel q / 2, channel half q % 2)
+            for (int q = pt; q < CK * 256; q += kConvProducers) {
+                const int j = q >> 8, p = (q & 255) >> 1, h = q & 1;
+                const int yy = ty0 + (p >> 5) + dy, xx = wrapx(tx0 + (p & 31) + dx, W);
+                const bool ok = yy >= 0 && yy < H;
+                const bf16* src = ok ? x + (size_t(b * H + yy) * W + xx) * ct_in + (cg * CK + j) * 16 + h * 8 : x;
+                cp_async16_ca(da + j * kAChunk + (p >> 3) * 256 + h * 128 + (p & 7) * 16, src, ok ? 16u : 0u);
+            }
+            // B: CK chunks x NT * 2 pieces of the packed (chunk, tap) blocks
+            for (int q = pt; q < CK * NT * 2; q += kConvProducers) {
+                const int j = q / (NT * 2), r = q % (NT * 2);
+                const bf16* wsrc = wblk + size_t((cg * CK + j) * 9 + t) * NT * 16;
+                cp_async16_cg(db + j * kBChunk + r * 16, wsrc + r * 8, 16u);
+            }
+            cp_async_commit();
+            if (it >= kConvLag) {
+                cp_async_wait<kConvLag>();
+                fence_proxy_async();
+                mbar_arrive(&full[(it - kConvLag) % kConvStages]);
+            }
+        }
+        cp_async_wait<0>();
         fence_proxy_async();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            const uint64_t da = smem_desc(smem_u32(sa + s * kABytes), 128, 256);
-            const uint64_t db = smem_desc(smem_u32(sb + s * kBBytes), 128, 256);
-            mma_bf16(tmem, da, db, idesc, it > 0 ? 1u : 0u);
-            mma_commit(&bars[s]);
-        }
-        const int nxt = it + kStages - 1;
-        if (nxt < KT) {
-            // the buffer of nxt was last read by the MMA of iteration nxt - kStages
-            if (nxt >= kStages) mbar_wait(&bars[nxt % kStages], uint32_t((nxt / kStages) - 1) & 1u, err);
-            load(nxt);
-        }
-        cp_async_commit();
+        for (int it = KT > kConvLag ? KT - kConvLag : 0; it < KT; ++it) mbar_arrive(&full[it % kConvStages]);
     }
-    cp_async_wait<0>();
-    mbar_wait(&bars[(KT - 1) % kStages], uint32_t((KT - 1) / kStages) & 1u, err);
+    mbar_wait_alive(&empty[(KT - 1) % kConvStages], uint32_t((KT - 1) / kConvStages) & 1u, err, alive);
     tc_fence_after();
 
     // epilogue: lane = pixel, 16 columns at a time
@@ -983,20 +1013,29 @@ int launch_conv_row(const void* x, int ct_in, int kc, const void* wt, const floa
     return status(cudaGetLastError());
 }
 
-template <int NT>
-int launch_conv(const void* x, int ct_in, int kc, const void* wt, const float* bias, void* y, int ct_out, int cout,
-                int n, int h, int wd, int relu, cudaStream_t st)
+template <int NT, int CK>
+int launch_conv_tile(const void* x, int ct_in, int kc, const void* wt, const float* bias, void* y, int ct_out,
+                     int cout, int n, int h, int wd, int relu, cudaStream_t st)
 {
-    if (wd % kRowPix == 0) return launch_conv_row<NT>(x, ct_in, kc, wt, bias, y, ct_out, cout, n, h, wd, relu, st);
-    constexpr int needed = kStages * (128 * 32 + NT * 32) + kStages * 8 + 16;
-    const int smem = smem_for_tmem(int(tmem_cols(NT)), needed);
-    auto k = conv3x3_tc_kernel<NT>;
+    const int smem = smem_for_tmem(int(tmem_cols(NT)), conv_smem_needed<NT, CK>());
+    auto k = conv3x3_tc_kernel<NT, CK>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return int(e);
     dim3 grid((h / kTileRows) * (wd / kTileCols), cout / NT, n);
     k<<<grid, kTcThreads, smem, st>>>((const bf16*)x, ct_in, kc, (const bf16*)wt, bias, (bf16*)y, ct_out, h, wd, relu,
                                       err_ptr());
     return status(cudaGetLastError());
+}
+
+template <int NT>
+int launch_conv(const void* x, int ct_in, int kc, const void* wt, const float* bias, void* y, int ct_out, int cout,
+                int n, int h, int wd, int relu, cudaStream_t st)
+{
+    if (wd % kRowPix == 0) return launch_conv_row<NT>(x, ct_in, kc, wt, bias, y, ct_out, cout, n, h, wd, relu, st);
+    // chunks of 16 channels per ring slot: 4, 2 or 1, dividing kc
+    if (kc % 4 == 0) return launch_conv_tile<NT, 4>(x, ct_in, kc, wt, bias, y, ct_out, cout, n, h, wd, relu, st);
+    if (kc % 2 == 0) return launch_conv_tile<NT, 2>(x, ct_in, kc, wt, bias, y, ct_out, cout, n, h, wd, relu, st);
+    return launch_conv_tile<NT, 1>(x, ct_in, kc, wt, bias, y, ct_out, cout, n, h, wd, relu, st);
 }
 
 template <int NT, int P>

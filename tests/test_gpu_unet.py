@@ -53,6 +53,8 @@ def nhwc_buffer(t, x_nchw, extra, off):
 
 @pytest.mark.parametrize("ci,co,h,w", [(3, 32, 64, 256), (96, 32, 32, 64), (32, 64, 32, 32), (256, 128, 8, 32),
                                        (384, 128, 8, 32), (64, 96, 8, 64),
+                                       # 1 and 3 chunks of 16 input channels (one chunk per ring slot)
+                                       (16, 32, 8, 64), (48, 64, 8, 32),
                                        # images >= 128 wide: the one-row halo kernel
                                        (64, 128, 8, 128), (32, 64, 4, 256), (96, 32, 8, 128), (192, 64, 4, 128)])
 def test_conv3x3_forward_backward(env, ci, co, h, w):
