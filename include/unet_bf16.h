@@ -84,13 +84,15 @@ int unet_head_bwd(const void *x, int ct, int ci, const void *w, const float *dy,
                   void *dx, int ct_dx, float *dw, float *db, void *stream);
 
 /* 2x2 average pooling of an (h, wd) image and its adjoint (accumulate != 0
- * adds into dx instead of overwriting); c channels of NHWC views. */
+ * adds into dx instead of overwriting); c channels of NHWC views. c, ctx,
+ * cty multiples of 8, views 16-byte aligned, h and wd even, fewer than 2^34
+ * elements; otherwise -1. */
 int unet_pool2_fwd(const void *x, int ctx, void *y, int cty, int c, int n, int h, int wd, void *stream);
 int unet_pool2_bwd(const void *dy, int cty, void *dx, int ctx, int c, int n, int h, int wd, int accumulate,
                    void *stream);
 
-/* Nearest 2x upsampling of an (h, wd) image and its adjoint (forward: c,
- * ctx, cty multiples of 8 and 16-byte aligned views). */
+/* Nearest 2x upsampling of an (h, wd) image and its adjoint (c, ctx, cty
+ * multiples of 8 and 16-byte aligned views; otherwise -1). */
 int unet_up2_fwd(const void *x, int ctx, void *y, int cty, int c, int n, int h, int wd, void *stream);
 int unet_up2_bwd(const void *dy, int cty, void *dx, int ctx, int c, int n, int h, int wd, void *stream);
 

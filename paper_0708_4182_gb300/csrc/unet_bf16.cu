@@ -38,7 +38,6 @@ using bf16 = __nv_bfloat16;
 
 constexpr int kT = 256;                      // threads of the SIMT kernels
 constexpr int kTcThreads = 128;              // threads of the tensor-core kernels (4 warps = 128 TMEM lanes)
-constexpr int kStages = 4;                   // operand ring depth of the tensor-core kernels
 constexpr uint32_t kWaitLimit = 1u << 18;    // try_wait rounds before giving up (about 1 s on a GB300)
 constexpr int kTileRows = 4, kTileCols = 32; // output pixels of one conv CTA (M = 128)
 constexpr int kSmemPerSm = 233472;           // shared memory of one SM (bytes)
@@ -512,7 +511,12 @@ __global__ void conv_pack_many_kernel(const long long* __restrict__ jobs)
 // pixels x NT channels (B, MN-major likewise: SBO = P + 2 pixels). Each
 // 16-pixel piece j of the step gives three MMAs, one per tap (dx = -1, 0, 1)
 // of the row: A starts 16 j pixels in, B 16 j + dx pixels in, into three
-// accumulators of NT columns (3 NT <= 512 tensor-memory columns).
+// accumulators of NT columns (3 NT <= 512 tensor-memory columns). With SW
+// (layers with more input than output channels) the operands swap roles:
+// the x halo row is A (M = 128 input channels) and dy is B (N = NT output
+// channels), so that the wider side fills the MMA's 128 rows; the shared
+// layouts and descriptors are the same, and the accumulators hold dw
+// transposed (lane = input channel).
 //
 // Warp roles: warps 1-3 stage the operands with 16-byte cp.async into a ring
 // of kWgStages slots; each producer thread waits for its own copies of a slot
@@ -526,12 +530,16 @@ constexpr int kWgStages = 4;   // operand ring depth of the weight gradient
 constexpr int kWgLag = 2;      // K-steps between a producer's copies and its "full" arrival
 constexpr int kWgProducers = kTcThreads - 32;
 template <int P> __host__ __device__ constexpr int wgrad_halo_pix() { return P + 2; }
-template <int NT, int P> __host__ __device__ constexpr int wgrad_smem_needed()
+// dy and x channels per CTA
+template <int NT, bool SW> __host__ __device__ constexpr int wgrad_co_tile() { return SW ? NT : 128; }
+template <int NT, bool SW> __host__ __device__ constexpr int wgrad_ci_tile() { return SW ? 128 : NT; }
+template <int NT, int P, bool SW> __host__ __device__ constexpr int wgrad_smem_needed()
 {
-    return kWgStages * (128 * P * 2 + (NT / 8) * wgrad_halo_pix<P>() * 16) + 2 * kWgStages * 8 + 16;
+    return kWgStages * (wgrad_co_tile<NT, SW>() * P * 2 + (wgrad_ci_tile<NT, SW>() / 8) * wgrad_halo_pix<P>() * 16) +
+           2 * kWgStages * 8 + 16;
 }
 
-template <int NT, int P>
+template <int NT, int P, bool SW>
 __global__ void __launch_bounds__(kTcThreads) wgrad_tc_kernel(const bf16* __restrict__ x, int ct_x, int ci,
                                                               const bf16* __restrict__ dy, int ct_dy, int co,
                                                               float* __restrict__ dw, int H, int W, int npix,
@@ -541,10 +549,10 @@ __global__ void __launch_bounds__(kTcThreads) wgrad_tc_kernel(const bf16* __rest
     static_assert(3 * NT <= 512, "three accumulators must fit the tensor memory");
     static_assert(P == 16 || P == 32 || P == 64, "K-step of 16, 32 or 64 pixels");
     static_assert(kWgLag < kWgStages, "a producer arrives on a slot before it needs it again");
-    constexpr int G = NT / 8;                              // 8-channel groups of B
+    constexpr int COT = wgrad_co_tile<NT, SW>(), CIT = wgrad_ci_tile<NT, SW>();
     constexpr int HP = wgrad_halo_pix<P>();                // halo row pixels
-    constexpr int kABytes = 128 * P * 2;                   // 128 output channels x P pixels
-    constexpr int kBBytes = G * HP * 16;                   // one halo row of B
+    constexpr int kABytes = COT * P * 2;                   // dy: COT output channels x P pixels
+    constexpr int kBBytes = (CIT / 8) * HP * 16;           // x: one halo row of CIT input channels
     constexpr uint32_t kCols = tmem_cols(3 * NT);
     unsigned char* sa = smem;
     unsigned char* sb = smem + kWgStages * kABytes;
@@ -553,10 +561,10 @@ __global__ void __launch_bounds__(kTcThreads) wgrad_tc_kernel(const bf16* __rest
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(empty + kWgStages);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int co0 = blockIdx.x * 128, ci0 = blockIdx.y * NT;
+    const int co0 = blockIdx.x * COT, ci0 = blockIdx.y * CIT;
     const int trow = blockIdx.z % 3;                       // taps 3 trow .. 3 trow + 2 (row offset trow - 1)
-    const int co_here = co - co0 < 128 ? co - co0 : 128;
-    const int ci_here = ci - ci0 < NT ? ci - ci0 : NT;
+    const int co_here = co - co0 < COT ? co - co0 : COT;
+    const int ci_here = ci - ci0 < CIT ? ci - ci0 : CIT;
     const int KT = npix / P;
 
     // rows of A beyond co_here and channel groups of B beyond ci_here are never loaded: zero them once
@@ -589,11 +597,14 @@ __global__ void __launch_bounds__(kTcThreads) wgrad_tc_kernel(const bf16* __rest
                 const uint32_t b0 = smem_u32(sb + s * kBBytes);
 #pragma unroll
                 for (int j = 0; j < P / 16; ++j) {
-                    const uint64_t da = smem_desc(a0 + j * 256, 128, P * 16);
+                    const uint64_t dd = smem_desc(a0 + j * 256, 128, P * 16);  // dy piece j
 #pragma unroll
                     for (int dx = 0; dx < 3; ++dx) {
-                        const uint64_t db = smem_desc(b0 + (16 * j + dx) * 16, 128, HP * 16);
-                        mma_bf16(tmem + dx * NT, da, db, idesc, (k > 0 || j > 0) ? 1u : 0u);
+                        const uint64_t dh = smem_desc(b0 + (16 * j + dx) * 16, 128, HP * 16);  // x, shifted dx
+                        if constexpr (SW)
+                            mma_bf16(tmem + dx * NT, dh, dd, idesc, (k > 0 || j > 0) ? 1u : 0u);
+                        else
+                            mma_bf16(tmem + dx * NT, dd, dh, idesc, (k > 0 || j > 0) ? 1u : 0u);
                     }
                 }
                 mma_commit(&empty[s]);
@@ -651,7 +662,8 @@ __global__ void __launch_bounds__(kTcThreads) wgrad_tc_kernel(const bf16* __rest
     mbar_wait_alive(&empty[(KT - 1) % kWgStages], uint32_t((KT - 1) / kWgStages) & 1u, err, alive);
     tc_fence_after();
 
-    const int m = warp * 32 + lane;  // output channel co0 + m
+    const int m = warp * 32 + lane;  // accumulator row: output channel co0 + m (input channel ci0 + m with SW)
+    const int m_here = SW ? ci_here : co_here, n_here = SW ? co_here : ci_here;
 #pragma unroll 1
     for (int dx = 0; dx < 3; ++dx) {
         const int tap = trow * 3 + dx;
@@ -659,10 +671,13 @@ __global__ void __launch_bounds__(kTcThreads) wgrad_tc_kernel(const bf16* __rest
         for (int n0 = 0; n0 < NT; n0 += 16) {
             float v[16];
             tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + dx * NT + n0, v);
-            if (m < co_here) {
+            if (m < m_here) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    if (n0 + j < ci_here) atomicAdd(&dw[(size_t(co0 + m) * ci + ci0 + n0 + j) * 9 + tap], v[j]);
+                for (int j = 0; j < 16; ++j) {
+                    if (n0 + j >= n_here) continue;
+                    const size_t o = SW ? (size_t(co0 + n0 + j) * ci + ci0 + m) : (size_t(co0 + m) * ci + ci0 + n0 + j);
+                    atomicAdd(&dw[o * 9 + tap], v[j]);
+                }
             }
         }
     }
@@ -758,33 +773,79 @@ __global__ void head_bwd_kernel(const bf16* __restrict__ x, int ct, int Ci, cons
 }
 
 // 2x2 average pooling of an (H, W) NHWC view and its adjoint
+// 8 BF16 values (16 bytes) <-> FP32
+__device__ __forceinline__ void unpack8(const uint4& q, float (&v)[8])
+{
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[2 * k] = __uint_as_float(w[k] << 16);
+        v[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+    }
+}
+__device__ __forceinline__ uint4 pack8(const float (&v)[8])
+{
+    uint32_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+        w[k] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// 2x2 average pooling of an (H, W) NHWC view and its adjoint. One thread per
+// coarse pixel and 8 channels (16-byte accesses): C, ctx, cty multiples of 8,
+// views 16-byte aligned (checked by the host entries).
 __global__ void pool2_fwd_kernel(const bf16* __restrict__ x, int ctx, bf16* __restrict__ y, int cty, int C, int H,
                                  int W, int B)
 {
-    const int h = H / 2, w = W / 2;
-    const long long n = (long long)B * h * w * C;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int c = int(i % C);
-        const long long pix = i / C;
-        const int xx = int(pix % w), yy = int((pix / w) % h), b = int(pix / ((long long)w * h));
-        const bf16* s = x + (size_t(b * H + 2 * yy) * W + 2 * xx) * ctx + c;
-        const float v = 0.25f * ((ld(s) + ld(s + ctx)) + (ld(s + size_t(W) * ctx) + ld(s + size_t(W + 1) * ctx)));
-        y[(size_t(b * h + yy) * w + xx) * cty + c] = __float2bfloat16_rn(v);
+    const int h = H / 2, w = W / 2, C8 = C / 8;
+    const int n = B * h * w * C8;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int c = (i % C8) * 8, pix = i / C8;
+        const int xx = pix % w, r = pix / w;  // r = b * h + yy
+        const bf16* s = x + (size_t(2 * r) * W + 2 * xx) * ctx + c;
+        float a[8], b2[8], c2[8], d[8];
+        unpack8(*reinterpret_cast<const uint4*>(s), a);
+        unpack8(*reinterpret_cast<const uint4*>(s + ctx), b2);
+        unpack8(*reinterpret_cast<const uint4*>(s + size_t(W) * ctx), c2);
+        unpack8(*reinterpret_cast<const uint4*>(s + size_t(W + 1) * ctx), d);
+        float o[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) o[k] = 0.25f * ((a[k] + b2[k]) + (c2[k] + d[k]));
+        *reinterpret_cast<uint4*>(y + size_t(pix) * cty + c) = pack8(o);
     }
 }
 
 __global__ void pool2_bwd_kernel(const bf16* __restrict__ dy, int cty, bf16* __restrict__ dx, int ctx, int C, int H,
                                  int W, int B, int accumulate)
 {
-    const long long n = (long long)B * H * W * C;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int c = int(i % C);
-        const long long pix = i / C;
-        const int xx = int(pix % W), yy = int((pix / W) % H), b = int(pix / ((long long)W * H));
-        float v = 0.25f * ld(dy + (size_t(b * (H / 2) + yy / 2) * (W / 2) + xx / 2) * cty + c);
-        bf16* o = dx + (size_t(b * H + yy) * W + xx) * ctx + c;
-        if (accumulate) v += ld(o);
-        *o = __float2bfloat16_rn(v);
+    const int h = H / 2, w = W / 2, C8 = C / 8;
+    const int n = B * h * w * C8;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int c = (i % C8) * 8, pix = i / C8;
+        const int xx = pix % w, r = pix / w;
+        float g[8];
+        unpack8(*reinterpret_cast<const uint4*>(dy + size_t(pix) * cty + c), g);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) g[k] *= 0.25f;
+        bf16* o = dx + (size_t(2 * r) * W + 2 * xx) * ctx + c;
+        const size_t offs[4] = {0, size_t(ctx), size_t(W) * ctx, size_t(W + 1) * ctx};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint4* dst = reinterpret_cast<uint4*>(o + offs[q]);
+            float v[8];
+            if (accumulate) {
+                unpack8(*dst, v);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) v[k] += g[k];
+            } else {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) v[k] = g[k];
+            }
+            *dst = pack8(v);
+        }
     }
 }
 
@@ -808,15 +869,21 @@ __global__ void up2_fwd_kernel(const bf16* __restrict__ x, int ctx, bf16* __rest
 __global__ void up2_bwd_kernel(const bf16* __restrict__ dy, int cty, bf16* __restrict__ dx, int ctx, int C, int h,
                                int w, int B)
 {
-    const int W = 2 * w;
-    const long long n = (long long)B * h * w * C;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int c = int(i % C);
-        const long long pix = i / C;
-        const int xx = int(pix % w), yy = int((pix / w) % h), b = int(pix / ((long long)w * h));
-        const bf16* s = dy + (size_t(b * 2 * h + 2 * yy) * W + 2 * xx) * cty + c;
-        const float v = (ld(s) + ld(s + cty)) + (ld(s + size_t(W) * cty) + ld(s + size_t(W + 1) * cty));
-        dx[(size_t(b * h + yy) * w + xx) * ctx + c] = __float2bfloat16_rn(v);
+    const int W = 2 * w, C8 = C / 8;
+    const int n = B * h * w * C8;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int c = (i % C8) * 8, pix = i / C8;
+        const int xx = pix % w, r = pix / w;
+        const bf16* s = dy + (size_t(2 * r) * W + 2 * xx) * cty + c;
+        float a[8], b2[8], c2[8], d[8];
+        unpack8(*reinterpret_cast<const uint4*>(s), a);
+        unpack8(*reinterpret_cast<const uint4*>(s + cty), b2);
+        unpack8(*reinterpret_cast<const uint4*>(s + size_t(W) * cty), c2);
+        unpack8(*reinterpret_cast<const uint4*>(s + size_t(W + 1) * cty), d);
+        float o[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) o[k] = (a[k] + b2[k]) + (c2[k] + d[k]);
+        *reinterpret_cast<uint4*>(dx + size_t(pix) * ctx + c) = pack8(o);
     }
 }
 
@@ -833,21 +900,40 @@ __global__ void relu_bwd_kernel(const bf16* __restrict__ y, int cty, bf16* __res
     const int G = C / 8, lanes = kT / G;
     const int grp = threadIdx.x % G, lane = threadIdx.x / G;
     float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (lane < lanes) {
-        for (long long p = (long long)blockIdx.x * lanes + lane; p < npix; p += (long long)gridDim.x * lanes) {
-            const uint4 yv = *reinterpret_cast<const uint4*>(y + p * cty + grp * 8);
-            uint4* gp = reinterpret_cast<uint4*>(dy + p * ctd + grp * 8);
-            uint4 gv = *gp;
-            const bf16* ye = reinterpret_cast<const bf16*>(&yv);
-            bf16* ge = reinterpret_cast<bf16*>(&gv);
+    // each pixel's 8 gradients: zero where y <= 0, else kept and summed
+    auto step = [&](const uint4& yv, uint4& gv) {
+        const bf16* ye = reinterpret_cast<const bf16*>(&yv);
+        bf16* ge = reinterpret_cast<bf16*>(&gv);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                if (__bfloat162float(ye[j]) > 0.f)
-                    s[j] += __bfloat162float(ge[j]);
-                else
-                    ge[j] = __float2bfloat16_rn(0.f);
+        for (int j = 0; j < 8; ++j) {
+            if (__bfloat162float(ye[j]) > 0.f)
+                s[j] += __bfloat162float(ge[j]);
+            else
+                ge[j] = __float2bfloat16_rn(0.f);
+        }
+    };
+    if (lane < lanes) {
+        // four pixels per round, their loads issued together
+        const long long stride = (long long)gridDim.x * lanes;
+        long long p = (long long)blockIdx.x * lanes + lane;
+        for (; p + 3 * stride < npix; p += 4 * stride) {
+            uint4 yv[4], gv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                yv[u] = *reinterpret_cast<const uint4*>(y + (p + u * stride) * cty + grp * 8);
+                gv[u] = *reinterpret_cast<const uint4*>(dy + (p + u * stride) * ctd + grp * 8);
             }
-            *gp = gv;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                step(yv[u], gv[u]);
+                *reinterpret_cast<uint4*>(dy + (p + u * stride) * ctd + grp * 8) = gv[u];
+            }
+        }
+        for (; p < npix; p += stride) {
+            const uint4 yv = *reinterpret_cast<const uint4*>(y + p * cty + grp * 8);
+            uint4 gv = *reinterpret_cast<const uint4*>(dy + p * ctd + grp * 8);
+            step(yv, gv);
+            *reinterpret_cast<uint4*>(dy + p * ctd + grp * 8) = gv;
         }
     }
     if (!db) return;
@@ -1038,29 +1124,30 @@ int launch_conv(const void* x, int ct_in, int kc, const void* wt, const float* b
     return launch_conv_tile<NT, 1>(x, ct_in, kc, wt, bias, y, ct_out, cout, n, h, wd, relu, st);
 }
 
-template <int NT, int P>
+template <int NT, int P, bool SW>
 int launch_wgrad_p(const void* x, int ct_x, int ci, const void* dy, int ct_dy, int co, float* dw, int h, int wd,
                    int npix, long long total, cudaStream_t st)
 {
-    const int smem = smem_for_tmem(int(tmem_cols(3 * NT)), wgrad_smem_needed<NT, P>());
-    auto k = wgrad_tc_kernel<NT, P>;
+    const int smem = smem_for_tmem(int(tmem_cols(3 * NT)), wgrad_smem_needed<NT, P, SW>());
+    auto k = wgrad_tc_kernel<NT, P, SW>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return int(e);
-    dim3 grid((co + 127) / 128, (ci + NT - 1) / NT, int(3 * (total / npix)));
+    constexpr int COT = wgrad_co_tile<NT, SW>(), CIT = wgrad_ci_tile<NT, SW>();
+    dim3 grid((co + COT - 1) / COT, (ci + CIT - 1) / CIT, int(3 * (total / npix)));
     k<<<grid, kTcThreads, smem, st>>>((const bf16*)x, ct_x, ci, (const bf16*)dy, ct_dy, co, dw, h, wd, npix,
                                       err_ptr());
     return status(cudaGetLastError());
 }
 
 // CTAs of the weight gradient that fit on one SM (shared and tensor memory)
-template <int NT, int P> int wgrad_ctas_per_sm()
+template <int NT, int P, bool SW> int wgrad_ctas_per_sm()
 {
-    const int smem = smem_for_tmem(int(tmem_cols(3 * NT)), wgrad_smem_needed<NT, P>());
+    const int smem = smem_for_tmem(int(tmem_cols(3 * NT)), wgrad_smem_needed<NT, P, SW>());
     const int by_smem = kSmemPerSm / (smem + 1024), by_tmem = 512 / int(tmem_cols(3 * NT));
     return by_smem < by_tmem ? (by_smem > 0 ? by_smem : 1) : by_tmem;
 }
 
-template <int NT, int P>
+template <int NT, int P, bool SW>
 int launch_wgrad_np(const void* x, int ct_x, int ci, const void* dy, int ct_dy, int co, float* dw, int n, int h,
                     int wd, cudaStream_t st)
 {
@@ -1071,23 +1158,24 @@ int launch_wgrad_np(const void* x, int ct_x, int ci, const void* dy, int ct_dy, 
     const long long total = (long long)n * h * wd;
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
-    const long long slots = (long long)(sms > 0 ? sms : 148) * wgrad_ctas_per_sm<NT, P>();
-    const long long tiles = 3LL * ((co + 127) / 128) * ((ci + NT - 1) / NT);
+    const long long slots = (long long)(sms > 0 ? sms : 148) * wgrad_ctas_per_sm<NT, P, SW>();
+    constexpr int COT = wgrad_co_tile<NT, SW>(), CIT = wgrad_ci_tile<NT, SW>();
+    const long long tiles = 3LL * ((co + COT - 1) / COT) * ((ci + CIT - 1) / CIT);
     int npix = 4096;
     while (npix > P && total % npix) npix >>= 1;
     while (npix > 8 * P && tiles * (total / npix) < slots / 2 && total % (npix / 2) == 0) npix >>= 1;
-    return launch_wgrad_p<NT, P>(x, ct_x, ci, dy, ct_dy, co, dw, h, wd, npix, total, st);
+    return launch_wgrad_p<NT, P, SW>(x, ct_x, ci, dy, ct_dy, co, dw, h, wd, npix, total, st);
 }
 
-template <int NT>
+template <int NT, bool SW>
 int launch_wgrad(const void* x, int ct_x, int ci, const void* dy, int ct_dy, int co, float* dw, int n, int h,
                  int wd, cudaStream_t st)
 {
     // K-step: the widest of 64, 32, 16 pixels that divides the row (every
     // step stays inside one image row)
-    if (wd % 64 == 0) return launch_wgrad_np<NT, 64>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
-    if (wd % 32 == 0) return launch_wgrad_np<NT, 32>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
-    return launch_wgrad_np<NT, 16>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
+    if (wd % 64 == 0) return launch_wgrad_np<NT, 64, SW>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
+    if (wd % 32 == 0) return launch_wgrad_np<NT, 32, SW>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
+    return launch_wgrad_np<NT, 16, SW>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
 }
 
 }  // namespace
@@ -1149,16 +1237,27 @@ int unet_conv3x3_bwd_weight(const void* x, int ct_x, int ci, const void* dy, int
         (reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(dy)) & 15)
         return -1;
     cudaStream_t st = (cudaStream_t)stream;
-    // input-channel tile: 128, 64, 32 or 16 (at most ci rounded up to 16)
+    // The MMA's 128 rows take the wider of the two channel counts: output
+    // channels (tiles of 128; input channels in N tiles of 128, 64, 32 or 16,
+    // at most ci rounded up to 16), or with more input than output channels
+    // (at most 128 of them) input channels (tiles of 128; output channels in
+    // one N tile of 32, 64 or 128).
     int rc;
-    if (ci > 64)
-        rc = launch_wgrad<128>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
+    if (ci > co && co <= 128) {
+        if (co <= 32)
+            rc = launch_wgrad<32, true>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
+        else if (co <= 64)
+            rc = launch_wgrad<64, true>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
+        else
+            rc = launch_wgrad<128, true>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
+    } else if (ci > 64)
+        rc = launch_wgrad<128, false>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
     else if (ci > 32)
-        rc = launch_wgrad<64>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
+        rc = launch_wgrad<64, false>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
     else if (ci > 16)
-        rc = launch_wgrad<32>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
+        rc = launch_wgrad<32, false>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
     else
-        rc = launch_wgrad<16>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
+        rc = launch_wgrad<16, false>(x, ct_x, ci, dy, ct_dy, co, dw, n, h, wd, st);
     if (rc || !db) return rc;
     const long long npix = (long long)n * h * wd;
     const int per = 1024;
@@ -1200,9 +1299,18 @@ int unet_head_bwd(const void* x, int ct, int ci, const void* w, const float* dy,
     return status(cudaGetLastError());
 }
 
+// the vector pooling/upsampling kernels: 8-channel groups, 16-byte aligned
+// views, 32-bit element counts
+static bool vec8_ok(const void* a, int cta, const void* b, int ctb, int c, long long elems)
+{
+    return c % 8 == 0 && cta % 8 == 0 && ctb % 8 == 0 && elems / 8 < (1LL << 31) &&
+           ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15) == 0;
+}
+
 int unet_pool2_fwd(const void* x, int ctx, void* y, int cty, int c, int n, int h, int wd, void* stream)
 {
-    pool2_fwd_kernel<<<blocks_for((long long)n * c * h * wd / 4), kT, 0, (cudaStream_t)stream>>>(
+    if (!vec8_ok(x, ctx, y, cty, c, (long long)n * c * h * wd) || h % 2 || wd % 2) return -1;
+    pool2_fwd_kernel<<<blocks_for((long long)n * c / 8 * h * wd / 4), kT, 0, (cudaStream_t)stream>>>(
         (const bf16*)x, ctx, (bf16*)y, cty, c, h, wd, n);
     return status(cudaGetLastError());
 }
@@ -1210,7 +1318,8 @@ int unet_pool2_fwd(const void* x, int ctx, void* y, int cty, int c, int n, int h
 int unet_pool2_bwd(const void* dy, int cty, void* dx, int ctx, int c, int n, int h, int wd, int accumulate,
                    void* stream)
 {
-    pool2_bwd_kernel<<<blocks_for((long long)n * c * h * wd), kT, 0, (cudaStream_t)stream>>>(
+    if (!vec8_ok(dy, cty, dx, ctx, c, (long long)n * c * h * wd) || h % 2 || wd % 2) return -1;
+    pool2_bwd_kernel<<<blocks_for((long long)n * c / 8 * h * wd / 4), kT, 0, (cudaStream_t)stream>>>(
         (const bf16*)dy, cty, (bf16*)dx, ctx, c, h, wd, n, accumulate);
     return status(cudaGetLastError());
 }
@@ -1226,7 +1335,8 @@ int unet_up2_fwd(const void* x, int ctx, void* y, int cty, int c, int n, int h, 
 
 int unet_up2_bwd(const void* dy, int cty, void* dx, int ctx, int c, int n, int h, int wd, void* stream)
 {
-    up2_bwd_kernel<<<blocks_for((long long)n * c * h * wd), kT, 0, (cudaStream_t)stream>>>(
+    if (!vec8_ok(dy, cty, dx, ctx, c, (long long)n * c * h * wd * 4)) return -1;
+    up2_bwd_kernel<<<blocks_for((long long)n * c / 8 * h * wd), kT, 0, (cudaStream_t)stream>>>(
         (const bf16*)dy, cty, (bf16*)dx, ctx, c, h, wd, n);
     return status(cudaGetLastError());
 }
@@ -1236,8 +1346,8 @@ int unet_relu_bwd(const void* y, int cty, void* dy, int ctd, int c, long npix, f
     if (c < 8 || c > kT || c % 8 || cty % 8 || ctd % 8 ||
         (reinterpret_cast<uintptr_t>(y) | reinterpret_cast<uintptr_t>(dy)) & 15)
         return -1;
-    long long blocks = (long long)npix * (c / 8) / (kT * 4) + 1;  // about 4 pixels per thread
-    if (blocks > 1024) blocks = 1024;
+    long long blocks = (long long)npix * (c / 8) / (kT * 4) + 1;  // about 4 pixels per thread: one round
+    if (blocks > 1184) blocks = 1184;                                 // 8 per SM
     relu_bwd_kernel<<<int(blocks), kT, 0, (cudaStream_t)stream>>>((const bf16*)y, cty, (bf16*)dy, ctd, c, npix, db);
     return status(cudaGetLastError());
 }

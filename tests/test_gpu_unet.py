@@ -124,6 +124,10 @@ def test_pool_upsample_head_relu(env):
     assert lib.unet_pool2_bwd(vp(ybn), c, vp(dx), c, c, n, h, w, 0, s) == 0
     lhs = (F.avg_pool2d(x, 2) * yb).sum().item()
     assert abs(lhs - (x * dx.permute(0, 3, 1, 2).double().cpu()).sum().item()) < 2e-2 * abs(lhs) + 1e-3
+    # accumulating form: adds the same adjoint onto what dx holds
+    before = dx.clone()
+    assert lib.unet_pool2_bwd(vp(ybn), c, vp(dx), c, c, n, h, w, 1, s) == 0
+    assert rel((dx.float() - before.float()).cpu(), before.float().cpu()) < 1e-2
     bb = t.randn((n, c, h, w), generator=g).to(t.bfloat16).double()
     bbn = nhwc_buffer(t, bb, 0, 0)
     da = t.zeros((n, h // 2, w // 2, c), dtype=t.bfloat16, device="cuda")
