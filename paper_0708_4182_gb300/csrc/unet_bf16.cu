@@ -56,26 +56,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
-// Bounded wait on one phase of an mbarrier; on timeout raise *err and return
-// (the caller goes on without the data, so nothing hangs).
-__device__ __forceinline__ void mbar_wait(uint64_t* bar, uint32_t parity, int* err)
-{
-    for (uint32_t i = 0; i < kWaitLimit; ++i) {
-        uint32_t ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(ok)
-            : "r"(smem_u32(bar)), "r"(parity)
-            : "memory");
-        if (ok) return;
-    }
-    atomicOr(err, 1);
-}
-
-// The same for a thread that waits many times: after its first timeout
-// (alive = false) it waits no more, so a kernel that lost a phase ends after
-// one time limit per thread rather than one per wait.
+// Bounded wait on one phase of an mbarrier. On timeout raise *err and set
+// alive = false: the thread waits no more (each later call returns at once),
+// so a kernel that lost a phase ends after one time limit per thread rather
+// than one per wait, and nothing hangs.
 __device__ __forceinline__ void mbar_wait_alive(uint64_t* bar, uint32_t parity, int* err, bool& alive)
 {
     if (!alive) return;
@@ -341,11 +325,13 @@ __global__ void __launch_bounds__(kTcThreads) conv3x3_tc_kernel(const bf16* __re
 // planes of 8 channels, LBO = the plane distance, SBO = 8 pixels), and the 9
 // taps are 9 MMAs whose A descriptors start at that halo shifted by dx pixels
 // (16 bytes each) and dy rows: the input crosses shared memory once per chunk
-// instead of once per tap. Two stages: the next chunk loads while the MMAs of
-// this one run.
+// instead of once per tap. Three ring slots of one chunk each, with the warp
+// roles of conv3x3_tc_kernel: the next chunks load while this one's MMAs run.
 constexpr int kRowPix = 128, kHaloPix = kRowPix + 2;
 constexpr int kHaloPlane = kHaloPix * 16;      // bytes of one 8-channel plane of one halo row
 constexpr int kHaloBytes = 3 * 2 * kHaloPlane; // 3 rows x 2 planes
+constexpr int kRowStages = 3;                  // ring slots (one chunk each)
+constexpr int kRowLag = 1;                     // chunks between a producer's copies and its "full" arrival
 
 template <int NT>
 __global__ void __launch_bounds__(kTcThreads) conv3x3_tc_row_kernel(const bf16* __restrict__ x, int ct_in, int kc,
@@ -356,12 +342,13 @@ __global__ void __launch_bounds__(kTcThreads) conv3x3_tc_row_kernel(const bf16* 
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     static_assert(NT <= int(tmem_cols(NT)), "the accumulator must fit the allocation");
-    constexpr int kRowStages = 2;
+    static_assert(kRowLag < kRowStages, "a producer arrives on a slot before it needs it again");
     constexpr int kBBytes = 9 * NT * 16 * 2;  // the 9 taps' weights of one chunk
     unsigned char* sa = smem;
     unsigned char* sb = smem + kRowStages * kHaloBytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sb + kRowStages * kBBytes);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + kRowStages);
+    uint64_t* full = reinterpret_cast<uint64_t*>(sb + kRowStages * kBBytes);
+    uint64_t* empty = full + kRowStages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(empty + kRowStages);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tiles_x = W / kRowPix;
@@ -370,7 +357,10 @@ __global__ void __launch_bounds__(kTcThreads) conv3x3_tc_row_kernel(const bf16* 
     const bf16* wblk = wt + size_t(nb) * kc * 9 * NT * 16;
 
     if (tid == 0) {
-        for (int s = 0; s < kRowStages; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < kRowStages; ++s) {
+            mbar_init(&full[s], kConvProducers);
+            mbar_init(&empty[s], 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) tmem_alloc(tmem_slot, tmem_cols(NT));
@@ -378,54 +368,59 @@ __global__ void __launch_bounds__(kTcThreads) conv3x3_tc_row_kernel(const bf16* 
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    bool alive = true;
 
-    auto load = [&](int c) {
-        const int s = c % kRowStages;
-        unsigned char* da = sa + s * kHaloBytes;
-        // 3 rows x 130 pixels x 2 planes of 16 bytes
-        for (int q = tid; q < 3 * kHaloPix * 2; q += kTcThreads) {
-            const int h = q & 1, pix = (q >> 1) % kHaloPix, r = (q >> 1) / kHaloPix;
-            const int yy = y0 + r - 1, xx = wrapx(x0 + pix - 1, W);
-            const bool ok = yy >= 0 && yy < H;
-            const bf16* src = ok ? x + (size_t(b * H + yy) * W + xx) * ct_in + c * 16 + h * 8 : x;
-            cp_async16_ca(da + (r * 2 + h) * kHaloPlane + pix * 16, src, ok ? 16u : 0u);
-        }
-        const bf16* wsrc = wblk + size_t(c) * 9 * NT * 16;
-        unsigned char* db = sb + s * kBBytes;
-        for (int q = tid; q < 9 * NT * 2; q += kTcThreads) cp_async16_cg(db + q * 16, wsrc + q * 8, 16u);
-    };
-
-    constexpr uint32_t idesc = idesc_bf16(NT, false, false);
-    load(0);
-    cp_async_commit();
+    if (warp == 0) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(NT, false, false);
 #pragma unroll 1
-    for (int c = 0; c < kc; ++c) {
-        const int s = c % kRowStages;
+            for (int c = 0; c < kc; ++c) {
+                const int s = c % kRowStages;
+                mbar_wait_alive(&full[s], uint32_t(c / kRowStages) & 1u, err, alive);
+                tc_fence_after();
+                const uint32_t a0 = smem_u32(sa + s * kHaloBytes);
+                const uint32_t b0 = smem_u32(sb + s * kBBytes);
+#pragma unroll
+                for (int t = 0; t < 9; ++t) {
+                    const int dy = t / 3, dx = t % 3;  // halo row and pixel shift of this tap
+                    const uint64_t da = smem_desc(a0 + dy * 2 * kHaloPlane + dx * 16, kHaloPlane, 128);
+                    const uint64_t db = smem_desc(b0 + t * NT * 32, 128, 256);
+                    mma_bf16(tmem, da, db, idesc, (c > 0 || t > 0) ? 1u : 0u);
+                }
+                mma_commit(&empty[s]);
+            }
+        }
+        __syncwarp();
+    } else {
+        const int pt = tid - 32;
+#pragma unroll 1
+        for (int c = 0; c < kc; ++c) {
+            const int s = c % kRowStages;
+            if (c >= kRowStages) mbar_wait_alive(&empty[s], uint32_t((c / kRowStages) - 1) & 1u, err, alive);
+            unsigned char* da = sa + s * kHaloBytes;
+            // 3 rows x 130 pixels x 2 planes of 16 bytes
+            for (int q = pt; q < 3 * kHaloPix * 2; q += kConvProducers) {
+                const int h = q & 1, pix = (q >> 1) % kHaloPix, r = (q >> 1) / kHaloPix;
+                const int yy = y0 + r - 1, xx = wrapx(x0 + pix - 1, W);
+                const bool ok = yy >= 0 && yy < H;
+                const bf16* src = ok ? x + (size_t(b * H + yy) * W + xx) * ct_in + c * 16 + h * 8 : x;
+                cp_async16_ca(da + (r * 2 + h) * kHaloPlane + pix * 16, src, ok ? 16u : 0u);
+            }
+            const bf16* wsrc = wblk + size_t(c) * 9 * NT * 16;
+            unsigned char* db = sb + s * kBBytes;
+            for (int q = pt; q < 9 * NT * 2; q += kConvProducers) cp_async16_cg(db + q * 16, wsrc + q * 8, 16u);
+            cp_async_commit();
+            if (c >= kRowLag) {
+                cp_async_wait<kRowLag>();
+                fence_proxy_async();
+                mbar_arrive(&full[(c - kRowLag) % kRowStages]);
+            }
+        }
         cp_async_wait<0>();
         fence_proxy_async();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            const uint32_t a0 = smem_u32(sa + s * kHaloBytes);
-            const uint32_t b0 = smem_u32(sb + s * kBBytes);
-#pragma unroll 1
-            for (int t = 0; t < 9; ++t) {
-                const int dy = t / 3, dx = t % 3;  // halo row and pixel shift of this tap
-                const uint64_t da = smem_desc(a0 + dy * 2 * kHaloPlane + dx * 16, kHaloPlane, 128);
-                const uint64_t db = smem_desc(b0 + t * NT * 32, 128, 256);
-                mma_bf16(tmem, da, db, idesc, (c > 0 || t > 0) ? 1u : 0u);
-            }
-            mma_commit(&bars[s]);
-        }
-        if (c + 1 < kc) {
-            // the buffer of chunk c + 1 was last read by the MMAs of chunk c - 1
-            if (c >= 1) mbar_wait(&bars[(c + 1) % kRowStages], uint32_t(((c + 1) / kRowStages) - 1) & 1u, err);
-            load(c + 1);
-        }
-        cp_async_commit();
+        for (int c = kc > kRowLag ? kc - kRowLag : 0; c < kc; ++c) mbar_arrive(&full[c % kRowStages]);
     }
-    cp_async_wait<0>();
-    mbar_wait(&bars[(kc - 1) % kRowStages], uint32_t((kc - 1) / kRowStages) & 1u, err);
+    mbar_wait_alive(&empty[(kc - 1) % kRowStages], uint32_t((kc - 1) / kRowStages) & 1u, err, alive);
     tc_fence_after();
 
     const int p = warp * 32 + lane;
@@ -1088,7 +1083,7 @@ template <int NT>
 int launch_conv_row(const void* x, int ct_in, int kc, const void* wt, const float* bias, void* y, int ct_out,
                     int cout, int n, int h, int wd, int relu, cudaStream_t st)
 {
-    constexpr int needed = 2 * (kHaloBytes + 9 * NT * 32) + 2 * 8 + 16;
+    constexpr int needed = kRowStages * (kHaloBytes + 9 * NT * 32) + 2 * kRowStages * 8 + 16;
     const int smem = smem_for_tmem(int(tmem_cols(NT)), needed);
     auto k = conv3x3_tc_row_kernel<NT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
