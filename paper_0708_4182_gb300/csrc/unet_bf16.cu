@@ -695,19 +695,59 @@ __global__ void bias_grad_kernel(const bf16* __restrict__ dy, int ct, int C, lon
     atomicAdd(&db[c], s);
 }
 
+// 8 BF16 values (16 bytes) <-> FP32
+__device__ __forceinline__ void unpack8(const uint4& q, float (&v)[8])
+{
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[2 * k] = __uint_as_float(w[k] << 16);
+        v[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+    }
+}
+__device__ __forceinline__ uint4 pack8(const float (&v)[8])
+{
+    uint32_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+        w[k] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
 // 1x1 head: y[b, o, p] = bias[o] + sum_i w[o][i] x[b, p, i] (x NHWC view, y FP32 NCHW)
 __global__ void head_fwd_kernel(const bf16* __restrict__ x, int ct, int Ci, const bf16* __restrict__ w,
                                 const float* __restrict__ bias, float* __restrict__ y, int Co, int HW, int B)
 {
+    // the Co x Ci weights (at most 8 x 64) once per block, read as broadcasts
+    __shared__ float ws[8 * 64];
+    for (int k = threadIdx.x; k < Co * Ci; k += blockDim.x) ws[k] = ld(w + k);
+    __syncthreads();
     const long long n = (long long)B * HW;
+    const bool vec = (Ci % 8 == 0) && (ct % 8 == 0) && ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const int b = int(i / HW), p = int(i % HW);
         const bf16* xp = x + i * ct;
-        for (int o = 0; o < Co; ++o) {
-            float s = bias[o];
-            for (int c = 0; c < Ci; ++c) s = fmaf(ld(w + o * Ci + c), ld(xp + c), s);
-            y[((long long)b * Co + o) * HW + p] = s;
+        float s[8];
+        for (int o = 0; o < Co; ++o) s[o] = bias[o];
+        if (vec) {
+            // the pixel's channels 8 at a time (16-byte loads), each used by every output
+            for (int c0 = 0; c0 < Ci; c0 += 8) {
+                float xv[8];
+                unpack8(*reinterpret_cast<const uint4*>(xp + c0), xv);
+                for (int o = 0; o < Co; ++o) {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) s[o] = fmaf(ws[o * Ci + c0 + k], xv[k], s[o]);
+                }
+            }
+        } else {
+            for (int c = 0; c < Ci; ++c) {
+                const float xv = ld(xp + c);
+                for (int o = 0; o < Co; ++o) s[o] = fmaf(ws[o * Ci + c], xv, s[o]);
+            }
         }
+        for (int o = 0; o < Co; ++o) y[((long long)b * Co + o) * HW + p] = s[o];
     }
 }
 
@@ -768,27 +808,6 @@ __global__ void head_bwd_kernel(const bf16* __restrict__ x, int ct, int Ci, cons
 }
 
 // 2x2 average pooling of an (H, W) NHWC view and its adjoint
-// 8 BF16 values (16 bytes) <-> FP32
-__device__ __forceinline__ void unpack8(const uint4& q, float (&v)[8])
-{
-    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        v[2 * k] = __uint_as_float(w[k] << 16);
-        v[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
-    }
-}
-__device__ __forceinline__ uint4 pack8(const float (&v)[8])
-{
-    uint32_t w[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
-        w[k] = *reinterpret_cast<const uint32_t*>(&h);
-    }
-    return make_uint4(w[0], w[1], w[2], w[3]);
-}
-
 // 2x2 average pooling of an (H, W) NHWC view and its adjoint. One thread per
 // coarse pixel and 8 channels (16-byte accesses): C, ctx, cty multiples of 8,
 // views 16-byte aligned (checked by the host entries).
@@ -932,15 +951,42 @@ __global__ void relu_bwd_kernel(const bf16* __restrict__ y, int cty, bf16* __res
         }
     }
     if (!db) return;
+    if (lane >= lanes) {
 #pragma unroll
-    for (int j = 0; j < 8; ++j) red[threadIdx.x][j] = lane < lanes ? s[j] : 0.f;
-    __syncthreads();
-    if (lane == 0) {
-        for (int k = 1; k < lanes; ++k)
+        for (int j = 0; j < 8; ++j) s[j] = 0.f;
+    }
+    // bias gradient: the partial sums of group grp over the block's pixels
+    const int tid = threadIdx.x;
+    if ((G & (G - 1)) == 0) {
+        // G divides 32: threads tid ^ m (m = G, 2G, .., 16) hold the same
+        // group, so shuffles sum a warp's lanes; then one value per warp and
+        // group goes through shared memory
+        for (int m = G; m < 32; m <<= 1) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) s[j] += red[k * G + grp][j];
+            for (int j = 0; j < 8; ++j) s[j] += __shfl_xor_sync(0xffffffffu, s[j], m);
+        }
+        const int wl = tid & 31, wp = tid >> 5;
+        if (wl < G) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) atomicAdd(&db[grp * 8 + j], s[j]);
+            for (int j = 0; j < 8; ++j) red[wp * G + wl][j] = s[j];
+        }
+        __syncthreads();
+        if (tid < C) {
+            const int g = tid / 8, j = tid % 8;
+            float t = 0.f;
+            for (int w = 0; w < kT / 32; ++w) t += red[w * G + g][j];
+            atomicAdd(&db[g * 8 + j], t);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) red[tid][j] = s[j];
+        __syncthreads();
+        if (tid < C) {
+            const int g = tid / 8, j = tid % 8;
+            float t = 0.f;
+            for (int k = 0; k < lanes; ++k) t += red[k * G + g][j];
+            atomicAdd(&db[g * 8 + j], t);
+        }
     }
 }
 
@@ -1279,7 +1325,7 @@ int unet_tc_error(void* stream, int reset)
 int unet_head_fwd(const void* x, int ct, int ci, const void* w, const float* bias, float* y, int co, int n, int hw,
                   void* stream)
 {
-    if (co > 8 || ci > 64) return -1;
+    if (co < 1 || co > 8 || ci < 1 || ci > 64) return -1;
     head_fwd_kernel<<<blocks_for((long long)n * hw), kT, 0, (cudaStream_t)stream>>>((const bf16*)x, ct, ci,
                                                                                    (const bf16*)w, bias, y, co, hw, n);
     return status(cudaGetLastError());
@@ -1289,7 +1335,11 @@ int unet_head_bwd(const void* x, int ct, int ci, const void* w, const float* dy,
                   int ct_dx, float* dw, float* db, void* stream)
 {
     if (co != 3 || ci < 1 || ci > kT) return -1;
-    head_bwd_kernel<3><<<blocks_for((long long)n * hw * ci) / 4 + 1, kT, 0, (cudaStream_t)stream>>>(
+    // at most 8 blocks per SM: each block adds its partial sums into the same
+    // 3 (ci + 1) addresses of dw and db
+    long long blocks = (long long)n * hw * ci / (kT * 4) + 1;
+    if (blocks > 1184) blocks = 1184;
+    head_bwd_kernel<3><<<int(blocks), kT, 0, (cudaStream_t)stream>>>(
         (const bf16*)x, ct, ci, (const bf16*)w, dy, hw, n, (bf16*)dx, ct_dx, dw, db);
     return status(cudaGetLastError());
 }

@@ -164,6 +164,24 @@ def test_pool_upsample_head_relu(env):
     assert rel(dbh.cpu() - 0.25, brh.grad) < 1e-4
 
 
+@pytest.mark.parametrize("c", [32, 96, 256])
+def test_relu_backward_and_bias_gradient(env, c):
+    """ReLU backward with the fused bias gradient over a 2 x 32 x 256 image:
+    8-channel groups per pixel of 4, 12 (not a power of two) and 32."""
+    t, surrogate, lib = env
+    g = t.Generator().manual_seed(c)
+    n, h, w = 2, 32, 256
+    s = ctypes.c_void_p(t.cuda.current_stream().cuda_stream)
+    yv = t.randn((n, c, h, w), generator=g).to(t.bfloat16).double()
+    gv = t.randn((n, c, h, w), generator=g).to(t.bfloat16).double()
+    yb, gb = nhwc_buffer(t, yv, 8, 0), nhwc_buffer(t, gv, 16, 8)
+    db = t.full((c,), 0.25, device="cuda")
+    assert lib.unet_relu_bwd(vp(yb), yb.shape[-1], vp(gb, 8), gb.shape[-1], c, n * h * w, vp(db), s) == 0
+    want = t.where(yv > 0, gv, t.zeros_like(gv))
+    assert t.equal(gb[..., 8:8 + c].permute(0, 3, 1, 2).double().cpu(), want)
+    assert rel(db.cpu() - 0.25, want.sum(dim=(0, 2, 3))) < 1e-5
+
+
 def test_network_matches_reference(env):
     """Whole forward pass, loss and every layer's gradients vs the FP64
     reference with the same (BF16-rounded) weights and inputs."""
