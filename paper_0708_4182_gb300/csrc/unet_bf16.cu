@@ -523,7 +523,8 @@ __global__ void conv_pack_many_kernel(const long long* __restrict__ jobs)
 // accumulators into dw (FP32 atomics; the grid splits the pixels).
 constexpr int kWgStages = 4;   // operand ring depth of the weight gradient
 constexpr int kWgLag = 2;      // K-steps between a producer's copies and its "full" arrival
-constexpr int kWgProducers = kTcThreads - 32;
+constexpr int kWgThreads = 256;                 // 8 warps: one issues the MMAs, seven stage operands
+constexpr int kWgProducers = kWgThreads - 32;
 template <int P> __host__ __device__ constexpr int wgrad_halo_pix() { return P + 2; }
 // dy and x channels per CTA
 template <int NT, bool SW> __host__ __device__ constexpr int wgrad_co_tile() { return SW ? NT : 128; }
@@ -535,7 +536,7 @@ template <int NT, int P, bool SW> __host__ __device__ constexpr int wgrad_smem_n
 }
 
 template <int NT, int P, bool SW>
-__global__ void __launch_bounds__(kTcThreads) wgrad_tc_kernel(const bf16* __restrict__ x, int ct_x, int ci,
+__global__ void __launch_bounds__(kWgThreads) wgrad_tc_kernel(const bf16* __restrict__ x, int ct_x, int ci,
                                                               const bf16* __restrict__ dy, int ct_dy, int co,
                                                               float* __restrict__ dw, int H, int W, int npix,
                                                               int* __restrict__ err)
@@ -563,7 +564,7 @@ __global__ void __launch_bounds__(kTcThreads) wgrad_tc_kernel(const bf16* __rest
     const int KT = npix / P;
 
     // rows of A beyond co_here and channel groups of B beyond ci_here are never loaded: zero them once
-    for (int i = tid; i < kWgStages * (kABytes + kBBytes) / 16; i += kTcThreads)
+    for (int i = tid; i < kWgStages * (kABytes + kBBytes) / 16; i += kWgThreads)
         reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
         for (int s = 0; s < kWgStages; ++s) {
@@ -657,15 +658,18 @@ __global__ void __launch_bounds__(kTcThreads) wgrad_tc_kernel(const bf16* __rest
     mbar_wait_alive(&empty[(KT - 1) % kWgStages], uint32_t((KT - 1) / kWgStages) & 1u, err, alive);
     tc_fence_after();
 
-    const int m = warp * 32 + lane;  // accumulator row: output channel co0 + m (input channel ci0 + m with SW)
+    // warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (its quadrant) and
+    // the accumulator columns of every (w / 4)-th 16-column block
+    const int quad = warp & 3, half = warp >> 2;
+    const int m = quad * 32 + lane;  // accumulator row: output channel co0 + m (input channel ci0 + m with SW)
     const int m_here = SW ? ci_here : co_here, n_here = SW ? co_here : ci_here;
 #pragma unroll 1
     for (int dx = 0; dx < 3; ++dx) {
         const int tap = trow * 3 + dx;
 #pragma unroll 1
-        for (int n0 = 0; n0 < NT; n0 += 16) {
+        for (int n0 = 16 * half; n0 < NT; n0 += 16 * (kWgThreads / 128)) {
             float v[16];
-            tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + dx * NT + n0, v);
+            tmem_ld16(tmem + (uint32_t(quad * 32) << 16) + dx * NT + n0, v);
             if (m < m_here) {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
@@ -1175,7 +1179,7 @@ int launch_wgrad_p(const void* x, int ct_x, int ci, const void* dy, int ct_dy, i
     if (e != cudaSuccess) return int(e);
     constexpr int COT = wgrad_co_tile<NT, SW>(), CIT = wgrad_ci_tile<NT, SW>();
     dim3 grid((co + COT - 1) / COT, (ci + CIT - 1) / CIT, int(3 * (total / npix)));
-    k<<<grid, kTcThreads, smem, st>>>((const bf16*)x, ct_x, ci, (const bf16*)dy, ct_dy, co, dw, h, wd, npix,
+    k<<<grid, kWgThreads, smem, st>>>((const bf16*)x, ct_x, ci, (const bf16*)dy, ct_dy, co, dw, h, wd, npix,
                                       err_ptr());
     return status(cudaGetLastError());
 }
