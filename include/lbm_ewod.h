@@ -181,6 +181,19 @@ lbm_status lbm_set_geometry(lbm_ctx *ctx, const uint8_t *solid, int on_device);
  * (LBM_ESTATE otherwise). */
 lbm_status lbm_set_field(lbm_ctx *ctx, int which, const double *data, int on_device);
 
+/* Set the state of a fluid at rest from an FP32 density rho = float[ny][nx]
+ * (host or device memory, on_device as for lbm_set_field; values on solid
+ * nodes are ignored). The state is the one LBM_RHO describes (f_a = w_a rho,
+ * Eq. 3 at u = 0, after streaming) with FP32 arithmetic and weights: the
+ * post-collision populations are f*_a(x) = w_a rho(s_a), s_a = x + e_a or, if
+ * that node is solid, x (the half-way bounce-back); the deviation forms store
+ * rho* = rho(x) + delta with delta = sum_a w_a (rho(s_a) - rho(x)) and
+ * d_a = w_a ((rho(s_a) - rho(x)) - delta). One memory-bound kernel on half the
+ * bytes of LBM_RHO's FP64 input; the populations differ from LBM_RHO's by
+ * FP32 rounding. No counterpart in the paper (a set-up path). Needs
+ * lbm_set_geometry first (LBM_ESTATE otherwise); LBM_EINVAL for NULL. */
+lbm_status lbm_set_density_f32(lbm_ctx *ctx, const float *rho, int on_device);
+
 /* Read the current state into out (layouts as for lbm_set_field).
  * LBM_RHO_U: rho and the velocity u = (sum_a f_a e_a + F/2)/rho, 0 on solids.
  * LBM_POPS:  post-streaming populations f_a(x, t), 0 on solids.

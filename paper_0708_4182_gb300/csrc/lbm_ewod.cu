@@ -121,17 +121,18 @@ __constant__ double kW[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
 
 __device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
-// Write the solid sentinel into every plane of both buffers at solid nodes
-// and zero at fluid nodes (pitch padding is left untouched).
+// Write the solid sentinel into every plane of both buffers at solid nodes.
+// Fluid nodes are left as they are: the state there is written by the next
+// lbm_set_field (the spare buffer's by the next step); pitch padding is left
+// untouched too.
 __global__ void geometry_kernel(const uint8_t* __restrict__ mask, float* A,
                                 float* B, Geom g)
 {
-    const long long n = (long long)g.nx * g.ny;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int y = int(i / g.nx), x = int(i % g.nx);
-        const float v = mask[i] ? __uint_as_float(kSolidBits) : 0.f;
-        const int o = y * g.pitch + x;
+    const int n = g.nx * g.ny;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (!mask[i]) continue;
+        const float v = __uint_as_float(kSolidBits);
+        const int o = (i / g.nx) * g.pitch + i % g.nx;
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
             A[a * g.plane + o] = v;
@@ -203,6 +204,68 @@ __global__ void feq_rest_kernel(const double* __restrict__ rho, const uint8_t* _
 #pragma unroll
         for (int a = 0; a < 9; ++a) f[a * g.plane + o] = solid ? __uint_as_float(kSolidBits) : float(kW[a] * r);
     }
+}
+
+// State of a fluid at rest from an FP32 density rho [y][x] (dense, nx per
+// row), directly in the storage form ST of `out`: f*_a(x) = w_a rho(s_a) with
+// s_a = x + e_a, or x where that node is solid (un-streaming of f_a = w_a rho
+// with the half-way bounce-back). Deviation forms: delta = sum_a w_a Delta_a,
+// Delta_a = rho(s_a) - rho(x); rho* = rho(x) + delta, d_a = w_a (Delta_a -
+// delta). FP32 arithmetic with the step kernel's weights. Solid nodes get the
+// sentinel (plane 0; every plane in plain storage).
+template <int ST>
+__global__ void rest_f32_kernel(const float* __restrict__ rho, const uint8_t* __restrict__ mask,
+                                float* __restrict__ out, Geom g)
+{
+    using T = typename StoreT<ST>::T;
+    constexpr float w1 = 1.f / 9.f, w2 = 1.f / 36.f, w0 = 4.f / 9.f;
+    const int n = g.nx * g.ny;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int y = i / g.nx, x = i % g.nx;
+        const int o = y * g.pitch + x;
+        if (mask[i]) {
+            if constexpr (ST == kF32) {
+#pragma unroll
+                for (int a = 0; a < 9; ++a) out[a * g.plane + o] = __uint_as_float(kSolidBits);
+            } else {
+                out[o] = __uint_as_float(kSolidBits);
+            }
+            continue;
+        }
+        const float r = rho[i];
+        float rs[9];
+        rs[0] = r;
+#pragma unroll
+        for (int a = 1; a < 9; ++a) {
+            const int xn = wrapi(x + kEx[a], g.nx), yn = wrapi(y + kEy[a], g.ny);
+            const int j = yn * g.nx + xn;
+            rs[a] = mask[j] ? r : rho[j];
+        }
+        if constexpr (ST == kF32) {
+#pragma unroll
+            for (int a = 0; a < 9; ++a) out[a * g.plane + o] = __fmul_rn(a == 0 ? w0 : (a <= 4 ? w1 : w2), rs[a]);
+        } else {
+            float dl[9];
+#pragma unroll
+            for (int a = 1; a < 9; ++a) dl[a] = __fsub_rn(rs[a], r);
+            const float delta = fmaf(w1, __fadd_rn(__fadd_rn(dl[1], dl[3]), __fadd_rn(dl[2], dl[4])),
+                                     __fmul_rn(w2, __fadd_rn(__fadd_rn(dl[5], dl[7]), __fadd_rn(dl[6], dl[8]))));
+            out[o] = __fadd_rn(r, delta);
+            T* od = reinterpret_cast<T*>(out + g.plane);
+#pragma unroll
+            for (int a = 1; a < 9; ++a)
+                od[dev_index<T>(size_t(o), a, size_t(g.plane))] =
+                    from_f<T>(__fmul_rn(a <= 4 ? w1 : w2, __fsub_rn(dl[a], delta)));
+        }
+    }
+}
+
+// plane p of buffer f <- the solid sentinel on solid nodes (other nodes untouched)
+__global__ void solid_plane_kernel(const uint8_t* __restrict__ mask, float* __restrict__ f, int p, Geom g)
+{
+    const int n = g.nx * g.ny;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        if (mask[i]) f[size_t(p) * g.plane + (i / g.nx) * g.pitch + i % g.nx] = __uint_as_float(kSolidBits);
 }
 
 // Model constants in FP64 for the force-corrected initial state.
@@ -1068,6 +1131,39 @@ lbm_status lbm_set_field(lbm_ctx* c, int which, const double* data, int on_devic
         if ((s = plain_to_storage(c))) return s;
     } else {
         return fail(c, LBM_EINVAL, "unknown field selector %d", which);
+    }
+    c->has_field = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_density_f32(lbm_ctx* c, const float* rho, int on_device)
+{
+    if (!c) return LBM_EINVAL;
+    if (!rho) return fail(c, LBM_EINVAL, "density is NULL");
+    if (!c->has_geometry) return fail(c, LBM_ESTATE, "lbm_set_geometry must come before lbm_set_density_f32");
+    const size_t n = size_t(c->g.nx) * c->g.ny;
+    lbm_status s;
+    const float* src = rho;
+    // a host density goes into the spare buffer's last plane (no form stores
+    // anything there that the set-up reads), restored to sentinels below
+    float* tmp = c->nxt + size_t(8) * c->g.plane;
+    if (!on_device) {
+        if ((s = check_cuda(c, cudaMemcpyAsync(tmp, rho, n * sizeof(float), cudaMemcpyHostToDevice, c->stream),
+                            "density upload")))
+            return s;
+        src = tmp;
+    }
+    const int b = aux_blocks((long long)n, c->sm_count);
+    switch (c->prm.storage) {
+    case LBM_FP32_DEV: rest_f32_kernel<kF32Dev><<<b, kAuxThreads, 0, c->stream>>>(src, c->mask, c->cur, c->g); break;
+    case LBM_FP16_DEV: rest_f32_kernel<kF16Dev><<<b, kAuxThreads, 0, c->stream>>>(src, c->mask, c->cur, c->g); break;
+    case LBM_BF16_DEV: rest_f32_kernel<kBF16Dev><<<b, kAuxThreads, 0, c->stream>>>(src, c->mask, c->cur, c->g); break;
+    default: rest_f32_kernel<kF32><<<b, kAuxThreads, 0, c->stream>>>(src, c->mask, c->cur, c->g); break;
+    }
+    if ((s = check_launch(c, "rest state kernel launch"))) return s;
+    if (!on_device) {
+        solid_plane_kernel<<<b, kAuxThreads, 0, c->stream>>>(c->mask, c->nxt, 8, c->g);
+        if ((s = check_launch(c, "sentinel kernel launch"))) return s;
     }
     c->has_field = true;
     return LBM_OK;

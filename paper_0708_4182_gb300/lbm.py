@@ -6,7 +6,7 @@ missing; there is no CPU fallback. PyTorch is used for device memory (the
 workspace tensor) and for the CUDA stream the context enqueues on.
 
 Low level: ``lbm_workspace_bytes``, ``lbm_create``, ``lbm_set_geometry``,
-``lbm_set_field``, ``lbm_get_field``, ``lbm_step``, ``lbm_observables``,
+``lbm_set_field``, ``lbm_set_density_f32``, ``lbm_get_field``, ``lbm_step``, ``lbm_observables``,
 ``lbm_obs_latest``, ``lbm_obs_latest_async``, ``lbm_time``, ``lbm_last_error``, ``lbm_status_string``,
 ``lbm_destroy``; each raises ``LbmError`` on a non-zero status.
 High level: ``Lattice`` owns a workspace tensor and a context.
@@ -85,6 +85,7 @@ def load():
             "lbm_create": (ctypes.c_int, [P, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]),
             "lbm_set_geometry": (ctypes.c_int, [vp, vp, ctypes.c_int]),
             "lbm_set_field": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int]),
+            "lbm_set_density_f32": (ctypes.c_int, [vp, vp, ctypes.c_int]),
             "lbm_get_field": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int]),
             "lbm_step": (ctypes.c_int, [vp, ctypes.c_int64]),
             "lbm_observables": (ctypes.c_int, [vp, O]),
@@ -143,6 +144,10 @@ def lbm_set_geometry(ctx, solid_ptr: int, on_device: bool):
 
 def lbm_set_field(ctx, which: int, data_ptr: int, on_device: bool):
     _check(ctx, load().lbm_set_field(ctx, which, ctypes.c_void_p(data_ptr), int(on_device)))
+
+
+def lbm_set_density_f32(ctx, rho_ptr: int, on_device: bool):
+    _check(ctx, load().lbm_set_density_f32(ctx, ctypes.c_void_p(rho_ptr), int(on_device)))
 
 
 def lbm_get_field(ctx, which: int, out_ptr: int, on_device: bool):
@@ -292,6 +297,22 @@ class Lattice:
             self._set(LBM_RHO, rho.reshape(1, self.ny, self.nx), 1)
         else:
             self._set(LBM_RHO, np.asarray(rho, np.float64).reshape(1, self.ny, self.nx), 1)
+
+    def set_density_f32(self, rho):
+        """A fluid at rest from an FP32 density [ny, nx] (numpy array or CUDA
+        tensor): the LBM_RHO state with FP32 set-up arithmetic
+        (lbm_set_density_f32)."""
+        if hasattr(rho, "is_cuda") and rho.is_cuda:
+            t = rho.to(dtype=__import__("torch").float32).contiguous()
+            if tuple(t.shape) != (self.ny, self.nx):
+                raise ValueError("bad density shape")
+            lbm_set_density_f32(self.ctx, t.data_ptr(), True)
+            self.stream.synchronize()
+        else:
+            a, p = _host_ptr(rho, np.float32)
+            if a.shape != (self.ny, self.nx):
+                raise ValueError(f"density shape {a.shape} != {(self.ny, self.nx)}")
+            lbm_set_density_f32(self.ctx, p, False)
 
     def set_rho_u_field(self, data, physical=False):
         """(rho, u_x, u_y) as one [3, ny, nx] array or device tensor (FP64)."""

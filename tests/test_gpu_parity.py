@@ -498,6 +498,42 @@ def test_density_only_setup_equals_rest_equilibrium(lbm, storage):
     assert np.array_equal(a.populations(), b.populations())
 
 
+@pytest.mark.parametrize("storage", [0, 1, 2, 3])
+def test_fp32_density_setup(lbm, storage):
+    """lbm_set_density_f32 (FP32 set-up arithmetic) against LBM_RHO (FP64,
+    rounded once) on a rough channel with a droplet row: the populations
+    agree to FP32 rounding (relative to the field's maximum: 2e-7 in the
+    32-bit forms; the 16-bit forms round both to the same deviations but
+    for the rare value on a rounding boundary), from host and device input,
+    and 40 steps from it stay within the oracle tolerances."""
+    import torch
+    w = wl.droplet_row_channel(nx=512, ny=96, amp=6, seed=2, radius=12.0, pitch=96, body_fx=1e-5, f_elec=0.125)
+    rho32 = np.where(w.mask == 0, w.rho, 0.0).astype(np.float32)
+    ref = lbm.Lattice(w.nx, w.ny, **dict(w.params, storage=storage))
+    ref.set_geometry(w.mask)
+    ref.set_rho(rho32.astype(np.float64))
+    fr = ref.populations()
+    fl = w.mask == 0
+    scale = np.abs(fr[:, fl]).max()
+    for device in (False, True):
+        lat = lbm.Lattice(w.nx, w.ny, **dict(w.params, storage=storage))
+        lat.set_geometry(w.mask)
+        lat.set_density_f32(torch.from_numpy(rho32).cuda() if device else rho32)
+        f = lat.populations()
+        err = np.abs(f - fr)[:, fl].max() / scale
+        bound = 2e-7 if storage < 2 else 2e-3
+        assert err <= bound, (device, err)
+        assert np.all(f[:, ~fl] == 0)
+        if not device:
+            lat.step(40)
+            p = oracle.Params(w.nx, w.ny, **w.params)
+            f_ref = oracle.step(p, w.mask, oracle.equilibrium(p, w.mask, rho32.astype(np.float64), 0, 0), 40)
+            if storage < 2:
+                assert_pops(lat.populations(), f_ref, w.mask)
+        lat.close()
+    ref.close()
+
+
 def test_unit_normal_reading_matches_oracle(lbm):
     """The electric force along the unit face normal (LBM_NORMAL_UNIT) on a
     rough channel full of liquid, so that conductive liquid fills the
