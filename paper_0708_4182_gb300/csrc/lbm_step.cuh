@@ -331,6 +331,34 @@ __device__ __forceinline__ void set_lane(float2& v, int k, float a)
     if (k == 0) v.x = a; else v.y = a;
 }
 
+// The compensated sum of Acc in both lanes at once (lane k accumulates the
+// values of its lane, operation for operation as Acc::add).
+struct Acc2 {
+    float2 s = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
+    __device__ __forceinline__ void add(float2 v)
+    {
+        const float2 t = add2(s, v);
+        const float2 bp = sub2(t, s);
+        c = add2(c, add2(sub2(s, sub2(t, bp)), sub2(v, bp)));
+        s = t;
+    }
+    __device__ __forceinline__ double value() const
+    {
+        return ((double)s.x + (double)c.x) + ((double)s.y + (double)c.y);
+    }
+};
+
+// Observables state of the pair layout: lane k sums the nodes of lane k.
+struct ObsAcc2 {
+    Acc2 mass, q, px, py;
+    float umax2 = 0.f, rmin = __builtin_huge_valf();  // +inf
+    unsigned bad = 0;
+    __device__ __forceinline__ double value(int k) const
+    {
+        return k == 0 ? mass.value() : k == 1 ? q.value() : k == 2 ? px.value() : py.value();
+    }
+};
+
 // ------------------------------------------------------------------ node math
 
 // Pull node (column c of the staged rows) from the three ring rows holding
@@ -410,6 +438,11 @@ struct ObsAcc {
     Acc mass, q, px, py;
     float umax2 = 0.f, rmin = __builtin_huge_valf();  // +inf
     unsigned bad = 0;
+    // sum q (0 mass, 1 flux, 2 x momentum, 3 y momentum)
+    __device__ __forceinline__ double value(int k) const
+    {
+        return k == 0 ? mass.value() : k == 1 ? q.value() : k == 2 ? px.value() : py.value();
+    }
 };
 
 // Eq. 6 and the electric force of a node with solid pull sources (flags sb,
@@ -953,17 +986,44 @@ __device__ __forceinline__ void node_force2(float2 rho, const uint32_t (&sb)[2],
     Fy_out = fma2(rho, splat(p.bfy), Fy);
 }
 
-// Observables / fields epilogue of the lanes that are collided fluid nodes.
+// Observables / fields epilogue of the lanes that are collided fluid nodes:
+// node_observe lane for lane, the velocities and sums on the paired
+// instructions (a lane that is not collided, or not finite, adds zero).
 template <int MODE>
 __device__ __forceinline__ void observe_pair(const float2& rho, const float2& rinv, const float2& jx,
                                              const float2& jy, const float2& Fx, const float2& Fy, const bool (&use)[2],
-                                             const Geom& g, double* __restrict__ fields, int x, int r, ObsAcc& acc)
+                                             const Geom& g, double* __restrict__ fields, int x, int r, ObsAcc2& acc)
 {
+    if constexpr (MODE == kFields) {
+        ObsAcc unused;
 #pragma unroll
-    for (int k = 0; k < 2; ++k)
-        if (use[k])
-            node_observe<MODE>(lane_of(rho, k), lane_of(rinv, k), lane_of(jx, k), lane_of(jy, k), lane_of(Fx, k),
-                               lane_of(Fy, k), g, fields, x + k, r, acc);
+        for (int k = 0; k < 2; ++k)
+            if (use[k])
+                node_observe<MODE>(lane_of(rho, k), lane_of(rinv, k), lane_of(jx, k), lane_of(jy, k),
+                                   lane_of(Fx, k), lane_of(Fy, k), g, fields, x + k, r, unused);
+    } else {
+        // physical velocity u = (rho u + F/2)/rho
+        const float2 mx = fma2(splat(0.5f), Fx, jx), my = fma2(splat(0.5f), Fy, jy);
+        const float2 nrho = make_float2(-rho.x, -rho.y);
+        const float2 vx = div2(mx, nrho, rinv), vy = div2(my, nrho, rinv);
+        const float2 u2 = fma2(vx, vx, mul2(vy, vy));
+        bool ok[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            // a NaN or infinity in any of the three makes the sum non-finite
+            ok[k] = use[k] && isfinite((lane_of(rho, k) + lane_of(vx, k)) + lane_of(vy, k));
+            if (use[k] && !ok[k]) ++acc.bad;
+            if (ok[k]) {
+                acc.umax2 = fmaxf(acc.umax2, lane_of(u2, k));
+                acc.rmin = fminf(acc.rmin, lane_of(rho, k));
+            }
+        }
+        auto sel = [&ok](float2 v) { return make_float2(ok[0] ? v.x : 0.f, ok[1] ? v.y : 0.f); };
+        acc.mass.add(sel(rho));
+        acc.q.add(sel(vx));
+        acc.px.add(sel(mx));
+        acc.py.add(sel(my));
+    }
 }
 
 // Shifted velocity (Eq. 10) of the pair from its force; rinv = 1/rho (approx).
@@ -983,7 +1043,7 @@ template <int MODE, bool T1>
 __device__ __forceinline__ void collide_pair(const Pulled2& n, const bool (&col)[2], const float* pm, const float* pc,
                                              const float* pp, int t, const Phys& p, const Geom& g,
                                              float* __restrict__ fout, double* __restrict__ fields, int x, int r,
-                                             ObsAcc& acc)
+                                             ObsAcc2& acc)
 {
     float2 Fx, Fy;
     node_force2(n.rho, n.sb, pm, pc, pp, t, p, Fx, Fy);
@@ -1034,7 +1094,7 @@ __device__ __forceinline__ void collide_dev_pair(const PulledDev2& n, const bool
                                                  const float* pc, const float* pp, int t, const Phys& p,
                                                  const Geom& g, float* __restrict__ fout0,
                                                  float* __restrict__ foutd, double* __restrict__ fields, int x,
-                                                 int r, ObsAcc& acc)
+                                                 int r, ObsAcc2& acc)
 {
     float2 Fx, Fy;
     node_force2(n.rho, n.sb, pm, pc, pp, t, p, Fx, Fy);
@@ -1325,7 +1385,7 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
     const int c = PR ? 2 * t + 1 + o : t + 1 + o;                  // staged column (of lane A)
     const int x = PR ? x0 + 2 * t : x0 - P + t;
     const int tr = PR ? 2 * t + 2 : t + 1 - P;                     // psi ring column (of lane A)
-    ObsAcc acc;
+    std::conditional_t<PR, ObsAcc2, ObsAcc> acc;
     bool ok = true;
     // prologue: the two oldest staged rows (y0-2, y0-1) must be present
     // (a segment stages at least 5 rows)
@@ -1485,7 +1545,7 @@ __device__ __forceinline__ void run_tile(const float* __restrict__ fin, float* _
         __shared__ double red_d[4][NCW];
         __shared__ float red_f[2][NCW];
         __shared__ unsigned red_u[NCW];
-        double d[4] = {acc.mass.value(), acc.q.value(), acc.px.value(), acc.py.value()};
+        double d[4] = {acc.value(0), acc.value(1), acc.value(2), acc.value(3)};
         float umax2 = acc.umax2, rmin = acc.rmin;
         unsigned bad = acc.bad;
 #pragma unroll
