@@ -72,15 +72,18 @@ enum Storage { kF32 = 0, kF32Dev = 1, kF16Dev = 2, kBF16Dev = 3 };
 __host__ __device__ constexpr bool is16(int st) { return st == kF16Dev || st == kBF16Dev; }
 
 // Staging ring depth (rows) and resident CTAs per SM the launch bounds aim
-// at. The 16-bit forms and the one-node layout of the 32-bit forms (288
-// threads): 6 and 3. The pair layout of the 32-bit forms (160 threads, a pair
-// of nodes per thread): LBM_STAGES_F32 / LBM_CTAS_F32 and LBM_STAGES_F32DEV /
-// LBM_CTAS_F32DEV for the tau = 1 instances, whose register needs are lower;
-// the tau != 1 instances aim at 3.
-// Shared memory and registers must allow that many CTAs. Measured at
-// 16384x4096 (GLUPS, FP32 / FP32 deviations / batch FP32 / batch FP32
-// deviations): 6 stages x 3 CTAs 89.4 / 85.9 / 80.5 / 72.8; FP32 4 x 5 and
-// deviations 5 x 4: 89.8 / 89.7 / 81.4 / 55.6 (spilling).
+// at. The one-node layout of the 32-bit forms (288 threads): 6 and 3. The
+// 16-bit forms (288 threads): LBM_STAGES_16 / LBM_CTAS_16, 6 and 3. The pair
+// layout of the 32-bit forms (160 threads, a pair of nodes per thread):
+// LBM_STAGES_F32 / LBM_CTAS_F32 and LBM_STAGES_F32DEV / LBM_CTAS_F32DEV for
+// the tau = 1 instances, whose register needs are lower; the tau != 1
+// instances aim at 3. Shared memory and registers must allow that many CTAs.
+// Measured at 16384x4096 (GLUPS, FP32 / FP32 deviations / batch FP32 / batch
+// FP32 deviations): pairs at 6 stages x 3 CTAs 89.4 / 85.9 / 80.5 / 72.8;
+// FP32 4 x 5 and deviations 5 x 4: 89.8 / 89.7 / 81.4 / 75.7 (the batch
+// kernel keeps its domain parameters in shared memory, which keeps it from
+// spilling at 4 CTAs). FP16 deviations at 4, 6 and 8 stages: 107.8 / 110.6
+// / 104.4; at 2 or 4 CTAs per SM: 84.3 / 105.9.
 #ifndef LBM_STAGES_F32
 #define LBM_STAGES_F32 4
 #endif
