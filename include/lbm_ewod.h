@@ -330,7 +330,7 @@ lbm_status lbm_batch_autotune_grid(lbm_batch *b, const int32_t *rows, int32_t nr
  * its last observables. LBM_ENAN if some domain became non-finite, else
  * LBM_ENOTCONV if some active domain did not converge within max_steps.
  * With an explicit tile height (lbm_batch_set_tile_rows or the autotuners),
- * the height is halved, down to 8 rows, whenever the domains still running
+ * the height is halved, down to 4 rows, whenever the domains still running
  * give fewer than two waves of tiles for the persistent grid (a tiling
  * change leaves every population bit for bit as it was). The caller's
  * active set and tile height are restored on return. */

@@ -1975,7 +1975,11 @@ lbm_status lbm_batch_run_to_steady(lbm_batch* b, double rel_tol, int64_t check_e
     auto retile = [&]() {
         if (b->tile_rows <= 0) return;  // each domain's own height (already sized for it alone)
         int r = b->tile_rows;
-        while (r > 8 && active_tiles(b, r) < 2 * slots) r = r / 2 < 8 ? 8 : r / 2;
+        // down to 4 rows: with fewer than two waves of tiles a step is bound by
+        // the latency of one tile's row pipeline, not by the re-staged halo
+        // rows (measured on 32 small channels: 1.04 s to steady at 8 rows,
+        // 0.82 s at 4)
+        while (r > 4 && active_tiles(b, r) < 2 * slots) r = r / 2 < 4 ? 4 : r / 2;
         if (r != b->tile_rows) {
             b->tile_rows = r;
             b->tiles_dirty = true;
