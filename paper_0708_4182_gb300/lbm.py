@@ -264,6 +264,7 @@ class Lattice:
             if a.shape != (self.ny, self.nx):
                 raise ValueError(f"mask shape {a.shape} != {(self.ny, self.nx)}")
             lbm_set_geometry(self.ctx, p, False)
+            self.stream.synchronize()  # page-locked input is read asynchronously
 
     def _set(self, which, data, comps):
         if hasattr(data, "is_cuda") and data.is_cuda:
@@ -277,6 +278,7 @@ class Lattice:
             if a.shape != (comps, self.ny, self.nx):
                 raise ValueError(f"field shape {a.shape} != {(comps, self.ny, self.nx)}")
             lbm_set_field(self.ctx, which, p, False)
+            self.stream.synchronize()
 
     def set_rho_u(self, rho, ux=0.0, uy=0.0, physical=False):
         """State f = f_eq(rho, u). With physical=True, u is the physical
@@ -313,6 +315,7 @@ class Lattice:
             if a.shape != (self.ny, self.nx):
                 raise ValueError(f"density shape {a.shape} != {(self.ny, self.nx)}")
             lbm_set_density_f32(self.ctx, p, False)
+            self.stream.synchronize()
 
     def set_rho_u_field(self, data, physical=False):
         """(rho, u_x, u_y) as one [3, ny, nx] array or device tensor (FP64)."""
